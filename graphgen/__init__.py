@@ -1,0 +1,14 @@
+"""Seeded synthetic inputs shared by the CPU oracle tests and the CUDA tests/benchmarks.
+
+This package generates inputs only and holds none of the method's arithmetic:
+  * R-MAT power-law graphs (symmetrised, self-loops and duplicates removed, 0/1 pattern,
+    int32 column indices) -- the stand-in for the paper's graph datasets (Section 4,
+    Table "graphs"), which are not available;
+  * graphs with closed-form spectra (cycle, complete, star, hypercube, disjoint unions);
+  * seeded N(0, 1) dense blocks.
+"""
+from .graphs import (CSR, rmat, cycle, complete, star, hypercube, path, erdos_renyi,
+                     disjoint_union, from_edges, normal_block, build)
+
+__all__ = ["CSR", "rmat", "cycle", "complete", "star", "hypercube", "path", "erdos_renyi",
+           "disjoint_union", "from_edges", "normal_block", "build"]
