@@ -144,8 +144,9 @@ def block_krylov_schur(rowptr, colidx, nev: int, block: int, nblocks: int, tol: 
     V = np.zeros((n, m + b))
     H = np.zeros((m + b, m))
     state = {"counter": 0, "replacements": 0}
+    # the start block's largest column norm seeds the ||A|| scale of the breakdown test
     anorm = float(np.max(np.linalg.norm(start, axis=0)))
-    Q, _, _ = orth_block(np.zeros((n, 0)), start, 1.0, seed, state)  # orthonormalise start
+    Q, _, _ = orth_block(np.zeros((n, 0)), start, anorm, seed, state)  # orthonormalise start
     V[:, :b] = Q
     k = 0
     restarts = 0
