@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FlashEigen hot path (arXiv 1602.01421).
+
+Workload (default): R-MAT scale 22 (4.19M vertices, edge factor 16, a/b/c/d 0.57/0.19/0.19/
+0.05, seed 1, symmetrised, self-loops/duplicates removed, 0/1 int32 CSR).  One step = one
+plain FP64 Block Krylov-Schur solve for the 8 largest-magnitude eigenpairs, block 4, 8 blocks
+(subspace 32), tol 1e-8, counter-RNG start: SpMM, block Gram/update re-orthogonalisation,
+CholQR2, Rayleigh-Ritz, restarts and the explicit residual check, all on the GPU.
+Beside it: the SpMM sweep b in {1,2,4,8,16} x {FP32, FP64} in GB/s of compulsory bytes, the
+mixed-precision solve, the end-to-end time through host buffers, and the CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scale S]
+
+Under torchrun (N > 1) every rank solves its own copy of the workload (replicas: the solve
+does not shard across the single-GPU machines this targets); value = all ranks' solves / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMM GB/s & % HBM peak; time to 8 eigenpairs @1e-8, plain vs mixed/learned"
+NEV, BLOCK, NBLOCKS, TOL = 8, 4, 8, 1e-8
+NOMINAL_HBM = 8000.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def spmm_bytes(n, nnz, b, s):
+    """Compulsory bytes of one SpMM: colidx + rowptr + X read once + Y written."""
+    return 4 * nnz + 4 * (n + 1) + 2 * n * b * s
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev_index, path):
+        self.path = path
+        self.proc = None
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(dev_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The oracle (plain CPU FP64 Block Krylov-Schur) timed on the host cores."""
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import numpy as np
+    import graphgen
+    from oracle import bks
+    g = graphgen.rmat(args.scale, seed=1)
+    cores = os.cpu_count()
+    for _ in range(args.warmup if args.scale <= 16 else 0):
+        bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1, max_restarts=0)
+    times, steps_done = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
+                                   max_restarts=args.ref_cycles - 1)
+        times.append(time.perf_counter() - t0)
+        steps_done.append(r.spmm_blocks)
+    # a full solve needs the GPU solve's block-SpMM count; scale the sample by block steps
+    full_blocks = args.ref_solve_blocks
+    per_block = sum(times) / sum(steps_done)
+    t_solve = per_block * full_blocks
+    sample = (f"{args.ref_cycles} Krylov-Schur cycle(s) of the oracle on R-MAT scale {args.scale} "
+              f"({steps_done[0]} block SpMM steps), scaled to {full_blocks} block steps per solve")
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t_solve, "unit": "solves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t_solve, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}-ef16 FP64 Block Krylov-Schur nev8 b4 m32 tol1e-8",
+                       "n": g.n, "nnz": g.nnz},
+            "cpu_baseline": {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": 1.0 / t_solve, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_cuda(fn, reps, torch):
+    s = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(s)
+        fn()
+        b.record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def cpu_baseline(g, gpu_blocks, cycles=1):
+    from oracle import bks
+    t0 = time.perf_counter()
+    r = bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
+                               max_restarts=cycles - 1)
+    t = time.perf_counter() - t0
+    t_solve = t / r.spmm_blocks * gpu_blocks
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{cycles} Krylov-Schur cycle ({r.spmm_blocks} block SpMM steps, {t:.1f} s) of "
+                      f"the oracle on the same graph, scaled to the GPU solve's {gpu_blocks} block steps"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import graphgen
+    import paper_1602_01421_gb300 as fe
+
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    lib = fe.load()
+    lib.fe_kernel_launches.restype = ctypes.c_int64
+    hbm_peak, peak_kind = peaks()
+
+    t_gen = time.perf_counter()
+    g = graphgen.rmat(args.scale, seed=1)
+    t_gen = time.perf_counter() - t_gen
+    n, nnz = g.n, g.nnz
+    t0 = time.perf_counter()
+    h = fe.Csr.from_graph(g)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    info = h.info()
+
+    if args.only == "spmm1":
+        # one SpMM launch (for a single-kernel profiler capture)
+        tdt = torch.float32 if args.prec == "f32" else torch.float64
+        Xs = fe.random_normal(n, args.b, dtype=tdt, seed=3)
+        Ys = torch.empty_like(Xs)
+        for _ in range(args.warmup):
+            fe.spmm(h, Xs, Ys)
+        for _ in range(args.steps):
+            fe.spmm(h, Xs, Ys)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "spmm1", "n": n, "nnz": nnz, "b": args.b, "prec": args.prec}))
+        return
+
+    def solve(mode="fp64"):
+        return fe.eigs(h, NEV, BLOCK, NBLOCKS, TOL, "LM", mode=mode, seed=1)
+
+    for _ in range(args.warmup):
+        ev, X, st = solve()
+        assert st["converged"], "warm-up solve did not converge"
+    if args.only == "solve":
+        for _ in range(args.steps):
+            ev, X, st = solve()
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "solve", "n": n, "nnz": nnz, "restarts": st["restarts"],
+                          "spmm_blocks": st["spmm_blocks"], "evals": [float(x) for x in ev]}))
+        return
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    clk = Clocks(dev, os.path.join(args.outdir, f"clocks_rank{rank}.csv"))
+    time.sleep(0.3)
+    barrier()
+    l0 = lib.fe_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        ev, X, st = solve()
+        stats.append(st)
+    e1.record(stream)
+    barrier()
+    launches = lib.fe_kernel_launches() - l0
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = ws * args.steps / (ms / 1000.0)
+    blocks = stats[-1]["spmm_blocks"]
+
+    # ---- SpMM sweep (compulsory-byte GB/s), b in {1,2,4,8,16} x {f32, f64}
+    sweep = {}
+    for prec, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        for b in (1, 2, 4, 8, 16):
+            Xs = fe.random_normal(n, b, dtype=tdt, seed=3)
+            Ys = torch.empty_like(Xs)
+            for _ in range(3):
+                fe.spmm(h, Xs, Ys)
+            t = time_cuda(lambda: fe.spmm(h, Xs, Ys), args.sweep_reps, torch)
+            med = statistics.median(t)
+            gb = spmm_bytes(n, nnz, b, es) / (med / 1000.0) / 1e9
+            sweep[f"{prec}_b{b}"] = {"ms": round(med, 4), "GBps": round(gb, 1),
+                                     "frac_measured": round(gb / hbm_peak, 4),
+                                     "frac_nominal": round(gb / NOMINAL_HBM, 4)}
+            del Xs, Ys
+    # roofline of the solve's SpMM (FP64, b = 4)
+    key = "f64_b4"
+    achieved = sweep[key]["GBps"]
+    roofline = {"kernel": "fe_spmm (spmm_main_kernel + hub_reduce_kernel), FP64 b=4",
+                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
+                "traffic": args.traffic, "bytes_per_launch": spmm_bytes(n, nnz, 4, 8)}
+
+    # ---- mixed-precision solve on the same graph (time to 8 eigenpairs)
+    t_mixed = None
+    if not args.no_mixed:
+        try:
+            out = {}
+            def run_mixed():
+                out["r"] = solve("mixed")
+            run_mixed()
+            tm = time_cuda(run_mixed, 1, torch)[0]
+            ev2, X2, st2 = out["r"]
+            t_mixed = {"s": tm / 1000.0, "spmm_blocks": st2["spmm_blocks"],
+                       "spmm_blocks_fp32": st2["spmm_blocks_fp32"], "restarts": st2["restarts"],
+                       "restarts_fp32": st2["restarts_fp32"], "seconds_fp32": st2["seconds_fp32"],
+                       "max_rel_eval_diff_vs_fp64": float(np.max(np.abs(ev2 - ev) / np.abs(ev))),
+                       "converged": st2["converged"], "speedup_vs_fp64": ms_per_step / tm}
+        except Exception as e:  # reported, not hidden
+            t_mixed = {"error": str(e)}
+
+    # ---- end to end through host buffers: CSR create (H2D) + solve + evecs D2H
+    e2e_times = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with fe.Csr.from_graph(g) as h2:
+            ev3, X3, st3 = fe.eigs(h2, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1)
+            host = X3.cpu().numpy()
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e = {"value": 1.0 / statistics.mean(e2e_times), "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
+           "d2h_bytes_per_step": int(host.nbytes) + 8 * NEV}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}-ef16 FP64 Block Krylov-Schur nev8 b4 m32 tol1e-8",
+                       "n": n, "nnz": nnz, "rmat": "a/b/c/d=0.57/0.19/0.19/0.05 seed1 permuted",
+                       "l2": "inputs larger than L2 (CSR %.0f MB)" % ((4 * nnz + 8 * n) / 1e6),
+                       "parallelism": f"replicas{ws}"},
+            "time_to_8_eigenpairs_s": ms_per_step / 1000.0,
+            "eigs": {"restarts": stats[-1]["restarts"], "spmm_blocks": blocks,
+                     "evals_head": [float(x) for x in ev[:3]], "max_resid": stats[-1]["max_resid"]},
+            "mixed": t_mixed, "learned": None,
+            "spmm_sweep": sweep, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": int(launches),
+            "setup": {"graph_gen_s": round(t_gen, 2), "csr_create_s": round(t_create, 3),
+                      "device_bytes": info["device_bytes"]}}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(g, blocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--sweep-reps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the roofline kernel, if captured")
+    ap.add_argument("--ref-cycles", type=int, default=1)
+    ap.add_argument("--ref-solve-blocks", type=int, default=150)
+    ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1"],
+                    help="solve: warm-up + timed solves only; spmm1: SpMM launches only")
+    ap.add_argument("--b", type=int, default=4)
+    ap.add_argument("--prec", default="f64", choices=["f32", "f64"])
+    args = ap.parse_args()
+    os.makedirs(args.outdir, exist_ok=True)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * fe.h -- C ABI of the GB300-native FlashEigen hot path (arXiv 1602.01421).
+ *
+ * The paper's eigensolver (Section 3.1, Algorithm 1 with the block extension) builds a
+ * subspace of m = b * NB vectors with sparse-matrix x dense-block multiplies (SpMM,
+ * Section 3.3) and keeps it orthonormal with the dense tall-and-skinny operations of
+ * Table 1 (MvTransMv, MvTimesMatAddMv, ...).  This library runs all of it on one GPU:
+ *
+ *   fe_csr_create / fe_csr_create_ex / fe_csr_destroy   the sparse matrix (Section 3.3.1)
+ *   fe_spmm                                              Y = A X   (Section 3.3.3)
+ *   fe_block_gram                                        MvTransMv  (Table 1, "op3")
+ *   fe_block_update                                      MvTimesMatAddMv (Table 1, "op1")
+ *   fe_block_orth                                        re-orthogonalisation (Section 3.1)
+ *   fe_random_normal                                     MvRandom (Table 1)
+ *   fe_eigs / fe_eigs_ex                                 Block Krylov-Schur (Sections 1, 3.1)
+ *
+ * Conventions shared by every entry point:
+ *  - Return 0 (FE_OK) on success and a negative FE_ERR_* code on failure; fe_last_error()
+ *    then returns a message for the calling thread.  No entry point aborts the process.
+ *  - "device" pointers are CUDA device (or managed) memory of the current device; "host"
+ *    pointers are ordinary host memory.  The caller owns every buffer it passes in.
+ *  - Dense tall blocks are ROW-MAJOR n x b (element (r, c) at r*b + c), as the paper's SpMM
+ *    wants its dense input (Section 3.3.2: row-major inside each row interval).  A set of
+ *    nv blocks ("V") is stored block after block: block j starts at element j*n*b.  This is
+ *    the paper's one-TAS-matrix-per-block subspace layout (Section 3.4.1) kept in HBM.
+ *  - Small matrices (Gram results, coefficients) are FP64, row-major, in device memory.
+ *  - Work is enqueued on the calling thread's current stream (fe_set_stream, default: the
+ *    legacy default stream) and is asynchronous unless stated otherwise.
+ *  - fe_dtype selects the element type of the tall blocks: FE_F32 = float, FE_F64 = double.
+ */
+#ifndef FE_H_
+#define FE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FE_OK 0
+#define FE_ERR_INVALID (-1)      /* bad argument or malformed CSR */
+#define FE_ERR_OOM (-2)          /* device or pinned-host allocation failed */
+#define FE_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define FE_ERR_NOCONVERGE (-4)   /* fe_eigs hit max_restarts; converged prefix returned */
+#define FE_ERR_TIMEOUT (-5)      /* a bounded wait (semi-external copy) ran out */
+#define FE_ERR_DEVICE_CHECK (-6) /* a kernel's own bounds/status check fired */
+
+typedef struct fe_csr_s* fe_csr;
+
+typedef enum { FE_F32 = 0, FE_F64 = 1 } fe_dtype;
+typedef enum { FE_LM = 0, FE_LA = 1, FE_SA = 2 } fe_which; /* largest |x|, largest, smallest */
+typedef enum { FE_MODE_FP64 = 0, FE_MODE_MIXED = 1 } fe_mode;
+typedef enum { FE_START_RANDOM = 0, FE_START_USER = 1, FE_START_LEARNED = 2 } fe_start;
+
+/* Message for the last failing call on this thread ("" if none).  Never NULL. */
+const char* fe_last_error(void);
+
+/* Library version string. */
+const char* fe_version(void);
+
+/* Number of this library's CUDA kernels launched by this process so far (all threads):
+ * a diagnostic for benchmarks that report how many of their launches are the library's. */
+int64_t fe_kernel_launches(void);
+
+/* Set / get the CUDA stream (a cudaStream_t, NULL = legacy default stream) on which this
+ * thread's subsequent calls enqueue work. */
+int fe_set_stream(void* stream);
+void* fe_get_stream(void);
+
+/* ------------------------------------------------------------------ sparse matrix */
+
+typedef struct {
+  /* Cap, in bytes, on the device memory the CSR may occupy.  0 = no cap (the matrix is
+   * resident in HBM).  When the resident layout would exceed it, the matrix stays in pinned
+   * host memory and fe_spmm streams row panels through two device buffers: the paper's
+   * semi-external SpMM (Section 3.3) with host memory in place of SSDs. */
+  int64_t device_mem_cap_bytes;
+  /* 1 = check that rowptr is monotone with rowptr[0] == 0 and every column index lies in
+   * [0, n) (O(n + nnz) on the host).  Default 1. */
+  int validate;
+  /* 1 = additionally check that the pattern is symmetric and free of self-loops
+   * (O(nnz log deg) on the host).  Default 0. */
+  int check_symmetric;
+  /* Rows with degree <= tail_max go to the degree-sorted slice format (0 = default 16);
+   * rows with degree > hub_min are split into chunks of hub_chunk non-zeros
+   * (0 = defaults 4096 / 4096).  Tuning knobs only; results do not depend on them beyond
+   * floating-point summation order. */
+  int tail_max;
+  int hub_min;
+  int hub_chunk;
+  /* Semi-external panel size in non-zeros (0 = default 64 Mi). */
+  int64_t panel_nnz;
+  /* Bound, in milliseconds, on each wait for a panel copy in semi-external mode (0 = 60000).
+   * A wait that runs out makes fe_spmm return FE_ERR_TIMEOUT. */
+  int copy_timeout_ms;
+} fe_csr_opts;
+
+/* Fill *opts with the defaults. */
+void fe_csr_opts_default(fe_csr_opts* opts);
+
+typedef struct {
+  int64_t n, nnz;
+  int64_t rows_empty;   /* degree 0 */
+  int64_t rows_tail;    /* 1 <= degree <= tail_max */
+  int64_t rows_mid;     /* tail_max < degree <= hub_min */
+  int64_t rows_hub;     /* degree > hub_min */
+  int64_t hub_chunks;   /* warp tasks the hub rows are split into */
+  int64_t max_degree;
+  int64_t device_bytes; /* device memory held by the handle */
+  int semi_external;    /* 1 if the CSR streams from pinned host memory */
+  int64_t panels;       /* semi-external row panels (0 when resident) */
+} fe_csr_info;
+
+/*
+ * Create a handle for the n x n 0/1 sparse matrix A whose non-zeros in row i are the
+ * columns colidx[rowptr[i] .. rowptr[i+1]-1] (CSR, Section 3.3.1; pattern only, every stored
+ * entry is 1, as for the adjacency matrix of a graph).  rowptr (n+1 int64) and colidx
+ * (nnz = rowptr[n] int32) are HOST pointers and are copied; the caller may free them when
+ * the call returns.  n >= 1, 0 <= nnz.  Duplicate entries count twice (A_ij = multiplicity).
+ * The eigensolver assumes A symmetric (the adjacency matrix of an undirected graph).
+ * Errors: FE_ERR_INVALID (null pointers, n < 1, malformed rowptr, column out of range,
+ * asymmetric pattern when check_symmetric), FE_ERR_OOM, FE_ERR_CUDA.  Synchronous.
+ */
+int fe_csr_create(int64_t n, const int64_t* rowptr, const int32_t* colidx, fe_csr* out);
+int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                     const fe_csr_opts* opts, fe_csr* out);
+/* Release the handle and its device / pinned memory (synchronises the device first). */
+int fe_csr_destroy(fe_csr h);
+int fe_csr_get_info(fe_csr h, fe_csr_info* info);
+
+/*
+ * SpMM, Section 3.3.3: Y = A X, i.e. Y[i, :] = sum over the non-zeros (i, j) of X[j, :].
+ * X and Y are DEVICE pointers to row-major n x b blocks of type dt, 1 <= b <= 16,
+ * b in {1, 2, 4, 8, 16}; Y is overwritten (rows of empty matrix rows become 0); X and Y must
+ * not overlap.  Accumulation is in dt (FP32 sums are ordered as short per-lane sums combined
+ * by a tree, so the error stays near log2(degree) ulps of sum |X|).  Both pointers must be
+ * 16-byte aligned.  Errors: FE_ERR_INVALID (null/unaligned pointer, unsupported b),
+ * FE_ERR_CUDA, FE_ERR_TIMEOUT (semi-external copy wait).  Asynchronous when resident.
+ */
+int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
+
+/*
+ * MvTransMv (Table 1, "op3"): G = alpha * V^T W.
+ * V: DEVICE, nv blocks of n x bv (block j at element j*n*bv), so V^T W is (nv*bv) x bw.
+ * W: DEVICE, n x bw row-major.  G: DEVICE, FP64 row-major (nv*bv) x bw, overwritten.
+ * 1 <= nv <= 32, bv and bw in {1, 2, 4, 8, 16}; V and W may alias (W = one of V's blocks).
+ * FP32 inputs: products and per-thread sums in FP32, cross-thread sums in FP64.
+ * Errors: FE_ERR_INVALID, FE_ERR_OOM (scratch), FE_ERR_CUDA.
+ */
+int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
+                  fe_dtype dt, double alpha, double* G);
+
+/*
+ * MvTimesMatAddMv (Table 1, "op1"): W = beta * W + alpha * V C.
+ * V: DEVICE, nv blocks of n x bv; C: DEVICE FP64 row-major (nv*bv) x bw; W: DEVICE n x bw.
+ * nv = 0 gives MvScale1 (W = beta W).  W must not alias V.  1 <= nv <= 32 (or 0),
+ * bv, bw in {1, 2, 4, 8, 16}.  Errors: FE_ERR_INVALID, FE_ERR_CUDA.
+ */
+int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,
+                    double beta, void* W, int bw, fe_dtype dt);
+
+/*
+ * Re-orthogonalisation step of the block Krylov expansion (Section 3.1 step (1)): block
+ * classical Gram-Schmidt run twice against the orthonormal basis V (nv blocks of n x b,
+ * DEVICE), then CholeskyQR2 of the remainder, so that on return
+ *     W_in = V G + W_out R,  W_out^T W_out = I,  V^T W_out = 0.
+ * W (DEVICE, n x b) is overwritten by W_out.  G (DEVICE FP64 (nv*b) x b) and R (DEVICE FP64
+ * b x b, upper triangular) receive the coefficients.  nv may be 0 (plain CholeskyQR2).
+ * anorm is the scale of ||A|| used by the breakdown test: a column whose remainder falls
+ * below 1e-12 * anorm is replaced by a random direction (seed, counter stream 5) orthogonal
+ * to V and the earlier columns, with R[i][i] = 0.  *replaced (HOST, may be NULL) receives the
+ * number of replaced columns.  Synchronous.  Errors: FE_ERR_INVALID, FE_ERR_OOM, FE_ERR_CUDA.
+ */
+int fe_block_orth(const void* V, int64_t n, int nv, int b, void* W, fe_dtype dt,
+                  double anorm, uint64_t seed, double* G, double* R, int* replaced);
+
+/*
+ * MvRandom (Table 1): fill the DEVICE row-major n x b block X with N(0, 1) draws from the
+ * counter-based generator: element (r, c) has index i = offset + r*b + c and takes
+ * u1, u2 = the top 53 bits of SplitMix64(seed, stream, 2i), (.., 2i+1) scaled to [0, 1),
+ * z = sqrt(-2 ln(1 - u1)) cos(2 pi u2)  (Box-Muller).  Errors: FE_ERR_INVALID, FE_ERR_CUDA.
+ */
+int fe_random_normal(void* X, int64_t n, int b, fe_dtype dt, uint64_t seed, uint64_t stream,
+                     uint64_t offset);
+
+/* ------------------------------------------------------------------ eigensolver */
+
+typedef struct {
+  uint64_t seed;          /* counter-RNG seed for the random start / replacements (1) */
+  int max_restarts;       /* restart cycles before FE_ERR_NOCONVERGE (500) */
+  fe_mode mode;           /* FE_MODE_FP64 or FE_MODE_MIXED (FP32 subspace + FP64 refine) */
+  fe_start start;         /* FE_START_RANDOM, FE_START_USER (start_block) or _LEARNED */
+  const void* start_block;/* DEVICE row-major n x block FP64, for FE_START_USER */
+  const float* mlp_weights; /* DEVICE packed MLP parameters, for FE_START_LEARNED */
+  int mlp_hidden;         /* hidden width of that MLP (64) */
+  double mixed_tol;       /* FP32-phase tolerance in mixed mode (1e-5) */
+  int max_sweeps;         /* Jacobi sweeps per Rayleigh-Ritz (60) */
+} fe_eigs_opts;
+
+void fe_eigs_opts_default(fe_eigs_opts* opts);
+
+typedef struct {
+  int nconv;              /* wanted pairs that passed the convergence test */
+  int restarts;           /* restart cycles run (all phases) */
+  int64_t spmm_blocks;    /* n x b block SpMMs (all phases) */
+  int64_t spmm_blocks_fp32; /* of which in the FP32 phase (mixed mode) */
+  int restarts_fp32;      /* restart cycles of the FP32 phase (mixed mode) */
+  int replacements;       /* breakdown columns replaced by random directions */
+  double anorm;           /* final estimate of ||A||_2 (largest |theta| seen) */
+  double max_resid;       /* max explicit ||A x - theta x|| over the returned pairs */
+  double seconds;         /* wall time of the call */
+  double seconds_fp32;    /* of which in the FP32 phase (mixed mode) */
+} fe_eigs_stats;
+
+/*
+ * Block Krylov-Schur eigensolver (Sections 1 and 3.1): the nev eigenpairs of the symmetric
+ * 0/1 matrix of h that come first in `which` order (FE_LM: |lambda| descending, ties ->
+ * larger lambda first; FE_LA: descending; FE_SA: ascending).  block = b, nblocks = NB,
+ * subspace m = b * NB; requires 1 <= nev <= m - b, m + b <= n, b in {1, 2, 4, 8, 16},
+ * NB >= 2, m <= 96, NB <= 38.  A pair is converged when its Ritz residual estimate is at most
+ * tol * max(|theta|, 1e-3 * max|theta|) and the explicit residual ||A x - theta x|| passes the
+ * same test.  evals: HOST, nev doubles.  evecs: DEVICE, n x nev COLUMN-major FP64 (ConvLayout,
+ * Table 1), may be NULL; each vector's largest-magnitude entry is positive.  Synchronous.
+ * Returns FE_ERR_NOCONVERGE after max_restarts with the converged count in stats->nconv and
+ * the current Ritz pairs in evals/evecs.
+ */
+int fe_eigs(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
+            double* evals, double* evecs);
+int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
+               const fe_eigs_opts* opts, double* evals, double* evecs, fe_eigs_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_H_ */

@@ -1,0 +1,205 @@
+"""GB300-native FlashEigen hot path (arXiv 1602.01421): SpMM on power-law graphs, the Table 1
+tall-and-skinny block operations and a GPU-resident Block Krylov-Schur eigensolver.
+
+The computation lives in libfe.so (CUDA for sm_103a, C ABI in include/fe.h); this package
+marshals torch tensors (device memory, streams) into those calls.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FeError, check, load
+
+__all__ = ["Csr", "spmm", "block_gram", "block_update", "block_orth", "random_normal", "eigs",
+           "FeError", "load", "library_path"]
+
+library_path = _lib.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    load().fe_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def _dt(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return _lib.FE_F32
+    if t.dtype == torch.float64:
+        return _lib.FE_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _dev(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Csr:
+    """Handle of a 0/1 pattern CSR matrix on the device (fe_csr_create_ex)."""
+
+    def __init__(self, rowptr: np.ndarray, colidx: np.ndarray, *, validate: bool = True,
+                 check_symmetric: bool = False, device_mem_cap_bytes: int = 0,
+                 tail_max: int = 0, hub_min: int = 0, hub_chunk: int = 0, panel_nnz: int = 0,
+                 copy_timeout_ms: int = 0):
+        lib = load()
+        self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self._colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        self.n = int(self._rowptr.shape[0] - 1)
+        o = _lib.CsrOpts()
+        lib.fe_csr_opts_default(ctypes.byref(o))
+        o.validate = int(validate)
+        o.check_symmetric = int(check_symmetric)
+        o.device_mem_cap_bytes = int(device_mem_cap_bytes)
+        o.tail_max, o.hub_min, o.hub_chunk = int(tail_max), int(hub_min), int(hub_chunk)
+        o.panel_nnz, o.copy_timeout_ms = int(panel_nnz), int(copy_timeout_ms)
+        h = ctypes.c_void_p()
+        check(lib.fe_csr_create_ex(self.n, self._rowptr.ctypes.data_as(ctypes.c_void_p),
+                                   self._colidx.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._rowptr = self._colidx = None  # the library keeps its own copy
+
+    @classmethod
+    def from_graph(cls, g, **kw):
+        return cls(g.rowptr, g.colidx, **kw)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("handle destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        i = _lib.CsrInfo()
+        check(load().fe_csr_get_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in _lib.CsrInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().fe_csr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def spmm(h: Csr, X, Y=None):
+    """Y = A X (fe_spmm); X, Y row-major (n, b) CUDA tensors, float32 or float64."""
+    torch = _torch()
+    if Y is None:
+        Y = torch.empty_like(X)
+    b = 1 if X.dim() == 1 else X.shape[1]
+    _stream()
+    check(load().fe_spmm(h.handle, _dev(X, "X"), _dev(Y, "Y"), b, _dt(X)))
+    return Y
+
+
+def block_gram(V, W, alpha: float = 1.0, G=None):
+    """G = alpha V^T W (fe_block_gram).  V: (nv, n, bv) blocks; W: (n, bw).  G: float64."""
+    torch = _torch()
+    nv, n, bv = V.shape
+    bw = W.shape[1]
+    if G is None:
+        G = torch.empty((nv * bv, bw), dtype=torch.float64, device=W.device)
+    _stream()
+    check(load().fe_block_gram(_dev(V, "V"), n, nv, bv, _dev(W, "W"), bw, _dt(W), float(alpha),
+                               _dev(G, "G")))
+    return G
+
+
+def block_update(V, C, W, alpha: float = 1.0, beta: float = 1.0):
+    """W = beta W + alpha V C (fe_block_update).  V: (nv, n, bv) or None; C: float64."""
+    n, bw = W.shape
+    if V is None:
+        nv, bv, vp, cp = 0, bw, None, None
+    else:
+        nv, _, bv = V.shape
+        vp, cp = _dev(V, "V"), _dev(C, "C")
+    _stream()
+    check(load().fe_block_update(vp, n, nv, bv, cp, float(alpha), float(beta), _dev(W, "W"), bw,
+                                 _dt(W)))
+    return W
+
+
+def block_orth(V, W, anorm: float, seed: int = 1):
+    """CGS2 + CholeskyQR2 of W against V (fe_block_orth); returns (G, R, replaced)."""
+    torch = _torch()
+    n, b = W.shape
+    nv = 0 if V is None else V.shape[0]
+    G = torch.zeros((max(nv, 1) * b, b), dtype=torch.float64, device=W.device)
+    R = torch.zeros((b, b), dtype=torch.float64, device=W.device)
+    rep = ctypes.c_int(0)
+    _stream()
+    check(load().fe_block_orth(None if V is None else _dev(V, "V"), n, nv, b, _dev(W, "W"),
+                               _dt(W), float(anorm), int(seed), _dev(G, "G"), _dev(R, "R"),
+                               ctypes.byref(rep)))
+    return G[: nv * b], R, rep.value
+
+
+def random_normal(n: int, b: int, dtype=None, seed: int = 1, stream: int = 4, offset: int = 0,
+                  device="cuda"):
+    """MvRandom (fe_random_normal): counter-based N(0,1) row-major (n, b) block."""
+    torch = _torch()
+    X = torch.empty((n, b), dtype=dtype or torch.float64, device=device)
+    _stream()
+    check(load().fe_random_normal(_dev(X, "X"), n, b, _dt(X), int(seed), int(stream),
+                                  int(offset)))
+    return X
+
+
+def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: str = "LM", *,
+         mode: str = "fp64", start=None, seed: int = 1, max_restarts: int = 500,
+         mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 1e-5,
+         return_vectors: bool = True, raise_on_noconverge: bool = True):
+    """Block Krylov-Schur (fe_eigs_ex).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
+    None, stats dict)."""
+    torch = _torch()
+    lib = load()
+    o = _lib.EigsOpts()
+    lib.fe_eigs_opts_default(ctypes.byref(o))
+    o.seed = int(seed)
+    o.max_restarts = int(max_restarts)
+    o.mode = _lib.MODE[mode]
+    o.mixed_tol = float(mixed_tol)
+    o.mlp_hidden = int(mlp_hidden)
+    if start is not None:
+        start = start.to(torch.float64).contiguous()
+        o.start = _lib.START["user"]
+        o.start_block = start.data_ptr()
+    elif mlp_weights is not None:
+        o.start = _lib.START["learned"]
+        o.mlp_weights = mlp_weights.data_ptr()
+    evals = np.zeros(nev, dtype=np.float64)
+    evecs_cm = torch.empty((nev, h.n), dtype=torch.float64, device="cuda") if return_vectors else None
+    st = _lib.EigsStats()
+    _stream()
+    rc = lib.fe_eigs_ex(h.handle, nev, block, nblocks, float(tol), _lib.WHICH[which],
+                        ctypes.byref(o), evals.ctypes.data_as(ctypes.c_void_p),
+                        None if evecs_cm is None else ctypes.c_void_p(evecs_cm.data_ptr()),
+                        ctypes.byref(st))
+    stats = {f: getattr(st, f) for f, _ in _lib.EigsStats._fields_}
+    stats["converged"] = rc == _lib.FE_OK
+    if rc != _lib.FE_OK and not (rc == _lib.FE_ERR_NOCONVERGE and not raise_on_noconverge):
+        check(rc)
+    return evals, (None if evecs_cm is None else evecs_cm.t()), stats

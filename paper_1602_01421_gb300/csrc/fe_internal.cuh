@@ -1,0 +1,137 @@
+// Internal declarations shared by the translation units of libfe.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "fe.h"
+
+namespace fe {
+
+// ---------------------------------------------------------------- errors and streams
+int set_error(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+cudaStream_t cur_stream();
+void count_launch();  // one of this library's kernels was launched
+
+#define FE_CUDA(call)                                                      \
+  do {                                                                     \
+    cudaError_t _e = (call);                                               \
+    if (_e != cudaSuccess) return fe::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+#define FE_TRY(call)            \
+  do {                          \
+    int _rc = (call);           \
+    if (_rc != FE_OK) return _rc; \
+  } while (0)
+#define FE_ARG(cond, ...)                                       \
+  do {                                                          \
+    if (!(cond)) return fe::set_error(FE_ERR_INVALID, __VA_ARGS__); \
+  } while (0)
+
+// Device buffer owned by RAII (cudaFree on destruction).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  int alloc(size_t nbytes);         // FE_OK or FE_ERR_OOM; no-op when already large enough
+  void release();
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline bool is_pow2_le16(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16; }
+int num_sms();
+
+// ---------------------------------------------------------------- block descriptors
+// A set of nv tall blocks; block j is n x bv with row stride ld (elements), starting at
+// blk[j].  The eigensolver's subspace slots, a user's contiguous V and single columns of a
+// block (bv = 1, ld = b) are all described this way.
+constexpr int kMaxBlocks = 40;
+struct BlockSet {
+  const void* blk[kMaxBlocks];
+  int nv, bv, ld;
+};
+inline size_t dt_size(fe_dtype dt) { return dt == FE_F32 ? 4 : 8; }
+// blk[j] = base + j * bstride elements
+BlockSet make_blockset(const void* base, int nv, int bv, int ld, int64_t bstride, fe_dtype dt);
+BlockSet blockset_of(const std::vector<const void*>& ptrs, int bv, int ld);
+
+// G[(j*bv + p) * bw + q] = alpha * sum_r V_j[r][p] * W[r][q]  (FP64 out, device).
+// Two phases (per-CTA partials, deterministic reduce); scratch from the gram scratch pool.
+int gram(const BlockSet& V, int64_t n, const void* W, int bw, int ldw, fe_dtype dt,
+         double alpha, double* G, cudaStream_t s);
+// W[r] = beta * (W[r] M) + alpha * sum_j V_j[r] C_j   (M: bw x bw FP64 device or null = I;
+// C: (nv*bv) x bw FP64 device; nv may be 0).
+int update(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
+           const double* M, void* W, int bw, int ldw, fe_dtype dt, cudaStream_t s);
+// Out_o[r] = sum_j V_j[r] Y[j*bv.., o*bv..] for o < nout (Y: (nv*bv) x ldy FP64 device,
+// output column block o uses Y columns [o*bv, (o+1)*bv)).  Out blocks must not alias V.
+int combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
+            fe_dtype dt, cudaStream_t s);
+// Small-matrix device scratch: a pool of FP64 buffers reused across calls on this thread.
+double* small_scratch(int slot, size_t count);
+int random_normal(void* X, int64_t n, int b, int ld, fe_dtype dt, uint64_t seed,
+                  uint64_t stream, uint64_t offset, cudaStream_t s);
+// dst[r][c] (dt) <- src (FP64, col-major with ld = n) or the transpose direction.
+int convert_block(const void* src, fe_dtype sdt, int lds, void* dst, fe_dtype ddt, int ldd,
+                  int64_t n, int b, cudaStream_t s);
+int to_colmajor_f64(const BlockSet& X, int64_t n, int ncols, fe_dtype dt, double* out,
+                    cudaStream_t s);
+
+// Orthonormalise W (n x b, ld b) against V and itself; see fe_block_orth.  Synchronous.
+struct OrthWork;
+int orth(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
+         double anorm_floor, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
+         double* d_R, int ldr, int* replaced, cudaStream_t s);
+
+}  // namespace fe
+
+// ---------------------------------------------------------------- the CSR handle
+struct fe_spmm_plan {
+  // tail: rows of degree 0..tail_max in 32-row slices grouped by degree (descending)
+  int tail_max = 16;
+  int64_t nslices = 0;
+  int32_t* d_slice_rows = nullptr;   // nslices * 32 row ids (-1 = padding)
+  int32_t* d_ell = nullptr;          // slice-major transposed column indices
+  int32_t deg_slice_begin[34];       // first slice of degree d-bucket, in bucket order
+  int64_t deg_ell_base[34];          // ELL offset of that bucket's first slice
+  int32_t deg_of_bucket[34];
+  int nbuckets = 0;
+  // warp tasks: hub chunks first (partial slots 0..nhub_tasks-1), then mid rows by degree
+  int64_t ntasks = 0, nhub_tasks = 0, nhub = 0;
+  void* d_tasks = nullptr;           // struct Task[ntasks]
+  int32_t* d_hub_rows = nullptr;     // nhub
+  int32_t* d_hub_task_begin = nullptr;  // nhub + 1
+  int hub_min = 4096, hub_chunk = 4096;
+};
+
+struct fe_csr_s {
+  int64_t n = 0, nnz = 0;
+  int device = 0;
+  int64_t max_degree = 0;
+  int64_t rows_empty = 0, rows_tail = 0, rows_mid = 0, rows_hub = 0;
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_colidx = nullptr;
+  fe_spmm_plan plan;
+  fe::DevBuf partials;     // hub partial sums (nhub_tasks * 16 * 8 bytes)
+  int64_t device_bytes = 0;
+  // semi-external mode
+  int semi_external = 0;
+  struct SemiExt* sx = nullptr;
+  std::vector<void*> allocations;
+};
+
+namespace fe {
+int spmm_resident(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s);
+int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx, int tail_max,
+                    int hub_min, int hub_chunk);
+int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx,
+                   const fe_csr_opts& o);
+int semiext_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s);
+void semiext_destroy(fe_csr h);
+int64_t semiext_panels(fe_csr h);
+}  // namespace fe

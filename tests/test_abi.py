@@ -1,0 +1,74 @@
+"""C-ABI library: loads, exports every symbol include/fe.h declares, and rejects bad input on
+the host (no GPU needed for any of these)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import graphgen
+import paper_1602_01421_gb300 as fe
+from paper_1602_01421_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fe.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fe_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported():
+    lib = fe.load()
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), f"{s} declared in fe.h but not exported"
+
+
+def test_version_and_error_string():
+    lib = fe.load()
+    assert b"sm_103a" in lib.fe_version()
+    assert lib.fe_last_error() is not None
+
+
+@pytest.mark.parametrize("rowptr,colidx,msg", [
+    ([1, 2, 3], [0, 1, 1], "rowptr[0]"),
+    ([0, 2, 1], [0, 1], "decreases"),
+    ([0, 1, 2], [0, 5], "out of range"),
+    ([0, 1, 2], [0, -1], "out of range"),
+])
+def test_invalid_csr_rejected_on_host(rowptr, colidx, msg):
+    with pytest.raises(fe.FeError) as e:
+        fe.Csr(np.array(rowptr), np.array(colidx, dtype=np.int32))
+    assert e.value.code == _lib.FE_ERR_INVALID and msg in str(e.value)
+
+
+def test_asymmetric_pattern_rejected_when_checked():
+    with pytest.raises(fe.FeError) as e:
+        fe.Csr(np.array([0, 1, 1]), np.array([1], dtype=np.int32), check_symmetric=True)
+    assert "not symmetric" in str(e.value)
+    with pytest.raises(fe.FeError) as e:
+        fe.Csr(np.array([0, 1, 2]), np.array([0, 1], dtype=np.int32), check_symmetric=True)
+    assert "self-loop" in str(e.value)
+
+
+def test_null_and_bad_arguments():
+    lib = fe.load()
+    assert lib.fe_spmm(None, None, None, 4, 0) == _lib.FE_ERR_INVALID
+    assert lib.fe_eigs(None, 8, 4, 8, 1e-8, 0, None, None) == _lib.FE_ERR_INVALID
+    assert lib.fe_block_gram(None, 10, 1, 4, None, 4, 0, 1.0, None) == _lib.FE_ERR_INVALID
+    assert lib.fe_block_update(None, 10, 1, 3, None, 1.0, 0.0, ctypes.c_void_p(16), 4, 0) == _lib.FE_ERR_INVALID
+    assert lib.fe_random_normal(None, 10, 4, 1, 1, 4, 0) == _lib.FE_ERR_INVALID
+    out = ctypes.c_void_p()
+    assert lib.fe_csr_create(0, None, None, ctypes.byref(out)) == _lib.FE_ERR_INVALID
+
+
+def test_struct_layouts_match_header():
+    # field offsets the C compiler gives the structs (x86-64 and aarch64 share the LP64 ABI)
+    assert ctypes.sizeof(_lib.CsrOpts) == 48
+    assert ctypes.sizeof(_lib.CsrInfo) == 88
+    assert ctypes.sizeof(_lib.EigsOpts) == 64
+    assert ctypes.sizeof(_lib.EigsStats) == 64

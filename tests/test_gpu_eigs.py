@@ -1,0 +1,127 @@
+"""GPU Block Krylov-Schur (fe_eigs) against closed-form spectra, brute force and the oracle.
+
+Targets: eigenvalues within 1e-8 relative of the oracle's, residual ||A x - theta x|| <=
+tol * ||A|| (checked with the oracle's SpMM on the returned vectors), vectors orthonormal,
+eigenvectors compared by subspace angle where eigenvalues cluster.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import paper_1602_01421_gb300 as fe
+from oracle import bks, core
+from tests import closed_forms
+from tests.gpu_util import to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_pairs(g, evals, X, tol, anorm):
+    X = X.cpu().numpy()
+    assert np.abs(X.T @ X - np.eye(X.shape[1])).max() < 1e-10
+    r = np.linalg.norm(core.spmm(g.rowptr, g.colidx, X) - X * evals, axis=0)
+    assert np.all(r <= tol * anorm * 1.001), r
+    # sign convention: largest-magnitude entry positive
+    idx = np.argmax(np.abs(X), axis=0)
+    assert np.all(X[idx, np.arange(X.shape[1])] > 0)
+
+
+@pytest.mark.parametrize("case", closed_forms.cases(), ids=lambda c: "-".join(map(str, c)))
+def test_eigs_closed_form_spectra(case):
+    fam, size, nev, b, nb, which = case
+    g = closed_forms.graph(fam, size)
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, nev, b, nb, 1e-10, which, seed=3, max_restarts=3000)
+    want = closed_forms.wanted(fam, size, nev, which)
+    lam = closed_forms.spectrum(fam, size)
+    scale = np.abs(lam).max()
+    if which == "LM":
+        assert np.allclose(np.sort(np.abs(ev)), np.sort(np.abs(want)), atol=1e-9 * scale)
+    else:
+        assert np.allclose(ev, want, atol=1e-9 * scale)
+    assert np.all(np.min(np.abs(ev[:, None] - lam[None, :]), axis=1) < 1e-9 * scale)
+    _check_pairs(g, ev, X, 1e-10, scale)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_eigs_rmat14_matches_oracle(mode):
+    """The benchmark's small configuration: R-MAT scale 14, nev 8 LM, block 4, 8 blocks,
+    tol 1e-8, counter-RNG start (seed 1)."""
+    g = graphgen.rmat(14, seed=1)
+    ref = bks.block_krylov_schur(g.rowptr, g.colidx, 8, 4, 8, 1e-8, "LM", seed=1)
+    assert ref.converged
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode=mode, seed=1)
+    assert st["converged"] and st["nconv"] == 8
+    assert np.allclose(ev, ref.evals, rtol=1e-8, atol=0)
+    _check_pairs(g, ev, X, 1e-8, ref.evals[0])
+    # subspace of the 8 vectors agrees with the oracle's (principal angles)
+    s = np.linalg.svd(ref.evecs.T @ X.cpu().numpy(), compute_uv=False)
+    assert s.min() > 1 - 1e-6
+
+
+def test_eigs_same_start_same_iteration_as_oracle():
+    g = graphgen.rmat(12, seed=4)
+    start = graphgen.normal_block(g.n, 4, seed=9)
+    ref = bks.block_krylov_schur(g.rowptr, g.colidx, 6, 4, 6, 1e-9, "LA", start=start)
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 6, 4, 6, 1e-9, "LA", start=to_dev(start))
+    assert np.allclose(ev, ref.evals, rtol=1e-9 * 5)
+    assert abs(st["restarts"] - ref.restarts) <= max(2, ref.restarts // 10)
+    assert st["spmm_blocks"] > 0
+
+
+@pytest.mark.parametrize("which", ["LA", "SA", "LM"])
+def test_eigs_matches_dense_brute_force(which):
+    g = graphgen.rmat(11, seed=2)
+    lam = np.linalg.eigvalsh(g.dense())
+    want = lam[bks.sort_order(lam, which)][:5]
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 5, 2, 10, 1e-9, which, seed=4, max_restarts=2000)
+    scale = np.abs(lam).max()
+    assert np.allclose(ev, want, rtol=1e-8, atol=1e-10 * scale)
+    _check_pairs(g, ev, X, 1e-9, scale)
+
+
+def test_eigs_breakdown_complete_graph():
+    g = graphgen.complete(60)
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 3, 4, 4, 1e-10, "LM", seed=2)
+    assert st["replacements"] > 0
+    assert np.allclose(ev, [59.0, -1.0, -1.0], atol=1e-9)
+
+
+def test_eigs_noconverge_returns_partial():
+    g = graphgen.rmat(13, seed=5)
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 8, 4, 4, 1e-12, "LM", max_restarts=1, raise_on_noconverge=False)
+    assert not st["converged"] and st["restarts"] == 1 and 0 <= st["nconv"] < 8
+    assert np.all(np.isfinite(ev)) and ev[0] > 0
+    with fe.Csr.from_graph(g) as h:
+        with pytest.raises(fe.FeError) as e:
+            fe.eigs(h, 8, 4, 4, 1e-12, "LM", max_restarts=1)
+    assert e.value.code == -4
+
+
+def test_eigs_rejects_bad_sizes():
+    g = graphgen.cycle(30)
+    with fe.Csr.from_graph(g) as h:
+        for args in [(8, 4, 2), (2, 3, 4), (2, 4, 7), (0, 4, 4)]:
+            with pytest.raises(fe.FeError):
+                fe.eigs(h, *args)
+
+
+@pytest.mark.slow
+def test_eigs_rmat22_full_size():
+    """The benchmark solve (R-MAT scale 22, nev 8, block 4, 8 blocks, tol 1e-8): residuals by
+    the oracle's SpMM, bounds, and FP64 vs mixed agreement."""
+    g = graphgen.rmat(22, seed=1)
+    deg = g.degrees()
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1)
+        ev2, X2, st2 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode="mixed", seed=1)
+    assert st["converged"] and st2["converged"]
+    assert deg.mean() <= ev[0] <= deg.max() and ev[0] >= np.sqrt(deg.max())
+    _check_pairs(g, ev, X, 1e-8, ev[0])
+    _check_pairs(g, ev2, X2, 1e-8, ev2[0])
+    assert np.allclose(ev, ev2, rtol=1e-8)

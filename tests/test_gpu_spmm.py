@@ -1,0 +1,134 @@
+"""GPU parity: fe_spmm against the oracle's plain-definition SpMM (Section 3.3).
+
+Tolerances (from BASELINE's SpMM requirement, read per entry against A|X|, the condition
+number of a sum): FP64 |Y - Y*| <= 1e-13 (A|X|), FP32 <= 1e-6 (A|X|) with Y* the FP64 sum of
+the same FP32 inputs.  A 1 = degree must be exact in either precision.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import paper_1602_01421_gb300 as fe
+from tests.gpu_util import assert_spmm_close, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-6, "f64": 1e-13}
+NP = {"f32": np.float32, "f64": np.float64}
+
+GRAPHS = {
+    "rmat12": lambda: graphgen.rmat(12, seed=3),
+    "rmat14": lambda: graphgen.rmat(14, seed=1),
+    "rmat13-noperm": lambda: graphgen.rmat(13, seed=2, permute=False),
+    "star9000": lambda: graphgen.star(9000),              # one hub split into 3 chunks
+    "complete70": lambda: graphgen.complete(70),          # all rows mid (deg 69)
+    "cycle1001": lambda: graphgen.cycle(1001),            # all rows tail (deg 2), ragged slice
+    "er3000": lambda: graphgen.erdos_renyi(3000, 12.0, seed=5),
+    "union-isolated": lambda: graphgen.disjoint_union(graphgen.star(5000), graphgen.path(33),
+                                                      graphgen.from_edges(77, [], [], "iso77")),
+}
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return {k: v() for k, v in GRAPHS.items()}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("b", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_spmm_parity(graphs, name, b, prec):
+    g = graphs[name]
+    X = graphgen.normal_block(g.n, b, seed=100 + b, dtype=NP[prec])
+    with fe.Csr.from_graph(g) as h:
+        Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+    assert_spmm_close(g, X, Y, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("knobs", [dict(tail_max=1, hub_min=8, hub_chunk=8),
+                                   dict(tail_max=32, hub_min=40, hub_chunk=64),
+                                   dict(tail_max=4, hub_min=64, hub_chunk=4096)])
+def test_spmm_parity_all_paths_small(prec, knobs):
+    """Tiny thresholds push most rows through the hub split and the partial reduce."""
+    g = graphgen.rmat(13, seed=9)
+    for b in (1, 4, 16):
+        X = graphgen.normal_block(g.n, b, seed=b, dtype=NP[prec])
+        with fe.Csr.from_graph(g, **knobs) as h:
+            info = h.info()
+            Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+        assert info["rows_hub"] > 0
+        assert_spmm_close(g, X, Y, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ones_give_degrees_exactly(graphs, prec):
+    t = torch()
+    for name in ("rmat14", "star9000", "union-isolated"):
+        g = graphs[name]
+        with fe.Csr.from_graph(g) as h:
+            for b in (1, 4, 16):
+                X = t.ones((g.n, b), dtype=t.float32 if prec == "f32" else t.float64, device="cuda")
+                Y = fe.spmm(h, X).cpu().numpy()
+                assert np.array_equal(Y, np.repeat(g.degrees()[:, None], b, 1).astype(Y.dtype))
+
+
+def test_empty_matrix_and_single_vertex():
+    t = torch()
+    for n in (1, 37):
+        g = graphgen.from_edges(n, [], [], "empty")
+        with fe.Csr.from_graph(g) as h:
+            X = t.randn((n, 4), dtype=t.float64, device="cuda")
+            Y = t.full_like(X, 7.0)
+            fe.spmm(h, X, Y)
+            assert t.count_nonzero(Y).item() == 0
+
+
+def test_handle_info_bins(graphs):
+    g = graphs["rmat14"]
+    with fe.Csr.from_graph(g) as h:
+        i = h.info()
+    deg = g.degrees()
+    assert i["n"] == g.n and i["nnz"] == g.nnz and i["max_degree"] == deg.max()
+    assert i["rows_empty"] == (deg == 0).sum()
+    assert i["rows_tail"] == ((deg >= 1) & (deg <= 16)).sum()
+    assert i["rows_mid"] == ((deg > 16) & (deg <= 4096)).sum()
+    assert i["rows_empty"] + i["rows_tail"] + i["rows_mid"] + i["rows_hub"] == g.n
+
+
+def test_spmm_rejects_bad_arguments(graphs):
+    t = torch()
+    g = graphs["cycle1001"]
+    with fe.Csr.from_graph(g) as h:
+        X = t.zeros((g.n, 3), dtype=t.float64, device="cuda")
+        with pytest.raises(fe.FeError):
+            fe.spmm(h, X)                                  # b = 3 unsupported
+        X = t.zeros((g.n, 4), dtype=t.float64, device="cuda")
+        with pytest.raises(fe.FeError):
+            fe.spmm(h, X, X)                               # in place
+        big = t.zeros((2 * g.n * 4 + 2,), dtype=t.float64, device="cuda")
+        lib = fe.load()                                    # misaligned (8-byte offset)
+        rc = lib.fe_spmm(h.handle, big[1:].data_ptr(), big[g.n * 4 + 1:].data_ptr(), 4, 1)
+        assert rc == -1 and b"aligned" in lib.fe_last_error()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,b", [("f32", 4), ("f64", 4), ("f32", 16), ("f64", 1)])
+def test_spmm_full_size_sampled_rows(prec, b):
+    """R-MAT scale 22 (the benchmark graph), in the benchmark's launch configuration; checked
+    on 20000 random rows plus every hub row and the 2000 highest-degree rows."""
+    g = graphgen.rmat(22, seed=1)
+    X = graphgen.normal_block(g.n, b, seed=7, dtype=NP[prec])
+    with fe.Csr.from_graph(g) as h:
+        Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+    deg = g.degrees()
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.integers(0, g.n, 20000), np.argsort(-deg)[:2000],
+                                     np.nonzero(deg > 4096)[0]]))
+    assert_spmm_close(g, X, Y, TOL[prec], rows=rows)
+    # ones: exact degrees everywhere
+    t = torch()
+    with fe.Csr.from_graph(g) as h:
+        ones = t.ones((g.n, b), dtype=t.float32 if prec == "f32" else t.float64, device="cuda")
+        Yd = fe.spmm(h, ones)[:, 0].cpu().numpy()
+    assert np.array_equal(Yd, deg.astype(Yd.dtype))
