@@ -151,6 +151,23 @@ int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int b
                   fe_dtype dt, double alpha, double* G);
 
 /*
+ * fe_block_gram without any device allocation.  The paper has no counterpart; this entry point
+ * exists for callers that cannot let the library call cudaMalloc: programs whose device
+ * memory is reserved up front by their own allocator, with nothing left to hand out, and code
+ * that must not make calls that can synchronise the whole device, as cudaMalloc and cudaFree
+ * may.  Arguments, layouts, result and error codes are those of fe_block_gram, except:
+ *  - nv * bv * bw must be at most 2048 (larger G: FE_ERR_INVALID with a message);
+ *  - the per-CTA partial sums live in a 2 MiB static device array inside the library, which
+ *    every GPU that loads the library holds until the process exits;
+ *  - the first call on each device looks up that array's device address (done with the
+ *    device current, kept for later calls); make that first call before any stream capture;
+ *  - all calls share the array, so calls whose work overlaps on the GPU (other streams, other
+ *    host threads) race; each call writes every partial it reads, so nothing needs clearing.
+ */
+int fe_block_gram_noalloc(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
+                          fe_dtype dt, double alpha, double* G);
+
+/*
  * MvTimesMatAddMv (Table 1, "op1"): W = beta * W + alpha * V C.
  * V: DEVICE, nv blocks of n x bv; C: DEVICE FP64 row-major (nv*bv) x bw; W: DEVICE n x bw.
  * nv = 0 gives MvScale1 (W = beta W).  W must not alias V.  1 <= nv <= 32 (or 0),

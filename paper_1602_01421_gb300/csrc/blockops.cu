@@ -495,3 +495,78 @@ int to_colmajor_f64(const BlockSet& X, int64_t n, int ncols, fe_dtype dt, double
 }
 
 }  // namespace fe
+
+namespace fe {
+
+// ---------------------------------------------------------------- gram into given scratch
+// Same kernels as gram(), but the per-CTA partials go to `scratch` (capacity doubles) supplied
+// by the caller, and nothing is allocated here.  The grid shrinks so the partials fit.
+template <typename T, int BV, int NQ>
+static int launch_gram_scratch(const BlockSet& V, int64_t n, const T* W, int bw, int ldw,
+                               double alpha, double* G, double* scratch, size_t capacity,
+                               cudaStream_t s) {
+  const int nout = V.nv * BV * bw;
+  int R = (int)(32768 / ((size_t)bw * sizeof(T)));
+  R = std::max(32, R - R % 32);
+  const size_t smem = (((size_t)R * bw * sizeof(T) + 15) & ~(size_t)15) + (size_t)nout * sizeof(double);
+  FE_ARG(smem <= 200 * 1024, "gram: output too large (%d entries)", nout);
+  static bool configured = false;
+  if (!configured) {
+    FE_CUDA(cudaFuncSetAttribute(gram_kernel<T, BV, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured = true;
+  }
+  int64_t nctas = std::min<int64_t>(ceil_div(n, R), 2 * num_sms());
+  nctas = std::min<int64_t>(nctas, (int64_t)(capacity / (size_t)nout));
+  FE_ARG(nctas >= 1, "gram: scratch of %zu doubles cannot hold %d outputs", capacity, nout);
+  gram_kernel<T, BV, NQ><<<(unsigned)nctas, 256, smem, s>>>(V, W, ldw, bw, n, R, scratch);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  gram_reduce_kernel<<<(unsigned)ceil_div(nout, 128), 128, 0, s>>>(scratch, (int)nctas, nout, alpha, G);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+template <typename T, int BV>
+static int gram_scratch_bv(const BlockSet& V, int64_t n, const T* W, int bw, int ldw,
+                           double alpha, double* G, double* scratch, size_t capacity,
+                           cudaStream_t s) {
+  constexpr int QMAX = 32 / BV >= 16 ? 16 : 32 / BV;
+  const int nq = std::min(bw, QMAX);
+  switch (nq) {
+    case 1: return launch_gram_scratch<T, BV, 1>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+    case 2: return launch_gram_scratch<T, BV, (QMAX >= 2 ? 2 : 1)>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+    case 4: return launch_gram_scratch<T, BV, (QMAX >= 4 ? 4 : 1)>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+    case 8: return launch_gram_scratch<T, BV, (QMAX >= 8 ? 8 : 1)>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+    case 16: return launch_gram_scratch<T, BV, (QMAX >= 16 ? 16 : 1)>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+  }
+  return set_error(FE_ERR_INVALID, "gram: bad bw %d", bw);
+}
+
+int gram_into_scratch(const BlockSet& V, int64_t n, const void* W, int bw, int ldw, fe_dtype dt,
+                      double alpha, double* G, double* scratch, size_t capacity, cudaStream_t s) {
+  FE_ARG(V.nv >= 1 && V.nv <= kMaxBlocks, "gram: nv = %d out of range", V.nv);
+  FE_ARG(is_pow2_le16(bw), "gram: bw = %d", bw);
+  if (dt == FE_F32) {
+    const float* w = static_cast<const float*>(W);
+    switch (V.bv) {
+      case 1: return gram_scratch_bv<float, 1>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 2: return gram_scratch_bv<float, 2>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 4: return gram_scratch_bv<float, 4>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 8: return gram_scratch_bv<float, 8>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 16: return gram_scratch_bv<float, 16>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+    }
+  } else {
+    const double* w = static_cast<const double*>(W);
+    switch (V.bv) {
+      case 1: return gram_scratch_bv<double, 1>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 2: return gram_scratch_bv<double, 2>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 4: return gram_scratch_bv<double, 4>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 8: return gram_scratch_bv<double, 8>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+      case 16: return gram_scratch_bv<double, 16>(V, n, w, bw, ldw, alpha, G, scratch, capacity, s);
+    }
+  }
+  return set_error(FE_ERR_INVALID, "gram: bv = %d not in {1,2,4,8,16}", V.bv);
+}
+
+}  // namespace fe
