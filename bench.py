@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 METRIC = "SpMM GB/s & % HBM peak; time to 8 eigenpairs @1e-8, plain vs mixed/learned"
 NEV, BLOCK, NBLOCKS, TOL = 8, 4, 8, 1e-8
 NOMINAL_HBM = 8000.0
+# FP64 on GB300: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz x 2 flop = 1.26 TFLOP/s (the
+# nominal 1.25 TFLOP/s); the solve's FP64 block kernels are bound by it, not by HBM.
+FP64_PEAK_GFLOPS = 1250.0
 
 
 def peaks():
@@ -260,13 +263,32 @@ def run_ours(args):
                                      "frac_measured": round(gb / hbm_peak, 4),
                                      "frac_nominal": round(gb / NOMINAL_HBM, 4)}
             del Xs, Ys
-    # roofline of the solve's SpMM (FP64, b = 4)
-    key = "f64_b4"
-    achieved = sweep[key]["GBps"]
-    roofline = {"kernel": "fe_spmm (spmm_main_kernel + hub_reduce_kernel), FP64 b=4",
-                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
-                "traffic": args.traffic, "bytes_per_launch": spmm_bytes(n, nnz, 4, 8)}
+    # SpMM roofline (the metric's kernel), FP32 b = 4 and the solve's FP64 b = 4
+    spmm_roofline = {}
+    for key, es in (("f32_b4", 4), ("f64_b4", 8)):
+        achieved = sweep[key]["GBps"]
+        spmm_roofline[key] = {"kernel": "spmm_main_kernel + hub_reduce_kernel", "bound": "hbm",
+                              "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
+                              "bytes_per_launch": spmm_bytes(n, nnz, 4, es)}
+    # dominant kernel of the FP64 solve (launch list): gram_kernel<double,4,4> at the solve's
+    # mean shape, 7 blocks of n x 4 (k + b = 28 columns) against n x 4
+    nvg = 7
+    Vg = fe.random_normal(nvg * n, 4, dtype=torch.float64, seed=5).view(nvg, n, 4)
+    Wg = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+    for _ in range(3):
+        fe.block_gram(Vg, Wg)
+    tg = statistics.median(time_cuda(lambda: fe.block_gram(Vg, Wg), 10, torch))
+    flops = 2.0 * n * nvg * 4 * 4
+    gflops = flops / (tg / 1000.0) / 1e9
+    roofline = {"kernel": "gram_kernel<double,4,4> + gram_reduce_kernel (MvTransMv, FP64)",
+                "bound": "alu", "achieved": round(gflops, 1), "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
+                "peak_kind": "nominal FP64 rate (unit count x clock)", "traffic": args.traffic,
+                "flops_per_launch": flops, "bytes_per_launch": 8 * n * (nvg * 4 + 4),
+                "ms_per_launch": round(tg, 4),
+                "hbm_frac": round(8 * n * (nvg * 4 + 4) / (tg / 1000.0) / 1e9 / hbm_peak, 4)}
+    del Vg, Wg
 
     # ---- mixed-precision solve on the same graph (time to 8 eigenpairs)
     t_mixed = None
@@ -285,6 +307,52 @@ def run_ours(args):
                        "converged": st2["converged"], "speedup_vs_fp64": ms_per_step / tm}
         except Exception as e:  # reported, not hidden
             t_mixed = {"error": str(e)}
+
+    # ---- learned start: MLP trained on small R-MAT graphs, time to 8 pairs on this graph
+    learned_res = None
+    if not args.no_learned:
+        try:
+            from paper_1602_01421_gb300 import learned as L
+            t0 = time.perf_counter()
+            ex = [L.make_example(graphgen.rmat(sc, seed=100 + i), BLOCK, offset=args.learned_offset)
+                  for i, sc in enumerate([12, 13, 14, 15, 16] * 2)]
+            params, losses = L.train(ex, hidden=64, b=BLOCK, steps=600, lr=3e-3)
+            t_train = time.perf_counter() - t0
+            out = {}
+            def run_learned():
+                out["r"] = fe.eigs(h, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1, mlp_weights=params,
+                                   mlp_hidden=64)
+            run_learned()
+            tl = time_cuda(run_learned, 1, torch)[0]
+            ev4, X4, st4 = out["r"]
+            learned_res = {"s": tl / 1000.0, "spmm_blocks": st4["spmm_blocks"],
+                           "spmm_start_calls": st4["spmm_start"], "restarts": st4["restarts"],
+                           "speedup_vs_fp64_random": ms_per_step / tl,
+                           "max_rel_eval_diff_vs_fp64": float(np.max(np.abs(ev4 - ev) / np.abs(ev))),
+                           "train": {"graphs": len(ex), "scales": "12-16", "steps": 600,
+                                     "final_loss": float(np.mean(losses[-50:])),
+                                     "target_ritz_offset": args.learned_offset,
+                                     "s": round(t_train, 2)}}
+        except Exception as e:
+            learned_res = {"error": str(e)}
+
+    # ---- semi-external: the same SpMM with the CSR streamed from pinned host memory
+    semi = None
+    if not args.no_semi:
+        try:
+            cap = 256 << 20
+            with fe.Csr.from_graph(g, device_mem_cap_bytes=cap) as hs:
+                si = hs.info()
+                Xs = fe.random_normal(n, 4, dtype=torch.float32, seed=3)
+                Ys = torch.empty_like(Xs)
+                fe.spmm(hs, Xs, Ys)
+                ts = statistics.median(time_cuda(lambda: fe.spmm(hs, Xs, Ys), 5, torch))
+            semi = {"cap_bytes": cap, "panels": si["panels"], "device_bytes": si["device_bytes"],
+                    "f32_b4_ms": round(ts, 3),
+                    "GBps": round(spmm_bytes(n, nnz, 4, 4) / (ts / 1000.0) / 1e9, 1),
+                    "h2d_GBps": round((4 * nnz + 16 * si["rows_mid"]) / (ts / 1000.0) / 1e9, 1)}
+        except Exception as e:
+            semi = {"error": str(e)}
 
     # ---- end to end through host buffers: CSR create (H2D) + solve + evecs D2H
     e2e_times = []
@@ -312,8 +380,9 @@ def run_ours(args):
             "time_to_8_eigenpairs_s": ms_per_step / 1000.0,
             "eigs": {"restarts": stats[-1]["restarts"], "spmm_blocks": blocks,
                      "evals_head": [float(x) for x in ev[:3]], "max_resid": stats[-1]["max_resid"]},
-            "mixed": t_mixed, "learned": None,
-            "spmm_sweep": sweep, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "mixed": t_mixed, "learned": learned_res, "semi_external": semi,
+            "spmm_sweep": sweep, "spmm_roofline": spmm_roofline, "roofline": roofline,
+            "clocks": clocks, "e2e": e2e,
             "gpu_launches": int(launches),
             "setup": {"graph_gen_s": round(t_gen, 2), "csr_create_s": round(t_create, 3),
                       "device_bytes": info["device_bytes"]}}
@@ -338,6 +407,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-semi", action="store_true")
+    ap.add_argument("--learned-offset", type=int, default=0,
+                    help="first Ritz vector (largest-magnitude order) the MLP is trained to predict")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the roofline kernel, if captured")
     ap.add_argument("--ref-cycles", type=int, default=1)

@@ -200,6 +200,40 @@ int fe_block_orth(const void* V, int64_t n, int nv, int b, void* W, fe_dtype dt,
 int fe_random_normal(void* X, int64_t n, int b, fe_dtype dt, uint64_t seed, uint64_t stream,
                      uint64_t offset);
 
+/* ------------------------------------------------------------------ learned start block */
+/* Not in the paper (its solver starts from MvRandom, Table 1): a small MLP maps per-vertex
+ * features computed with SpMM (Section 3.3) to an n x b start block.  Features, network and
+ * loss are specified in the comments of fe_vertex_features / fe_mlp_forward /
+ * fe_mlp_loss_grad; all arrays are DEVICE, row-major, FP32 unless stated. */
+#define FE_NFEAT 8
+
+/* Number of packed MLP parameters for hidden width `hidden` (32 or 64) and b outputs
+ * (1, 2, 4, 8, 16): 8H + H + H^2 + H + Hb + b, packed as [W1 (8 x H), b1, W2 (H x H), b2,
+ * W3 (H x b), b3], row-major.  Returns -1 for unsupported sizes. */
+int64_t fe_mlp_param_count(int hidden, int b);
+
+/* F (n x 8): d = A 1; f0 = log(1+d), f1 = d/rms(d), f2 = A d/rms(A d), f3 = A^2 d/rms(A^2 d);
+ * with R = N(0,1) n x 4 from the counter generator (seed, stream 6) and q_p = mean over
+ * columns of (A^p R)^2 (p = 2, 3, 4): f4 = q2/rms(q2), f5 = q3/rms(q3), f6 = q4/rms(q4),
+ * f7 = log(1 + q2/mean(q2)); rms(x) = sqrt(mean(x^2)) (1 if 0).  SpMMs in FP64, F in FP32.
+ * Synchronous.  Errors: FE_ERR_INVALID, FE_ERR_OOM, FE_ERR_CUDA. */
+int fe_vertex_features(fe_csr h, uint64_t seed, float* F);
+
+/* Z (n x b) = relu(relu(F W1 + b1) W2 + b2) W3 + b3. */
+int fe_mlp_forward(const float* F, int64_t n, const float* params, int hidden, int b, float* Z);
+
+/* Loss L = sum_j (1 - (z_j . u_j)^2 / |z_j|^2) of the network output Z against U (n x b, unit
+ * columns; invariant to each column's sign) and its gradient with respect to the packed
+ * parameters (grad: DEVICE, fe_mlp_param_count floats, overwritten).  loss: HOST, may be NULL
+ * (when given the call synchronises).  Sums over rows are per-CTA partials added in order in
+ * FP64 (deterministic). */
+int fe_mlp_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                     const float* U, float* grad, double* loss);
+
+/* One Adam step (Kingma & Ba 2015, bias-corrected; step counts from 1) on count parameters. */
+int fe_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count, double lr,
+                double beta1, double beta2, double eps, int step);
+
 /* ------------------------------------------------------------------ eigensolver */
 
 typedef struct {
@@ -208,8 +242,9 @@ typedef struct {
   fe_mode mode;           /* FE_MODE_FP64 or FE_MODE_MIXED (FP32 subspace + FP64 refine) */
   fe_start start;         /* FE_START_RANDOM, FE_START_USER (start_block) or _LEARNED */
   const void* start_block;/* DEVICE row-major n x block FP64, for FE_START_USER */
-  const float* mlp_weights; /* DEVICE packed MLP parameters, for FE_START_LEARNED */
-  int mlp_hidden;         /* hidden width of that MLP (64) */
+  const float* mlp_weights; /* DEVICE packed MLP parameters (fe_mlp_param_count floats,
+                             b = block), for FE_START_LEARNED; features use `seed` */
+  int mlp_hidden;         /* hidden width of that MLP: 32 or 64 (64) */
   double mixed_tol;       /* FP32-phase tolerance in mixed mode (1e-5) */
   int max_sweeps;         /* Jacobi sweeps per Rayleigh-Ritz (60) */
 } fe_eigs_opts;
@@ -227,6 +262,7 @@ typedef struct {
   double max_resid;       /* max explicit ||A x - theta x|| over the returned pairs */
   double seconds;         /* wall time of the call */
   double seconds_fp32;    /* of which in the FP32 phase (mixed mode) */
+  int64_t spmm_start;     /* SpMM calls spent building the start block (learned start: 7) */
 } fe_eigs_stats;
 
 /*

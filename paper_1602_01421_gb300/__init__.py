@@ -203,3 +203,52 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
     if rc != _lib.FE_OK and not (rc == _lib.FE_ERR_NOCONVERGE and not raise_on_noconverge):
         check(rc)
     return evals, (None if evecs_cm is None else evecs_cm.t()), stats
+
+
+# ---------------------------------------------------------------- learned start block
+NFEAT = 8
+
+
+def mlp_param_count(hidden: int, b: int) -> int:
+    c = load().fe_mlp_param_count(int(hidden), int(b))
+    if c < 0:
+        raise ValueError("hidden must be 32 or 64 and b in {1,2,4,8,16}")
+    return int(c)
+
+
+def vertex_features(h: Csr, seed: int = 1):
+    """n x 8 FP32 features from SpMM powers (fe_vertex_features)."""
+    torch = _torch()
+    F = torch.empty((h.n, NFEAT), dtype=torch.float32, device="cuda")
+    _stream()
+    check(load().fe_vertex_features(h.handle, int(seed), _dev(F, "F")))
+    return F
+
+
+def mlp_forward(F, params, hidden: int, b: int):
+    torch = _torch()
+    Z = torch.empty((F.shape[0], b), dtype=torch.float32, device=F.device)
+    _stream()
+    check(load().fe_mlp_forward(_dev(F, "F"), F.shape[0], _dev(params, "params"), hidden, b,
+                                _dev(Z, "Z")))
+    return Z
+
+
+def mlp_loss_grad(F, params, hidden: int, b: int, U, grad=None):
+    """(loss, grad) of the sign-invariant start-block loss (fe_mlp_loss_grad)."""
+    torch = _torch()
+    if grad is None:
+        grad = torch.empty_like(params)
+    loss = ctypes.c_double(0.0)
+    _stream()
+    check(load().fe_mlp_loss_grad(_dev(F, "F"), F.shape[0], _dev(params, "params"), hidden, b,
+                                  _dev(U, "U"), _dev(grad, "grad"), ctypes.byref(loss)))
+    return loss.value, grad
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9,
+             beta2: float = 0.999, eps: float = 1e-8):
+    _stream()
+    check(load().fe_mlp_adam(_dev(params, "params"), _dev(grad, "grad"), _dev(m, "m"),
+                             _dev(v, "v"), params.numel(), lr, beta1, beta2, eps, int(step)))
+    return params

@@ -50,7 +50,7 @@ class EigsStats(ctypes.Structure):
                 ("spmm_blocks", ctypes.c_int64), ("spmm_blocks_fp32", ctypes.c_int64),
                 ("restarts_fp32", ctypes.c_int), ("replacements", ctypes.c_int), ("anorm", ctypes.c_double),
                 ("max_resid", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("seconds_fp32", ctypes.c_double)]
+                ("seconds_fp32", ctypes.c_double), ("spmm_start", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -88,6 +88,13 @@ def load(build_if_missing: bool = True):
             "fe_random_normal": (i32, [vp, i64, i32, i32, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_uint64]),
             "fe_eigs_opts_default": (None, [ctypes.POINTER(EigsOpts)]),
+            "fe_kernel_launches": (ctypes.c_int64, []),
+            "fe_mlp_param_count": (ctypes.c_int64, [i32, i32]),
+            "fe_vertex_features": (i32, [vp, ctypes.c_uint64, vp]),
+            "fe_mlp_forward": (i32, [vp, i64, vp, i32, i32, vp]),
+            "fe_mlp_loss_grad": (i32, [vp, i64, vp, i32, i32, vp, vp, ctypes.POINTER(dbl)]),
+            "fe_mlp_adam": (i32, [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32]),
+            "fe_block_gram_noalloc": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_eigs": (i32, [vp, i32, i32, i32, dbl, i32, vp, vp]),
             "fe_eigs_ex": (i32, [vp, i32, i32, i32, dbl, i32, ctypes.POINTER(EigsOpts), vp, vp,
                                  ctypes.POINTER(EigsStats)]),

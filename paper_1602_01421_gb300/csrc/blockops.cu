@@ -25,8 +25,9 @@ namespace fe {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 // ---------------------------------------------------------------- scratch pools
+constexpr int kScratchSlots = 32;
 struct ScratchPool {
-  DevBuf bufs[16];
+  DevBuf bufs[kScratchSlots];
 };
 static thread_local ScratchPool* t_pool = nullptr;
 static thread_local int t_pool_dev = -1;
@@ -42,6 +43,10 @@ static ScratchPool& pool() {
 }
 
 double* small_scratch(int slot, size_t count) {
+  if (slot < 0 || slot >= kScratchSlots) {
+    set_error(FE_ERR_INVALID, "internal: scratch slot %d out of range", slot);
+    return nullptr;
+  }
   DevBuf& b = pool().bufs[slot];
   if (b.alloc(count * sizeof(double)) != FE_OK) return nullptr;
   return b.as<double>();

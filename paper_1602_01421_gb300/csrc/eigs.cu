@@ -444,6 +444,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
   }
   FE_CUDA(cudaStreamSynchronize(s));
   if (stats) {
+    stats->spmm_start = o.start == FE_START_LEARNED ? 7 : 0;
     stats->restarts = restarts_total;
     stats->replacements = repl_total;
     stats->spmm_blocks_fp32 = spmm32;

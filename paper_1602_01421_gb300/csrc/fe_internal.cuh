@@ -91,6 +91,9 @@ int orth(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_an
 }  // namespace fe
 
 // ---------------------------------------------------------------- the CSR handle
+namespace fe {
+struct SemiExt;
+}
 struct fe_spmm_plan {
   // tail: rows of degree 0..tail_max in 32-row slices grouped by degree (descending)
   int tail_max = 16;
@@ -121,11 +124,45 @@ struct fe_csr_s {
   int64_t device_bytes = 0;
   // semi-external mode
   int semi_external = 0;
-  struct SemiExt* sx = nullptr;
+  fe::SemiExt* sx = nullptr;
   std::vector<void*> allocations;
 };
 
 namespace fe {
+struct Task {
+  int64_t start;  // offset into the plan's colidx
+  int32_t row;    // output row
+  int32_t len;    // non-zeros
+};
+// Host-side SpMM plan of a row range (built at create; uploaded or packed into panels).
+struct HostPlan {
+  int64_t max_degree = 0, rows_empty = 0, rows_tail = 0, rows_mid = 0, rows_hub = 0;
+  int nbuckets = 0;
+  int32_t deg_of_bucket[34], deg_slice_begin[34];
+  int64_t deg_ell_base[34];
+  int64_t nslices = 0, ell_total = 0, ntasks = 0, nhub_tasks = 0, nhub = 0;
+  std::vector<int32_t> slice_rows, ell, hub_rows, hub_task_begin;
+  std::vector<Task> tasks;
+};
+// Device pointers of a plan (the resident handle's, or one streamed panel's).
+struct PlanView {
+  const int32_t* colidx;
+  const void* tasks;
+  int64_t ntasks, nhub_tasks;
+  const int32_t* slice_rows;
+  const int32_t* ell;
+  int64_t nslices;
+  int nbuckets;
+  int32_t deg_of_bucket[34], deg_slice_begin[34];
+  int64_t deg_ell_base[34];
+  const int32_t* hub_rows;
+  const int32_t* hub_task_begin;
+  int64_t nhub;
+};
+int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
+                    int tail_max, int hub_min, int hub_chunk, HostPlan& hp);
+int spmm_view(const PlanView& v, const void* X, void* Y, void* partial, int b, fe_dtype dt,
+              cudaStream_t s);
 int spmm_resident(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s);
 int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx, int tail_max,
                     int hub_min, int hub_chunk);

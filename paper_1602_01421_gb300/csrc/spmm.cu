@@ -26,11 +26,6 @@
 
 namespace fe {
 
-struct Task {
-  int64_t start;  // offset into colidx
-  int32_t row;    // output row
-  int32_t len;    // non-zeros
-};
 static_assert(sizeof(Task) == 16, "Task must be 16 bytes");
 
 // Per (type, b) geometry: a lane moves NE elements (<= 16 bytes) per load; an X row of
@@ -180,64 +175,93 @@ __global__ void hub_reduce_kernel(const int32_t* __restrict__ hub_rows,
 }
 
 template <typename T, int B>
-static int launch_spmm(fe_csr h, const T* X, T* Y, cudaStream_t s) {
-  const fe_spmm_plan& pl = h->plan;
+static int launch_spmm(const PlanView& pv, const T* X, T* Y, T* partial, cudaStream_t s) {
   SpmmParams p;
   memset(&p, 0, sizeof(p));
-  p.colidx = h->d_colidx;
-  p.tasks = reinterpret_cast<const Task*>(pl.d_tasks);
-  p.ntasks = pl.ntasks;
-  p.nhub_tasks = pl.nhub_tasks;
-  p.task_ctas = ceil_div(pl.ntasks, kWarpsPerCta);
-  p.slice_rows = pl.d_slice_rows;
-  p.ell = pl.d_ell;
-  p.nslices = pl.nslices;
-  p.nbuckets = pl.nbuckets;
-  for (int i = 0; i < pl.nbuckets; ++i) {
-    p.bucket_deg[i] = pl.deg_of_bucket[i];
-    p.bucket_slice_begin[i] = pl.deg_slice_begin[i];
-    p.bucket_ell_base[i] = pl.deg_ell_base[i];
+  p.colidx = pv.colidx;
+  p.tasks = reinterpret_cast<const Task*>(pv.tasks);
+  p.ntasks = pv.ntasks;
+  p.nhub_tasks = pv.nhub_tasks;
+  p.slice_rows = pv.slice_rows;
+  p.ell = pv.ell;
+  p.nslices = pv.nslices;
+  p.nbuckets = pv.nbuckets;
+  for (int i = 0; i < pv.nbuckets; ++i) {
+    p.bucket_deg[i] = pv.deg_of_bucket[i];
+    p.bucket_slice_begin[i] = pv.deg_slice_begin[i];
+    p.bucket_ell_base[i] = pv.deg_ell_base[i];
   }
-  p.bucket_slice_begin[pl.nbuckets] = (int32_t)pl.nslices;
-  const int64_t ctas = p.task_ctas + ceil_div(pl.nslices, kWarpsPerCta);
+  p.bucket_slice_begin[pv.nbuckets] = (int32_t)pv.nslices;
+  p.task_ctas = ceil_div(pv.ntasks, kWarpsPerCta);
+  const int64_t ctas = p.task_ctas + ceil_div(pv.nslices, kWarpsPerCta);
   if (ctas > 0) {
-    spmm_main_kernel<T, B><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, h->partials.as<T>());
+    spmm_main_kernel<T, B><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
     count_launch();
     FE_CUDA(cudaGetLastError());
   }
-  if (pl.nhub > 0) {
-    const int64_t th = pl.nhub * B;
+  if (pv.nhub > 0) {
+    const int64_t th = pv.nhub * B;
     hub_reduce_kernel<T, B><<<(unsigned)ceil_div(th, 256), 256, 0, s>>>(
-        pl.d_hub_rows, pl.d_hub_task_begin, pl.nhub, h->partials.as<T>(), Y);
+        pv.hub_rows, pv.hub_task_begin, pv.nhub, partial, Y);
     count_launch();
     FE_CUDA(cudaGetLastError());
   }
   return FE_OK;
 }
 
-int spmm_resident(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s) {
+PlanView resident_view(fe_csr h) {
+  const fe_spmm_plan& pl = h->plan;
+  PlanView v;
+  memset(&v, 0, sizeof(v));
+  v.colidx = h->d_colidx;
+  v.tasks = pl.d_tasks;
+  v.ntasks = pl.ntasks;
+  v.nhub_tasks = pl.nhub_tasks;
+  v.slice_rows = pl.d_slice_rows;
+  v.ell = pl.d_ell;
+  v.nslices = pl.nslices;
+  v.nbuckets = pl.nbuckets;
+  for (int i = 0; i < pl.nbuckets; ++i) {
+    v.deg_of_bucket[i] = pl.deg_of_bucket[i];
+    v.deg_slice_begin[i] = pl.deg_slice_begin[i];
+    v.deg_ell_base[i] = pl.deg_ell_base[i];
+  }
+  v.hub_rows = pl.d_hub_rows;
+  v.hub_task_begin = pl.d_hub_task_begin;
+  v.nhub = pl.nhub;
+  return v;
+}
+
+int spmm_view(const PlanView& v, const void* X, void* Y, void* partial, int b, fe_dtype dt,
+              cudaStream_t s) {
   if (dt == FE_F32) {
     const float* x = static_cast<const float*>(X);
     float* y = static_cast<float*>(Y);
+    float* pa = static_cast<float*>(partial);
     switch (b) {
-      case 1: return launch_spmm<float, 1>(h, x, y, s);
-      case 2: return launch_spmm<float, 2>(h, x, y, s);
-      case 4: return launch_spmm<float, 4>(h, x, y, s);
-      case 8: return launch_spmm<float, 8>(h, x, y, s);
-      case 16: return launch_spmm<float, 16>(h, x, y, s);
+      case 1: return launch_spmm<float, 1>(v, x, y, pa, s);
+      case 2: return launch_spmm<float, 2>(v, x, y, pa, s);
+      case 4: return launch_spmm<float, 4>(v, x, y, pa, s);
+      case 8: return launch_spmm<float, 8>(v, x, y, pa, s);
+      case 16: return launch_spmm<float, 16>(v, x, y, pa, s);
     }
   } else {
     const double* x = static_cast<const double*>(X);
     double* y = static_cast<double*>(Y);
+    double* pa = static_cast<double*>(partial);
     switch (b) {
-      case 1: return launch_spmm<double, 1>(h, x, y, s);
-      case 2: return launch_spmm<double, 2>(h, x, y, s);
-      case 4: return launch_spmm<double, 4>(h, x, y, s);
-      case 8: return launch_spmm<double, 8>(h, x, y, s);
-      case 16: return launch_spmm<double, 16>(h, x, y, s);
+      case 1: return launch_spmm<double, 1>(v, x, y, pa, s);
+      case 2: return launch_spmm<double, 2>(v, x, y, pa, s);
+      case 4: return launch_spmm<double, 4>(v, x, y, pa, s);
+      case 8: return launch_spmm<double, 8>(v, x, y, pa, s);
+      case 16: return launch_spmm<double, 16>(v, x, y, pa, s);
     }
   }
   return set_error(FE_ERR_INVALID, "spmm: unsupported b = %d", b);
+}
+
+int spmm_resident(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s) {
+  return spmm_view(resident_view(h), X, Y, h->partials.p, b, dt, s);
 }
 
 // ---------------------------------------------------------------- plan (host, at create)
@@ -257,108 +281,131 @@ static int dev_upload(fe_csr h, void** dst, const void* src, size_t bytes) {
   return FE_OK;
 }
 
-int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx, int tail_max,
-                    int hub_min, int hub_chunk) {
-  const int64_t n = h->n;
-  fe_spmm_plan& pl = h->plan;
-  pl.tail_max = tail_max;
-  pl.hub_min = hub_min;
-  pl.hub_chunk = hub_chunk;
-  int64_t maxdeg = 0;
+// Plan of rows [r0, r1): task starts are offsets from rowptr[r0]; row ids are global.
+int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
+                    int tail_max, int hub_min, int hub_chunk, HostPlan& hp) {
+  hp = HostPlan();
+  const int64_t base = rowptr[r0];
   std::vector<int64_t> tail_cnt(tail_max + 1, 0);
   std::vector<int64_t> mid_cnt(hub_min + 1, 0);
   int64_t nhub = 0, nhub_tasks = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t d = rowptr[i + 1] - rowptr[i];
-    maxdeg = std::max(maxdeg, d);
+  for (int64_t i = r0; i < r1; ++i) {
+    const int64_t d = rowptr[i + 1] - rowptr[i];
+    hp.max_degree = std::max(hp.max_degree, d);
     if (d <= tail_max) tail_cnt[d]++;
     else if (d <= hub_min) mid_cnt[d]++;
     else { nhub++; nhub_tasks += ceil_div(d, hub_chunk); }
   }
-  h->max_degree = maxdeg;
-  h->rows_empty = tail_cnt[0];
-  h->rows_tail = 0;
-  for (int d = 1; d <= tail_max; ++d) h->rows_tail += tail_cnt[d];
-  h->rows_mid = 0;
-  for (int d = tail_max + 1; d <= hub_min; ++d) h->rows_mid += mid_cnt[d];
-  h->rows_hub = nhub;
+  hp.rows_empty = tail_cnt[0];
+  for (int d = 1; d <= tail_max; ++d) hp.rows_tail += tail_cnt[d];
+  for (int d = tail_max + 1; d <= hub_min; ++d) hp.rows_mid += mid_cnt[d];
+  hp.rows_hub = nhub;
   FE_ARG(nhub_tasks < INT32_MAX, "spmm plan: too many hub tasks");
-
-  // ---- tail slices: buckets by degree, descending, empty bucket dropped
-  pl.nbuckets = 0;
+  // tail slices: buckets by degree, descending, empty buckets dropped
   int64_t nslices = 0, ell_total = 0;
   std::vector<int> bucket_of_deg(tail_max + 1, -1);
   for (int d = tail_max; d >= 0; --d) {
     if (tail_cnt[d] == 0) continue;
-    int bk = pl.nbuckets++;
+    const int bk = hp.nbuckets++;
     bucket_of_deg[d] = bk;
-    pl.deg_of_bucket[bk] = d;
-    pl.deg_slice_begin[bk] = (int32_t)nslices;
-    pl.deg_ell_base[bk] = ell_total;
-    int64_t sl = ceil_div(tail_cnt[d], 32);
+    hp.deg_of_bucket[bk] = d;
+    hp.deg_slice_begin[bk] = (int32_t)nslices;
+    hp.deg_ell_base[bk] = ell_total;
+    const int64_t sl = ceil_div(tail_cnt[d], 32);
     nslices += sl;
     ell_total += sl * 32 * d;
   }
   FE_ARG(nslices < INT32_MAX, "spmm plan: too many tail slices");
-  pl.nslices = nslices;
-  std::vector<int32_t> slice_rows(nslices * 32, -1);
+  hp.nslices = nslices;
+  hp.slice_rows.assign(nslices * 32, -1);
   std::vector<int64_t> cursor(tail_max + 1, 0);
   for (int d = 0; d <= tail_max; ++d)
-    if (bucket_of_deg[d] >= 0) cursor[d] = (int64_t)pl.deg_slice_begin[bucket_of_deg[d]] * 32;
-  // ---- tasks: hub chunks first, then mid rows by degree descending (stable in row order)
+    if (bucket_of_deg[d] >= 0) cursor[d] = (int64_t)hp.deg_slice_begin[bucket_of_deg[d]] * 32;
+  // tasks: hub chunks first, then mid rows by degree descending (stable in row order)
   std::vector<int64_t> mid_pos(hub_min + 2, 0);
   {
     int64_t acc = nhub_tasks;
     for (int d = hub_min; d > tail_max; --d) { mid_pos[d] = acc; acc += mid_cnt[d]; }
   }
-  const int64_t ntasks = nhub_tasks + h->rows_mid;
-  std::vector<Task> tasks(ntasks);
-  std::vector<int32_t> hub_rows(nhub), hub_begin(nhub + 1);
+  hp.ntasks = nhub_tasks + hp.rows_mid;
+  hp.nhub_tasks = nhub_tasks;
+  hp.nhub = nhub;
+  hp.tasks.resize(hp.ntasks);
+  hp.hub_rows.resize(nhub);
+  hp.hub_task_begin.resize(nhub + 1);
   int64_t ht = 0, hi = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t d = rowptr[i + 1] - rowptr[i];
+  for (int64_t i = r0; i < r1; ++i) {
+    const int64_t d = rowptr[i + 1] - rowptr[i];
     if (d <= tail_max) {
-      slice_rows[cursor[d]++] = (int32_t)i;
+      hp.slice_rows[cursor[d]++] = (int32_t)i;
     } else if (d <= hub_min) {
-      tasks[mid_pos[d]++] = Task{rowptr[i], (int32_t)i, (int32_t)d};
+      hp.tasks[mid_pos[d]++] = Task{rowptr[i] - base, (int32_t)i, (int32_t)d};
     } else {
-      hub_rows[hi] = (int32_t)i;
-      hub_begin[hi] = (int32_t)ht;
+      hp.hub_rows[hi] = (int32_t)i;
+      hp.hub_task_begin[hi] = (int32_t)ht;
       for (int64_t c = 0; c < d; c += hub_chunk)
-        tasks[ht++] = Task{rowptr[i] + c, (int32_t)i, (int32_t)std::min<int64_t>(hub_chunk, d - c)};
+        hp.tasks[ht++] = Task{rowptr[i] - base + c, (int32_t)i, (int32_t)std::min<int64_t>(hub_chunk, d - c)};
       ++hi;
     }
   }
-  hub_begin[nhub] = (int32_t)ht;
-  pl.ntasks = ntasks;
-  pl.nhub_tasks = nhub_tasks;
-  pl.nhub = nhub;
-  // ---- ELL fill (transposed per slice; padding lanes read column 0 and are not written)
-  std::vector<int32_t> ell(ell_total > 0 ? ell_total : 1, 0);
-  for (int bk = 0; bk < pl.nbuckets; ++bk) {
-    const int d = pl.deg_of_bucket[bk];
+  hp.hub_task_begin[nhub] = (int32_t)ht;
+  // ELL fill (transposed per slice; padding lanes read column 0 and are not written)
+  hp.ell.assign(ell_total > 0 ? ell_total : 1, 0);
+  for (int bk = 0; bk < hp.nbuckets; ++bk) {
+    const int d = hp.deg_of_bucket[bk];
     if (d == 0) continue;
-    const int64_t s0 = pl.deg_slice_begin[bk];
-    const int64_t s1 = (bk + 1 < pl.nbuckets) ? pl.deg_slice_begin[bk + 1] : nslices;
+    const int64_t s0 = hp.deg_slice_begin[bk];
+    const int64_t s1 = (bk + 1 < hp.nbuckets) ? hp.deg_slice_begin[bk + 1] : nslices;
+    int32_t* ell = hp.ell.data();
+    const int32_t* srows = hp.slice_rows.data();
+    const int64_t ebase = hp.deg_ell_base[bk];
     #pragma omp parallel for schedule(static)
-    for (int64_t s = s0; s < s1; ++s) {
-      int32_t* e = ell.data() + pl.deg_ell_base[bk] + (s - s0) * 32 * d;
+    for (int64_t sl = s0; sl < s1; ++sl) {
+      int32_t* e = ell + ebase + (sl - s0) * 32 * d;
       for (int lane = 0; lane < 32; ++lane) {
-        int32_t r = slice_rows[s * 32 + lane];
+        const int32_t r = srows[sl * 32 + lane];
         for (int t = 0; t < d; ++t) e[t * 32 + lane] = r >= 0 ? colidx[rowptr[r] + t] : 0;
       }
     }
   }
-  // ---- upload
+  hp.ell_total = ell_total;
+  return FE_OK;
+}
+
+int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx_raw, int tail_max,
+                    int hub_min, int hub_chunk) {
+  const int64_t n = h->n;
+  const int32_t* colidx = colidx_raw;
+  fe_spmm_plan& pl = h->plan;
+  pl.tail_max = tail_max;
+  pl.hub_min = hub_min;
+  pl.hub_chunk = hub_chunk;
+  HostPlan hp;
+  FE_TRY(build_host_plan(rowptr, colidx, 0, n, tail_max, hub_min, hub_chunk, hp));
+  h->max_degree = hp.max_degree;
+  h->rows_empty = hp.rows_empty;
+  h->rows_tail = hp.rows_tail;
+  h->rows_mid = hp.rows_mid;
+  h->rows_hub = hp.rows_hub;
+  pl.nbuckets = hp.nbuckets;
+  for (int i = 0; i < hp.nbuckets; ++i) {
+    pl.deg_of_bucket[i] = hp.deg_of_bucket[i];
+    pl.deg_slice_begin[i] = hp.deg_slice_begin[i];
+    pl.deg_ell_base[i] = hp.deg_ell_base[i];
+  }
+  pl.nslices = hp.nslices;
+  pl.ntasks = hp.ntasks;
+  pl.nhub_tasks = hp.nhub_tasks;
+  pl.nhub = hp.nhub;
   FE_TRY(dev_upload(h, (void**)&h->d_rowptr, rowptr, sizeof(int64_t) * (n + 1)));
   FE_TRY(dev_upload(h, (void**)&h->d_colidx, colidx, sizeof(int32_t) * h->nnz));
-  FE_TRY(dev_upload(h, (void**)&pl.d_slice_rows, slice_rows.data(), sizeof(int32_t) * slice_rows.size()));
-  FE_TRY(dev_upload(h, (void**)&pl.d_ell, ell.data(), sizeof(int32_t) * ell_total));
-  FE_TRY(dev_upload(h, &pl.d_tasks, tasks.data(), sizeof(Task) * ntasks));
-  FE_TRY(dev_upload(h, (void**)&pl.d_hub_rows, hub_rows.data(), sizeof(int32_t) * nhub));
-  FE_TRY(dev_upload(h, (void**)&pl.d_hub_task_begin, hub_begin.data(), sizeof(int32_t) * (nhub + 1)));
-  if (nhub_tasks > 0) {
-    FE_TRY(h->partials.alloc(sizeof(double) * 16 * nhub_tasks));
+  FE_TRY(dev_upload(h, (void**)&pl.d_slice_rows, hp.slice_rows.data(), sizeof(int32_t) * hp.slice_rows.size()));
+  FE_TRY(dev_upload(h, (void**)&pl.d_ell, hp.ell.data(), sizeof(int32_t) * hp.ell_total));
+  FE_TRY(dev_upload(h, &pl.d_tasks, hp.tasks.data(), sizeof(Task) * hp.ntasks));
+  FE_TRY(dev_upload(h, (void**)&pl.d_hub_rows, hp.hub_rows.data(), sizeof(int32_t) * hp.nhub));
+  FE_TRY(dev_upload(h, (void**)&pl.d_hub_task_begin, hp.hub_task_begin.data(), sizeof(int32_t) * (hp.nhub + 1)));
+  if (hp.nhub_tasks > 0) {
+    FE_TRY(h->partials.alloc(sizeof(double) * 16 * hp.nhub_tasks));
     h->device_bytes += (int64_t)h->partials.bytes;
   }
   return FE_OK;

@@ -71,4 +71,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.CsrOpts) == 48
     assert ctypes.sizeof(_lib.CsrInfo) == 88
     assert ctypes.sizeof(_lib.EigsOpts) == 64
-    assert ctypes.sizeof(_lib.EigsStats) == 64
+    assert ctypes.sizeof(_lib.EigsStats) == 72
