@@ -192,6 +192,15 @@ def run_ours(args):
     t_create = time.perf_counter() - t0
     info = h.info()
 
+    if args.only == "gram1":
+        # one Gram launch at the FP64 solve's mean shape (7 blocks of n x 4 against n x 4)
+        Vg = fe.random_normal(7 * n, 4, dtype=torch.float64, seed=5).view(7, n, 4)
+        Wg = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+        for _ in range(args.warmup + args.steps):
+            fe.block_gram(Vg, Wg)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "gram1", "n": n, "nv": 7, "b": 4}))
+        return
     if args.only == "spmm1":
         # one SpMM launch (for a single-kernel profiler capture)
         tdt = torch.float32 if args.prec == "f32" else torch.float64
@@ -396,6 +405,92 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_config(args):
+    """The other measurement configurations (one results line each, not the step metric)."""
+    import numpy as np
+    import torch
+    import graphgen
+    import paper_1602_01421_gb300 as fe
+    from oracle import core
+    torch.cuda.set_device(0)
+    out = {"config": args.config}
+    if args.config in ("mixed24", "learned24"):
+        t0 = time.perf_counter()
+        g = graphgen.rmat(24, seed=1 if args.config == "mixed24" else 24)
+        out.update(n=g.n, nnz=g.nnz, gen_s=round(time.perf_counter() - t0, 1))
+        h = fe.Csr.from_graph(g)
+
+        def timed(**kw):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ev, X, st = fe.eigs(h, **kw)
+            torch.cuda.synchronize()
+            return ev, X, st, time.perf_counter() - t
+
+        def cpu_resid(ev, X):
+            """explicit residuals with the CPU oracle's SpMM (FP64) on the returned vectors"""
+            Xh = X.cpu().numpy()
+            R = core.spmm(g.rowptr, g.colidx, Xh) - Xh * ev
+            return (np.linalg.norm(R, axis=0) / np.abs(ev)).max()
+
+        if args.config == "mixed24":
+            b, nb = 8, 8
+            ev64, X64, st64, t64 = timed(nev=8, block=b, nblocks=nb, tol=1e-8, which="LM", seed=1)
+            evm, Xm, stm, tm = timed(nev=8, block=b, nblocks=nb, tol=1e-8, which="LM", seed=1, mode="mixed")
+            out.update(workload="rmat24-ef16 nev8 b8 m64 tol1e-8",
+                       fp64={"s": t64, "restarts": st64["restarts"], "spmm_blocks": st64["spmm_blocks"],
+                             "max_rel_resid_cpu": cpu_resid(ev64, X64)},
+                       mixed={"s": tm, "restarts": stm["restarts"], "restarts_fp32": stm["restarts_fp32"],
+                              "spmm_blocks": stm["spmm_blocks"], "spmm_blocks_fp32": stm["spmm_blocks_fp32"],
+                              "s_fp32": stm["seconds_fp32"], "max_rel_resid_cpu": cpu_resid(evm, Xm),
+                              "max_rel_eval_diff_vs_fp64": float(np.max(np.abs(evm - ev64) / np.abs(ev64)))},
+                       speedup=t64 / tm, evals=[float(x) for x in ev64])
+        else:
+            from paper_1602_01421_gb300 import learned as L
+            ex = [L.make_example(graphgen.rmat(sc, seed=100 + i), BLOCK, offset=args.learned_offset)
+                  for i, sc in enumerate([16, 17, 18, 19, 20] * args.learned_graphs)]
+            params, losses = L.train(ex, hidden=64, b=BLOCK, steps=args.learned_steps, lr=3e-3)
+            res = []
+            for sd in (1, 2, 3):
+                ev, X, st, t = timed(nev=8, block=BLOCK, nblocks=NBLOCKS, tol=1e-8, which="LM", seed=sd,
+                                     mode="mixed", return_vectors=False)
+                res.append({"seed": sd, "s": t, "spmm_blocks": st["spmm_blocks"]})
+            ev, X, st, t = timed(nev=8, block=BLOCK, nblocks=NBLOCKS, tol=1e-8, which="LM", seed=1,
+                                 mode="mixed", mlp_weights=params, mlp_hidden=64)
+            out.update(workload="rmat24-ef16 (fresh seed) nev8 b4 m32 tol1e-8 mixed",
+                       train={"graphs": len(ex), "scales": "16-20", "steps": args.learned_steps,
+                              "final_loss": float(np.mean(losses[-50:]))},
+                       random=res, learned={"s": t, "spmm_blocks": st["spmm_blocks"],
+                                            "spmm_start_calls": st["spmm_start"],
+                                            "max_rel_resid_cpu": cpu_resid(ev, X)})
+        h.close()
+    elif args.config == "semiext27":
+        t0 = time.perf_counter()
+        g = graphgen.rmat(27, seed=1)
+        out.update(n=g.n, nnz=g.nnz, gen_s=round(time.perf_counter() - t0, 1))
+        cap = 6 << 30
+        t0 = time.perf_counter()
+        h = fe.Csr.from_graph(g, device_mem_cap_bytes=cap)
+        info = h.info()
+        out.update(create_s=round(time.perf_counter() - t0, 1), cap_bytes=cap, panels=info["panels"],
+                   device_bytes=info["device_bytes"])
+        for prec, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+            X = fe.random_normal(g.n, 4, dtype=tdt, seed=3)
+            Y = torch.empty_like(X)
+            fe.spmm(h, X, Y)
+            tt = statistics.median(time_cuda(lambda: fe.spmm(h, X, Y), 3, torch))
+            rows = np.random.default_rng(0).integers(0, g.n, 20000)
+            ref = core.spmm_rows(g.rowptr, g.colidx, X.cpu().numpy(), rows)
+            err = float(np.max(np.abs(Y.cpu().numpy()[rows] - ref) /
+                               (core.spmm_rows(g.rowptr, g.colidx, np.abs(X.cpu().numpy()), rows) + 1e-300)))
+            out[f"spmm_{prec}_b4"] = {"ms": round(tt, 2), "GBps": round(spmm_bytes(g.n, g.nnz, 4, es) / tt / 1e6, 1),
+                                      "h2d_GBps": round(4 * g.nnz / tt / 1e6, 1),
+                                      "max_rel_err_sampled_rows": err}
+            del X, Y
+        h.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,14 +511,20 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=1)
     ap.add_argument("--ref-solve-blocks", type=int, default=150)
     ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
-    ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1"],
+    ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1"],
                     help="solve: warm-up + timed solves only; spmm1: SpMM launches only")
     ap.add_argument("--b", type=int, default=4)
+    ap.add_argument("--config", default="rmat22", choices=["rmat22", "mixed24", "learned24", "semiext27"],
+                    help="rmat22: the step metric (default); others print their own results line")
+    ap.add_argument("--learned-graphs", type=int, default=2)
+    ap.add_argument("--learned-steps", type=int, default=800)
     ap.add_argument("--prec", default="f64", choices=["f32", "f64"])
     args = ap.parse_args()
     os.makedirs(args.outdir, exist_ok=True)
     if args.impl == "reference":
         run_reference(args)
+    elif args.config != "rmat22":
+        run_config(args)
     else:
         run_ours(args)
 
