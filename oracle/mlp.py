@@ -20,6 +20,8 @@ Parameters are packed as [W1 (8 x H), b1 (H), W2 (H x H), b2 (H), W3 (H x b), b3
 
 Loss against reference Ritz vectors U (n x b, unit columns), invariant to each column's sign:
   L = sum_j (1 - (z_j . u_j)^2 / |z_j|^2)
+Subspace form, against an orthonormal target basis U (n x t), invariant to any rotation of U:
+  L = sum_j (1 - |U^T z_j|^2 / |z_j|^2)    (the part of each output column outside span(U))
 """
 from __future__ import annotations
 
@@ -126,6 +128,39 @@ def loss_and_grad(F, p, hidden, b, U):
     db1 = dh1.sum(axis=0)
     g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
     return L, g
+
+
+def subspace_loss(F, p, hidden, b, U) -> float:
+    Z, _ = forward(F, p, hidden, b)
+    S = U.T @ Z
+    return float(np.sum(1.0 - np.sum(S * S, axis=0) / np.sum(Z * Z, axis=0)))
+
+
+def subspace_loss_and_grad(F, p, hidden, b, U):
+    """Subspace form of the loss and dL/dp; dL/dz_j = -2 U s_j / q_j + 2 |s_j|^2 / q_j^2 z_j
+    with s_j = U^T z_j, q_j = |z_j|^2."""
+    W1, b1, W2, b2, W3, b3 = unpack(p, hidden, b)
+    Z, (a1, h1, a2, h2) = forward(F, p, hidden, b)
+    S = U.T @ Z
+    q = np.sum(Z * Z, axis=0)
+    P = np.sum(S * S, axis=0)
+    L = float(np.sum(1.0 - P / q))
+    dZ = U @ (-2.0 * S / q) + (2.0 * P / (q * q)) * Z
+    return L, _backprop(F, p, hidden, b, dZ, (a1, h1, a2, h2))
+
+
+def _backprop(F, p, hidden, b, dZ, acts):
+    W1, b1, W2, b2, W3, b3 = unpack(p, hidden, b)
+    a1, h1, a2, h2 = acts
+    dW3 = h2.T @ dZ
+    db3 = dZ.sum(axis=0)
+    dh2 = (dZ @ W3.T) * (a2 > 0)
+    dW2 = h1.T @ dh2
+    db2 = dh2.sum(axis=0)
+    dh1 = (dh2 @ W2.T) * (a1 > 0)
+    dW1 = F.T @ dh1
+    db1 = dh1.sum(axis=0)
+    return np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
 
 
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

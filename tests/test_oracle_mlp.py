@@ -88,3 +88,22 @@ def test_training_reduces_loss_on_cpu():
         L, gr = mlp.loss_and_grad(F, p, H, b, U)
         p, m, v = mlp.adam_step(p, gr, m, v, t, lr=1e-2)
     assert mlp.loss(F, p, H, b, U) < L0
+
+
+def test_subspace_gradient_matches_central_differences_and_is_rotation_invariant():
+    H, b, t = 16, 4, 6
+    g, F, _, p = _setup(H, b)
+    U, _ = np.linalg.qr(np.random.default_rng(9).standard_normal((g.n, t)))
+    L, grad = mlp.subspace_loss_and_grad(F, p, H, b, U)
+    assert abs(L - mlp.subspace_loss(F, p, H, b, U)) < 1e-12
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((t, t)))
+    assert abs(mlp.subspace_loss(F, p, H, b, U @ Q) - L) < 1e-10      # any basis of span(U)
+    h = 1e-6
+    for i in np.random.default_rng(4).choice(p.size, 50, replace=False):
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.subspace_loss(F, p + e, H, b, U) - mlp.subspace_loss(F, p - e, H, b, U)) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(grad[i])) + 1e-7, (i, fd, grad[i])
+    # with t = b and U's columns paired to Z's, the subspace loss is at most the column loss
+    U4 = U[:, :b]
+    assert mlp.subspace_loss(F, p, H, b, U4) <= mlp.loss(F, p, H, b, U4) + 1e-12
