@@ -94,6 +94,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_aggregate(ms_local, steps, dist=None, device="cpu"):
+    """Replicas: every rank runs `steps` solves; the job time is the slowest rank's, and the
+    whole-job throughput counts all ranks' solves.  Returns (value, max_ms, world_size)."""
+    ws = 1
+    ms = float(ms_local)
+    if dist is not None and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ws * steps / (ms / 1000.0), ms, ws
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -248,13 +262,8 @@ def run_ours(args):
     barrier()
     launches = lib.fe_kernel_launches() - l0
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    value, ms, _ = replica_aggregate(e0.elapsed_time(e1), args.steps, dist, device="cuda")
     ms_per_step = ms / args.steps
-    value = ws * args.steps / (ms / 1000.0)
     blocks = stats[-1]["spmm_blocks"]
 
     # ---- SpMM sweep (compulsory-byte GB/s), b in {1,2,4,8,16} x {f32, f64}
