@@ -515,8 +515,10 @@ def main():
     ap.add_argument("--no-semi", action="store_true")
     ap.add_argument("--learned-offset", type=int, default=0,
                     help="first Ritz vector (largest-magnitude order) the MLP is trained to predict")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu dram bytes per launch of the roofline kernel, if captured")
+    # dram__bytes_read.sum + dram__bytes_write.sum of gram_kernel<double,4,4> at the roofline
+    # shape, one ncu capture (profiles/gram_f64_rmat22.md); update when that kernel changes
+    ap.add_argument("--traffic", type=float, default=1.073789e9 + 3.321856e6,
+                    help="ncu DRAM bytes per launch of the roofline kernel")
     ap.add_argument("--ref-cycles", type=int, default=1)
     ap.add_argument("--ref-solve-blocks", type=int, default=150)
     ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
