@@ -22,6 +22,9 @@ Loss against reference Ritz vectors U (n x b, unit columns), invariant to each c
   L = sum_j (1 - (z_j . u_j)^2 / |z_j|^2)
 Subspace form, against an orthonormal target basis U (n x t), invariant to any rotation of U:
   L = sum_j (1 - |U^T z_j|^2 / |z_j|^2)    (the part of each output column outside span(U))
+Span form (b <= t), invariant to rotations of U and to any invertible mixing of Z's columns:
+  L = b - tr((Z^T Z)^{-1} Z^T U U^T Z)     (b minus the squared cosines of the principal angles
+  between span(Z) and span(U)); b copies of one good direction score no better than one.
 """
 from __future__ import annotations
 
@@ -147,6 +150,26 @@ def subspace_loss_and_grad(F, p, hidden, b, U):
     L = float(np.sum(1.0 - P / q))
     dZ = U @ (-2.0 * S / q) + (2.0 * P / (q * q)) * Z
     return L, _backprop(F, p, hidden, b, dZ, (a1, h1, a2, h2))
+
+
+def span_loss(F, p, hidden, b, U) -> float:
+    Z, _ = forward(F, p, hidden, b)
+    S = U.T @ Z
+    M = Z.T @ Z
+    return float(b - np.trace(np.linalg.solve(M, S.T @ S)))
+
+
+def span_loss_and_grad(F, p, hidden, b, U):
+    """Span form and dL/dp.  With S = U^T Z, M = Z^T Z, N = S^T S:
+    dL/dZ = -2 U S M^{-1} + 2 Z M^{-1} N M^{-1}."""
+    Z, acts = forward(F, p, hidden, b)
+    S = U.T @ Z
+    M = Z.T @ Z
+    N = S.T @ S
+    Mi = np.linalg.inv(M)
+    L = float(b - np.trace(Mi @ N))
+    dZ = -2.0 * U @ (S @ Mi) + 2.0 * Z @ (Mi @ N @ Mi)
+    return L, _backprop(F, p, hidden, b, dZ, acts)
 
 
 def _backprop(F, p, hidden, b, dZ, acts):

@@ -107,3 +107,26 @@ def test_subspace_gradient_matches_central_differences_and_is_rotation_invariant
     # with t = b and U's columns paired to Z's, the subspace loss is at most the column loss
     U4 = U[:, :b]
     assert mlp.subspace_loss(F, p, H, b, U4) <= mlp.loss(F, p, H, b, U4) + 1e-12
+
+
+def test_span_loss_gradient_invariances_and_collapse():
+    H, b, t = 16, 4, 8
+    g, F, _, p = _setup(H, b)
+    U, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((g.n, t)))
+    L, grad = mlp.span_loss_and_grad(F, p, H, b, U)
+    assert abs(L - mlp.span_loss(F, p, H, b, U)) < 1e-12 and 0.0 <= L <= b
+    Q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((t, t)))
+    assert abs(mlp.span_loss(F, p, H, b, U @ Q) - L) < 1e-9            # basis of span(U)
+    # mixing the outputs (W3, b3 -> W3 T, b3 T) leaves span(Z), hence L, unchanged
+    T = np.random.default_rng(4).standard_normal((b, b)) + 3 * np.eye(b)
+    q = p.copy()
+    o = mlp.NFEAT * H + H + H * H + H
+    q[o:o + H * b] = (p[o:o + H * b].reshape(H, b) @ T).ravel()
+    q[o + H * b:] = p[o + H * b:] @ T
+    assert abs(mlp.span_loss(F, q, H, b, U) - L) < 1e-8
+    h = 1e-6
+    for i in np.random.default_rng(5).choice(p.size, 50, replace=False):
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.span_loss(F, p + e, H, b, U) - mlp.span_loss(F, p - e, H, b, U)) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-5 * max(1.0, abs(grad[i])) + 1e-7, (i, fd, grad[i])
