@@ -232,11 +232,11 @@ def run_ours(args):
         return fe.eigs(h, NEV, BLOCK, NBLOCKS, TOL, "LM", mode=mode, seed=1)
 
     for _ in range(args.warmup):
-        ev, X, st = solve()
+        ev, X, st = solve(args.solve_mode if args.only == "solve" else "fp64")
         assert st["converged"], "warm-up solve did not converge"
     if args.only == "solve":
         for _ in range(args.steps):
-            ev, X, st = solve()
+            ev, X, st = solve(args.solve_mode)
         torch.cuda.synchronize()
         print(json.dumps({"only": "solve", "n": n, "nnz": nnz, "restarts": st["restarts"],
                           "spmm_blocks": st["spmm_blocks"], "evals": [float(x) for x in ev]}))
@@ -332,9 +332,10 @@ def run_ours(args):
         try:
             from paper_1602_01421_gb300 import learned as L
             t0 = time.perf_counter()
-            ex = [L.make_example(graphgen.rmat(sc, seed=100 + i), BLOCK, offset=args.learned_offset)
-                  for i, sc in enumerate([12, 13, 14, 15, 16] * 2)]
-            params, losses = L.train(ex, hidden=64, b=BLOCK, steps=600, lr=3e-3)
+            # span loss against the nev wanted Ritz vectors of each training graph
+            ex = [L.make_subspace_example(graphgen.rmat(sc, seed=100 + i))
+                  for i, sc in enumerate([12, 13, 14, 15, 16, 17] * 3)]
+            params, losses = L.train(ex, hidden=64, b=BLOCK, steps=1500, lr=2e-3, loss="span")
             t_train = time.perf_counter() - t0
             out = {}
             def run_learned():
@@ -347,9 +348,9 @@ def run_ours(args):
                            "spmm_start_calls": st4["spmm_start"], "restarts": st4["restarts"],
                            "speedup_vs_fp64_random": ms_per_step / tl,
                            "max_rel_eval_diff_vs_fp64": float(np.max(np.abs(ev4 - ev) / np.abs(ev))),
-                           "train": {"graphs": len(ex), "scales": "12-16", "steps": 600,
+                           "train": {"graphs": len(ex), "scales": "12-17", "steps": 1500,
+                                     "loss": "span vs the 8 wanted Ritz vectors",
                                      "final_loss": float(np.mean(losses[-50:])),
-                                     "target_ritz_offset": args.learned_offset,
                                      "s": round(t_train, 2)}}
         except Exception as e:
             learned_res = {"error": str(e)}
@@ -359,16 +360,18 @@ def run_ours(args):
     if not args.no_semi:
         try:
             cap = 256 << 20
-            with fe.Csr.from_graph(g, device_mem_cap_bytes=cap) as hs:
-                si = hs.info()
-                Xs = fe.random_normal(n, 4, dtype=torch.float32, seed=3)
-                Ys = torch.empty_like(Xs)
-                fe.spmm(hs, Xs, Ys)
-                ts = statistics.median(time_cuda(lambda: fe.spmm(hs, Xs, Ys), 5, torch))
-            semi = {"cap_bytes": cap, "panels": si["panels"], "device_bytes": si["device_bytes"],
-                    "f32_b4_ms": round(ts, 3),
-                    "GBps": round(spmm_bytes(n, nnz, 4, 4) / (ts / 1000.0) / 1e9, 1),
-                    "h2d_GBps": round((4 * nnz + 16 * si["rows_mid"]) / (ts / 1000.0) / 1e9, 1)}
+            semi = {"cap_bytes": cap}
+            for mode in ("staged", "direct"):
+                with fe.Csr.from_graph(g, device_mem_cap_bytes=cap, semi_direct=mode == "direct") as hs:
+                    si = hs.info()
+                    Xs = fe.random_normal(n, 4, dtype=torch.float32, seed=3)
+                    Ys = torch.empty_like(Xs)
+                    fe.spmm(hs, Xs, Ys)
+                    ts = statistics.median(time_cuda(lambda: fe.spmm(hs, Xs, Ys), 5, torch))
+                semi[mode] = {"panels": si["panels"], "device_bytes": si["device_bytes"],
+                              "f32_b4_ms": round(ts, 3),
+                              "GBps": round(spmm_bytes(n, nnz, 4, 4) / (ts / 1000.0) / 1e9, 1),
+                              "host_read_GBps": round((4 * nnz + 16 * si["rows_mid"]) / (ts / 1000.0) / 1e9, 1)}
         except Exception as e:
             semi = {"error": str(e)}
 
@@ -456,9 +459,10 @@ def run_config(args):
                        speedup=t64 / tm, evals=[float(x) for x in ev64])
         else:
             from paper_1602_01421_gb300 import learned as L
-            ex = [L.make_example(graphgen.rmat(sc, seed=100 + i), BLOCK, offset=args.learned_offset)
-                  for i, sc in enumerate([16, 17, 18, 19, 20] * args.learned_graphs)]
-            params, losses = L.train(ex, hidden=64, b=BLOCK, steps=args.learned_steps, lr=3e-3)
+            ex = [L.make_subspace_example(graphgen.rmat(sc, seed=100 + i))
+                  for i, sc in enumerate([14, 15, 16, 17, 18, 19, 20] * args.learned_graphs)]
+            params, losses = L.train(ex, hidden=64, b=BLOCK, steps=args.learned_steps, lr=2e-3,
+                                     loss="span")
             res = []
             for sd in (1, 2, 3):
                 ev, X, st, t = timed(nev=8, block=BLOCK, nblocks=NBLOCKS, tol=1e-8, which="LM", seed=sd,
@@ -467,7 +471,8 @@ def run_config(args):
             ev, X, st, t = timed(nev=8, block=BLOCK, nblocks=NBLOCKS, tol=1e-8, which="LM", seed=1,
                                  mode="mixed", mlp_weights=params, mlp_hidden=64)
             out.update(workload="rmat24-ef16 (fresh seed) nev8 b4 m32 tol1e-8 mixed",
-                       train={"graphs": len(ex), "scales": "16-20", "steps": args.learned_steps,
+                       train={"graphs": len(ex), "scales": "14-20", "steps": args.learned_steps,
+                              "loss": "span vs the 8 wanted Ritz vectors",
                               "final_loss": float(np.mean(losses[-50:]))},
                        random=res, learned={"s": t, "spmm_blocks": st["spmm_blocks"],
                                             "spmm_start_calls": st["spmm_start"],
@@ -479,7 +484,7 @@ def run_config(args):
         out.update(n=g.n, nnz=g.nnz, gen_s=round(time.perf_counter() - t0, 1))
         cap = 6 << 30
         t0 = time.perf_counter()
-        h = fe.Csr.from_graph(g, device_mem_cap_bytes=cap)
+        h = fe.Csr.from_graph(g, device_mem_cap_bytes=cap, semi_direct=args.semi_direct)
         info = h.info()
         out.update(create_s=round(time.perf_counter() - t0, 1), cap_bytes=cap, panels=info["panels"],
                    device_bytes=info["device_bytes"])
@@ -513,8 +518,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-semi", action="store_true")
-    ap.add_argument("--learned-offset", type=int, default=0,
-                    help="first Ritz vector (largest-magnitude order) the MLP is trained to predict")
+
     # dram__bytes_read.sum + dram__bytes_write.sum of gram_kernel<double,4,4> at the roofline
     # shape, one ncu capture (profiles/gram_f64_rmat22.md); update when that kernel changes
     ap.add_argument("--traffic", type=float, default=1.073789e9 + 3.321856e6,
@@ -525,10 +529,14 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1"],
                     help="solve: warm-up + timed solves only; spmm1: SpMM launches only")
     ap.add_argument("--b", type=int, default=4)
+    ap.add_argument("--solve-mode", default="fp64", choices=["fp64", "mixed"],
+                    help="--only solve: which solve to run")
     ap.add_argument("--config", default="rmat22", choices=["rmat22", "mixed24", "learned24", "semiext27"],
                     help="rmat22: the step metric (default); others print their own results line")
     ap.add_argument("--learned-graphs", type=int, default=2)
-    ap.add_argument("--learned-steps", type=int, default=800)
+    ap.add_argument("--semi-direct", action="store_true",
+                    help="semiext27: kernels read the pinned panels directly (no staging copies)")
+    ap.add_argument("--learned-steps", type=int, default=1500)
     ap.add_argument("--prec", default="f64", choices=["f32", "f64"])
     args = ap.parse_args()
     os.makedirs(args.outdir, exist_ok=True)

@@ -93,6 +93,10 @@ typedef struct {
   /* Bound, in milliseconds, on each wait for a panel copy in semi-external mode (0 = 60000).
    * A wait that runs out makes fe_spmm return FE_ERR_TIMEOUT. */
   int copy_timeout_ms;
+  /* Semi-external panel access: 0 = staged (each panel is copied into one of two device
+   * buffers, copies overlapped with the previous panel's kernels); 1 = direct (the kernels read
+   * the packed panels in pinned host memory through its device mapping, with no copies). */
+  int semi_direct;
 } fe_csr_opts;
 
 /* Fill *opts with the defaults. */
@@ -230,6 +234,20 @@ int fe_mlp_forward(const float* F, int64_t n, const float* params, int hidden, i
 int fe_mlp_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
                      const float* U, float* grad, double* loss);
 
+/* Subspace form of the loss, invariant to any rotation of the targets: U (n x t) is an
+ * orthonormal target basis (e.g. the nev wanted Ritz vectors) and
+ * L = sum_j (1 - |U^T z_j|^2 / |z_j|^2), the part of each output column outside span(U).
+ * hidden = 64, b in {4, 8}, t in {4, 8, 16}.  Otherwise as fe_mlp_loss_grad. */
+int fe_mlp_subspace_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                              const float* U, int t, float* grad, double* loss);
+
+/* Span form, invariant to rotations of U and to any invertible mixing of the outputs:
+ * L = b - tr((Z^T Z)^{-1} Z^T U U^T Z), b minus the squared cosines of the principal angles
+ * between span(Z) and span(U), so b copies of one good direction score as one.  hidden = 64,
+ * (b, t) in {(4, 4), (4, 8), (8, 8)}.  Otherwise as fe_mlp_loss_grad. */
+int fe_mlp_span_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                          const float* U, int t, float* grad, double* loss);
+
 /* One Adam step (Kingma & Ba 2015, bias-corrected; step counts from 1) on count parameters. */
 int fe_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count, double lr,
                 double beta1, double beta2, double eps, int step);
@@ -245,7 +263,7 @@ typedef struct {
   const float* mlp_weights; /* DEVICE packed MLP parameters (fe_mlp_param_count floats,
                              b = block), for FE_START_LEARNED; features use `seed` */
   int mlp_hidden;         /* hidden width of that MLP: 32 or 64 (64) */
-  double mixed_tol;       /* FP32-phase tolerance in mixed mode (1e-5) */
+  double mixed_tol;       /* FP32-phase tolerance in mixed mode (5e-6) */
   int max_sweeps;         /* Jacobi sweeps per Rayleigh-Ritz (60) */
 } fe_eigs_opts;
 

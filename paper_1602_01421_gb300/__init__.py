@@ -52,7 +52,7 @@ class Csr:
     def __init__(self, rowptr: np.ndarray, colidx: np.ndarray, *, validate: bool = True,
                  check_symmetric: bool = False, device_mem_cap_bytes: int = 0,
                  tail_max: int = 0, hub_min: int = 0, hub_chunk: int = 0, panel_nnz: int = 0,
-                 copy_timeout_ms: int = 0):
+                 copy_timeout_ms: int = 0, semi_direct: bool = False):
         lib = load()
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(colidx, dtype=np.int32)
@@ -64,6 +64,7 @@ class Csr:
         o.device_mem_cap_bytes = int(device_mem_cap_bytes)
         o.tail_max, o.hub_min, o.hub_chunk = int(tail_max), int(hub_min), int(hub_chunk)
         o.panel_nnz, o.copy_timeout_ms = int(panel_nnz), int(copy_timeout_ms)
+        o.semi_direct = int(semi_direct)
         h = ctypes.c_void_p()
         check(lib.fe_csr_create_ex(self.n, self._rowptr.ctypes.data_as(ctypes.c_void_p),
                                    self._colidx.ctypes.data_as(ctypes.c_void_p),
@@ -170,7 +171,7 @@ def random_normal(n: int, b: int, dtype=None, seed: int = 1, stream: int = 4, of
 
 def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: str = "LM", *,
          mode: str = "fp64", start=None, seed: int = 1, max_restarts: int = 500,
-         mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 1e-5,
+         mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 5e-6,
          return_vectors: bool = True, raise_on_noconverge: bool = True):
     """Block Krylov-Schur (fe_eigs_ex).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
     None, stats dict)."""
@@ -243,6 +244,32 @@ def mlp_loss_grad(F, params, hidden: int, b: int, U, grad=None):
     _stream()
     check(load().fe_mlp_loss_grad(_dev(F, "F"), F.shape[0], _dev(params, "params"), hidden, b,
                                   _dev(U, "U"), _dev(grad, "grad"), ctypes.byref(loss)))
+    return loss.value, grad
+
+
+def mlp_subspace_loss_grad(F, params, hidden: int, b: int, U, grad=None):
+    """(loss, grad) of the rotation-invariant subspace loss against an n x t basis U."""
+    torch = _torch()
+    if grad is None:
+        grad = torch.empty_like(params)
+    loss = ctypes.c_double(0.0)
+    _stream()
+    check(load().fe_mlp_subspace_loss_grad(_dev(F, "F"), F.shape[0], _dev(params, "params"),
+                                           hidden, b, _dev(U, "U"), U.shape[1], _dev(grad, "grad"),
+                                           ctypes.byref(loss)))
+    return loss.value, grad
+
+
+def mlp_span_loss_grad(F, params, hidden: int, b: int, U, grad=None):
+    """(loss, grad) of the span form: b - tr((Z^T Z)^-1 Z^T U U^T Z)."""
+    torch = _torch()
+    if grad is None:
+        grad = torch.empty_like(params)
+    loss = ctypes.c_double(0.0)
+    _stream()
+    check(load().fe_mlp_span_loss_grad(_dev(F, "F"), F.shape[0], _dev(params, "params"), hidden,
+                                       b, _dev(U, "U"), U.shape[1], _dev(grad, "grad"),
+                                       ctypes.byref(loss)))
     return loss.value, grad
 
 

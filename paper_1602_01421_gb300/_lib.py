@@ -27,7 +27,8 @@ class CsrOpts(ctypes.Structure):
     _fields_ = [("device_mem_cap_bytes", ctypes.c_int64), ("validate", ctypes.c_int),
                 ("check_symmetric", ctypes.c_int), ("tail_max", ctypes.c_int),
                 ("hub_min", ctypes.c_int), ("hub_chunk", ctypes.c_int),
-                ("panel_nnz", ctypes.c_int64), ("copy_timeout_ms", ctypes.c_int)]
+                ("panel_nnz", ctypes.c_int64), ("copy_timeout_ms", ctypes.c_int),
+                ("semi_direct", ctypes.c_int)]
 
 
 class CsrInfo(ctypes.Structure):
@@ -94,6 +95,10 @@ def load(build_if_missing: bool = True):
             "fe_mlp_forward": (i32, [vp, i64, vp, i32, i32, vp]),
             "fe_mlp_loss_grad": (i32, [vp, i64, vp, i32, i32, vp, vp, ctypes.POINTER(dbl)]),
             "fe_mlp_adam": (i32, [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32]),
+            "fe_mlp_subspace_loss_grad": (i32, [vp, i64, vp, i32, i32, vp, i32, vp,
+                                                ctypes.POINTER(dbl)]),
+            "fe_mlp_span_loss_grad": (i32, [vp, i64, vp, i32, i32, vp, i32, vp,
+                                            ctypes.POINTER(dbl)]),
             "fe_block_gram_noalloc": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_eigs": (i32, [vp, i32, i32, i32, dbl, i32, vp, vp]),
             "fe_eigs_ex": (i32, [vp, i32, i32, i32, dbl, i32, ctypes.POINTER(EigsOpts), vp, vp,

@@ -575,3 +575,167 @@ int gram_into_scratch(const BlockSet& V, int64_t n, const void* W, int bw, int l
 }
 
 }  // namespace fe
+
+namespace fe {
+
+// ---------------------------------------------------------------- fused update + Gram
+// One sweep over the rows: W[r] = beta (W[r] M) + alpha sum_j V_j[r] C_j (thread per row, as
+// update_kernel), then the Gram partials of [V_0 .. V_{nv-1}, W_new]^T W_new (only of W_new^T
+// W_new when gram_v == 0), accumulated per CTA like gram_kernel.  Phase A leaves the tile's new
+// W rows in shared memory; phase B re-reads the tile's V rows, which phase A has just pulled
+// into L1, so V comes from DRAM once for both operations.
+template <typename T, int BV, int BW>
+__global__ void __launch_bounds__(256) update_gram_kernel(const BlockSet V, const double* __restrict__ C,
+                                                          double alpha, double beta,
+                                                          const double* __restrict__ M,
+                                                          T* __restrict__ W, int64_t n, int gram_v,
+                                                          const int* __restrict__ skip,
+                                                          double* __restrict__ partial) {
+  if (skip && *skip) return;
+  constexpr int R = 256;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = V.nv * BV;
+  T* sC = reinterpret_cast<T*>(smem_raw);
+  T* sM = sC + (size_t)k * BW;
+  T* sW = sM + BW * BW;
+  double* sP = reinterpret_cast<double*>(smem_raw + ((((size_t)k * BW + BW * BW + (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15));
+  const int gblocks = gram_v ? V.nv + 1 : 1;  // Gram row blocks: the V blocks (if any), then W
+  const int nout = (gram_v ? k : 0) * BW + BW * BW;
+  for (int e = threadIdx.x; e < k * BW; e += blockDim.x) sC[e] = (T)(alpha * C[e]);
+  if (M)
+    for (int e = threadIdx.x; e < BW * BW; e += blockDim.x) sM[e] = (T)(beta * M[e]);
+  for (int e = threadIdx.x; e < nout; e += blockDim.x) sP[e] = 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < n; r0 += (int64_t)gridDim.x * R) {
+    __syncthreads();  // coefficients loaded / previous tile's sW consumed
+    const int rows = (int)min((int64_t)R, n - r0);
+    // phase A: update (thread per row)
+    if ((int)threadIdx.x < rows) {
+      const int64_t r = r0 + threadIdx.x;
+      T acc[BW];
+      if (beta == 0.0) {
+#pragma unroll
+        for (int q = 0; q < BW; ++q) acc[q] = T(0);
+      } else {
+        T w[BW];
+        ld_row_rw<T, BW>(W + r * BW, w);
+        if (M) {
+#pragma unroll
+          for (int q = 0; q < BW; ++q) {
+            T a = T(0);
+#pragma unroll
+            for (int p = 0; p < BW; ++p) a = fma(w[p], sM[p * BW + q], a);
+            acc[q] = a;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < BW; ++q) acc[q] = (T)beta * w[q];
+        }
+      }
+      for (int j = 0; j < V.nv; ++j) {
+        T v[BV];
+        load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r, v);
+        const T* c = sC + j * BV * BW;
+#pragma unroll
+        for (int p = 0; p < BV; ++p)
+#pragma unroll
+          for (int q = 0; q < BW; ++q) acc[q] = fma(v[p], c[p * BW + q], acc[q]);
+      }
+      st_row<T, BW>(W + r * BW, acc);
+#pragma unroll
+      for (int q = 0; q < BW; ++q) sW[threadIdx.x * BW + q] = acc[q];
+    }
+    __syncthreads();
+    // phase B: Gram tiles (warp per row block, lane = row)
+    for (int tile = warp; tile < gblocks; tile += nwarps) {
+      const bool isW = tile == gblocks - 1;
+      const int j = tile;
+      constexpr int NR = BV > BW ? BV : BW;
+      T acc[NR][BW];
+#pragma unroll
+      for (int p = 0; p < NR; ++p)
+#pragma unroll
+        for (int q = 0; q < BW; ++q) acc[p][q] = T(0);
+      for (int r = lane; r < rows; r += 32) {
+        T wq[BW];
+#pragma unroll
+        for (int q = 0; q < BW; ++q) wq[q] = sW[r * BW + q];
+        if (isW) {
+#pragma unroll
+          for (int p = 0; p < BW; ++p)
+#pragma unroll
+            for (int q = 0; q < BW; ++q) acc[p][q] = fma(wq[p], wq[q], acc[p][q]);
+        } else {
+          T v[BV];
+          load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r0 + r, v);
+#pragma unroll
+          for (int p = 0; p < BV; ++p)
+#pragma unroll
+            for (int q = 0; q < BW; ++q) acc[p][q] = fma(v[p], wq[q], acc[p][q]);
+        }
+      }
+      const int np = isW ? BW : BV;
+      const int rowoff = isW ? (gram_v ? k : 0) : j * BV;
+#pragma unroll
+      for (int p = 0; p < NR; ++p) {
+        if (p >= np) break;
+#pragma unroll
+        for (int q = 0; q < BW; ++q) {
+          double a = (double)acc[p][q];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFullMask, a, off);
+          if (lane == 0) sP[(rowoff + p) * BW + q] += a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nout; e += blockDim.x) partial[(int64_t)blockIdx.x * nout + e] = sP[e];
+}
+
+template <typename T, int BV, int BW>
+static int launch_update_gram(const BlockSet& V, int64_t n, const double* C, double alpha,
+                              double beta, const double* M, T* W, int gram_v, const int* skip,
+                              double* G, cudaStream_t s) {
+  constexpr int R = 256;
+  const int k = V.nv * BV;
+  const int nout = (gram_v ? k : 0) * BW + BW * BW;
+  const size_t smem = ((((size_t)k * BW + BW * BW + (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15) +
+                      (size_t)nout * sizeof(double);
+  FE_ARG(smem <= 200 * 1024, "update_gram: coefficient matrix too large");
+  static bool configured = false;
+  if (!configured) {
+    FE_CUDA(cudaFuncSetAttribute(update_gram_kernel<T, BV, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured = true;
+  }
+  int nctas = (int)std::min<int64_t>(ceil_div(n, R), 2 * num_sms());
+  nctas = std::max(nctas, 1);
+  double* part = small_scratch(0, (size_t)nctas * nout);
+  if (!part) return FE_ERR_OOM;
+  update_gram_kernel<T, BV, BW><<<nctas, 256, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, part);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  gram_reduce_kernel<<<(unsigned)ceil_div(nout, 128), 128, 0, s>>>(part, nctas, nout, 1.0, G);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// W = beta W M + alpha V C; G = [V; W]^T W (gram_v) or W^T W, rows (j*b + p) then W's b rows.
+// V blocks and W must all be n x b with ld b (the solver's subspace blocks).
+int update_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
+                const double* M, void* W, int b, fe_dtype dt, int gram_v, const int* skip,
+                double* G, cudaStream_t s) {
+  FE_ARG(V.nv >= 0 && V.nv <= kMaxBlocks, "update_gram: nv = %d", V.nv);
+  FE_ARG(V.nv == 0 || (V.bv == b && V.ld == b), "update_gram: blocks must be n x b");
+#define UG(T, B) return launch_update_gram<T, B, B>(V, n, C, alpha, beta, M, static_cast<T*>(W), gram_v, skip, G, s)
+  if (dt == FE_F32) {
+    switch (b) { case 1: UG(float, 1); case 2: UG(float, 2); case 4: UG(float, 4); case 8: UG(float, 8); }
+  } else {
+    switch (b) { case 1: UG(double, 1); case 2: UG(double, 2); case 4: UG(double, 4); case 8: UG(double, 8); }
+  }
+#undef UG
+  return set_error(FE_ERR_INVALID, "update_gram: b = %d not in {1, 2, 4, 8}", b);
+}
+
+}  // namespace fe

@@ -315,7 +315,7 @@ void fe_eigs_opts_default(fe_eigs_opts* o) {
   o->mode = FE_MODE_FP64;
   o->start = FE_START_RANDOM;
   o->mlp_hidden = 64;
-  o->mixed_tol = 1e-5;
+  o->mixed_tol = 5e-6;
   o->max_sweeps = 60;
 }
 
@@ -386,9 +386,9 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
     }
   } else {
     // FP32 phase (stops early if it stagnates above its tolerance)
-    p1.tol = std::max(tol, o.mixed_tol > 0 ? o.mixed_tol : 1e-5);
+    p1.tol = std::max(tol, o.mixed_tol > 0 ? o.mixed_tol : 5e-6);
     p1.dt = FE_F32;
-    p1.stagnation_window = 20;
+    p1.stagnation_window = 100;
     rc = p1.run(start, block);
     if (rc != FE_OK && rc != FE_ERR_NOCONVERGE && rc != kStagnated) return rc;
     FE_CUDA(cudaStreamSynchronize(s));

@@ -215,20 +215,31 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restric
 }
 
 // ---------------------------------------------------------------- loss statistics
-// partial[cta][2B]: s_j = sum z_ij u_ij, q_j = sum z_ij^2
-template <int H, int B>
+// TT = 0 (column form): partial[cta] = [s_j = sum_i z_ij u_ij (B), q_j = sum_i z_ij^2 (B)].
+// TT > 0 (subspace form, U is n x TT): partial[cta] = [S_tj = sum_i u_it z_ij (TT x B), q_j (B)].
+// SPAN: the second block holds the full Gram M = Z^T Z (B x B) instead of its diagonal q.
+template <int TT, int B, bool SPAN = false> struct StatsShape {
+  static constexpr int NS = TT == 0 ? B : TT * B;
+  static constexpr int NQ = SPAN ? B * B : B;
+  static constexpr int NP = NS + NQ;
+};
+
+template <int H, int B, int TT, bool SPAN = false>
 __global__ void __launch_bounds__(256) mlp_stats_kernel(const float* __restrict__ F, int64_t n,
                                                         const float* __restrict__ params,
                                                         const float* __restrict__ U,
                                                         double* __restrict__ partial) {
   using P = MlpParams<H, B>;
+  using SS = StatsShape<TT, B, SPAN>;
   __shared__ float sp[P::COUNT];
-  __shared__ double red[2 * B][8];
+  __shared__ double red[SS::NP][8];
   for (int e = threadIdx.x; e < P::COUNT; e += blockDim.x) sp[e] = params[e];
   __syncthreads();
-  double s[B], q[B];
+  double s[SS::NS], q[SS::NQ];
 #pragma unroll
-  for (int j = 0; j < B; ++j) s[j] = q[j] = 0.0;
+  for (int j = 0; j < SS::NS; ++j) s[j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < SS::NQ; ++j) q[j] = 0.0;
 #pragma unroll 1
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     // keep the weight loads inside the loop (hoisting 64 x 64 shared loads spills registers)
@@ -237,29 +248,39 @@ __global__ void __launch_bounds__(256) mlp_stats_kernel(const float* __restrict_
 #pragma unroll
     for (int k = 0; k < kNFeat; ++k) f[k] = F[i * kNFeat + k];
     mlp_row_forward<H, B>(sp, f, h1, z, nullptr);
+    if (TT == 0) {
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      s[j] += (double)z[j] * (double)U[i * B + j];
-      q[j] += (double)z[j] * (double)z[j];
+      for (int j = 0; j < B; ++j) s[j] += (double)z[j] * (double)U[i * B + j];
+    } else {
+#pragma unroll
+      for (int t = 0; t < (TT == 0 ? 1 : TT); ++t) {
+        const double u = (double)U[i * (TT == 0 ? 1 : TT) + t];
+#pragma unroll
+        for (int j = 0; j < B; ++j) s[t * B + j] += u * (double)z[j];
+      }
+    }
+    if (SPAN) {
+#pragma unroll
+      for (int k = 0; k < B; ++k)
+#pragma unroll
+        for (int j = 0; j < B; ++j) q[(k * B + j) % SS::NQ] += (double)z[k] * (double)z[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < B; ++j) q[j] += (double)z[j] * (double)z[j];
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < B; ++j) {
-    for (int off = 16; off > 0; off >>= 1) {
-      s[j] += __shfl_xor_sync(0xffffffffu, s[j], off);
-      q[j] += __shfl_xor_sync(0xffffffffu, q[j], off);
-    }
-    if (lane == 0) {
-      red[j][warp] = s[j];
-      red[B + j][warp] = q[j];
-    }
+  for (int j = 0; j < SS::NP; ++j) {
+    double v = j < SS::NS ? s[j] : q[j - SS::NS];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[j][warp] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 2 * B) {
+  for (int e = threadIdx.x; e < SS::NP; e += blockDim.x) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
-    partial[(int64_t)blockIdx.x * 2 * B + threadIdx.x] = t;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[e][w];
+    partial[(int64_t)blockIdx.x * SS::NP + e] = t;
   }
 }
 
@@ -270,32 +291,32 @@ __global__ void __launch_bounds__(256) mlp_stats_kernel(const float* __restrict_
 constexpr int kTR = 128;
 
 // Row strides are padded by one float so a warp writing 32 consecutive rows hits 32 banks.
-template <int H, int B>
+template <int H, int B, int TT, bool SPAN = false>
 struct GradSmem {
   static constexpr int LDF = kNFeat + 1, LD = H + 1, LDZ = B + 1;
   static constexpr int F = 0, H1 = F + kTR * LDF, H2 = H1 + kTR * LD, DH1 = H2 + kTR * LD,
                        DH2 = DH1 + kTR * LD, DZ = DH2 + kTR * LD, PAR = DZ + kTR * LDZ,
-                       TOTAL = PAR + MlpParams<H, B>::COUNT;
+                       COEF = PAR + MlpParams<H, B>::COUNT,
+                       TOTAL = COEF + StatsShape<TT, B, SPAN>::NP;
 };
 
-template <int H, int B>
+// dz_ij: column form ca_j u_ij + cb_j z_ij; subspace form sum_t u_it A_tj + c_j z_ij, with the
+// coefficients (per column, from mlp_loss_coef_kernel) in shared memory.
+template <int H, int B, int TT, bool SPAN = false>
 __global__ void __launch_bounds__(kTR) mlp_grad_kernel(const float* __restrict__ F, int64_t n,
                                                        const float* __restrict__ params,
                                                        const float* __restrict__ U,
                                                        const double* __restrict__ coef,
                                                        double* __restrict__ partial) {
   using P = MlpParams<H, B>;
-  using S = GradSmem<H, B>;
+  using S = GradSmem<H, B, TT, SPAN>;
+  using SS = StatsShape<TT, B, SPAN>;
   constexpr int KPER = (P::COUNT + kTR - 1) / kTR;
   extern __shared__ __align__(16) float sm[];
   float* sp = sm + S::PAR;
+  float* sc = sm + S::COEF;
   for (int e = threadIdx.x; e < P::COUNT; e += kTR) sp[e] = params[e];
-  float ca[B], cb[B];
-#pragma unroll
-  for (int j = 0; j < B; ++j) {
-    ca[j] = (float)coef[j];
-    cb[j] = (float)coef[B + j];
-  }
+  for (int e = threadIdx.x; e < SS::NP; e += kTR) sc[e] = (float)coef[e];
   float acc[KPER];
 #pragma unroll
   for (int k = 0; k < KPER; ++k) acc[k] = 0.0f;
@@ -314,11 +335,31 @@ __global__ void __launch_bounds__(kTR) mlp_grad_kernel(const float* __restrict__
 #pragma unroll
       for (int k = 0; k < kNFeat; ++k) sm[S::F + t * S::LDF + k] = f[k];
       float dz[B];
+      if (SPAN) {                            // z-term: z C with C (B x B)
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        dz[j] = ca[j] * U[i * B + j] + cb[j] * z[j];
-        sm[S::DZ + t * S::LDZ + j] = dz[j];
+        for (int j = 0; j < B; ++j) {
+          float a = 0.0f;
+#pragma unroll
+          for (int k = 0; k < B; ++k) a = fmaf(z[k], sc[SS::NS + (k * B + j) % SS::NQ], a);
+          dz[j] = a;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < B; ++j) dz[j] = sc[SS::NS + j] * z[j];
       }
+      if (TT == 0) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) dz[j] = fmaf(sc[j], U[i * B + j], dz[j]);
+      } else {
+#pragma unroll
+        for (int tt = 0; tt < (TT == 0 ? 1 : TT); ++tt) {
+          const float u = U[i * (TT == 0 ? 1 : TT) + tt];
+#pragma unroll
+          for (int j = 0; j < B; ++j) dz[j] = fmaf(u, sc[tt * B + j], dz[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < B; ++j) sm[S::DZ + t * S::LDZ + j] = dz[j];
       // dh2 = (dz W3^T) * [h2 > 0]
 #pragma unroll 1
       for (int q = 0; q < H; ++q) {
@@ -380,27 +421,97 @@ __global__ void grad_reduce_kernel(const double* __restrict__ partial, int nctas
   grad[e] = (float)s;
 }
 
-// coef = [-2 s/q, 2 s^2/q^2] (2B), loss = sum_j (1 - s_j^2/q_j)
-__global__ void loss_coef_kernel(const double* __restrict__ partial, int nctas, int B,
+// From the per-CTA partials (added in CTA order): T = 0 (column form) coef = [-2 s_j/q_j (B),
+// 2 s_j^2/q_j^2 (B)], L = sum_j (1 - s_j^2/q_j); T > 0 (subspace form) coef = [-2 S_tj/q_j
+// (T x B), 2 P_j/q_j^2 (B)] with P_j = sum_t S_tj^2, L = sum_j (1 - P_j/q_j).
+__global__ void loss_coef_kernel(const double* __restrict__ partial, int nctas, int B, int T,
                                  double* __restrict__ coef, double* __restrict__ loss) {
   if (threadIdx.x != 0) return;
+  const int ns = T == 0 ? B : T * B, np = ns + B;
   double L = 0.0;
   for (int j = 0; j < B; ++j) {
-    double s = 0.0, q = 0.0;
-    for (int c = 0; c < nctas; ++c) {
-      s += partial[(int64_t)c * 2 * B + j];
-      q += partial[(int64_t)c * 2 * B + B + j];
+    double q = 0.0;
+    for (int c = 0; c < nctas; ++c) q += partial[(int64_t)c * np + ns + j];
+    const int rows = T == 0 ? 1 : T;
+    double P = 0.0;
+    for (int t = 0; t < rows; ++t) {
+      double st = 0.0;
+      const int idx = T == 0 ? j : t * B + j;
+      for (int c = 0; c < nctas; ++c) st += partial[(int64_t)c * np + idx];
+      P += st * st;
+      coef[idx] = q > 0.0 ? -2.0 * st / q : 0.0;
     }
-    if (q > 0.0) {
-      coef[j] = -2.0 * s / q;
-      coef[B + j] = 2.0 * s * s / (q * q);
-      L += 1.0 - s * s / q;
-    } else {
-      coef[j] = coef[B + j] = 0.0;
-      L += 1.0;
-    }
+    coef[ns + j] = q > 0.0 ? 2.0 * P / (q * q) : 0.0;
+    L += q > 0.0 ? 1.0 - P / q : 1.0;
   }
   *loss = L;
+}
+
+// Span form: from partials [S (T x B), M (B x B)]: N = S^T S, Mi = M^{-1} (Gauss-Jordan with
+// partial pivoting, B <= 8), coef = [A = -2 S Mi (T x B), C = 2 Mi N Mi (B x B)],
+// loss = B - tr(Mi N).
+__global__ void span_coef_kernel(const double* __restrict__ partial, int nctas, int B, int T,
+                                 double* __restrict__ coef, double* __restrict__ loss) {
+  if (threadIdx.x != 0) return;
+  const int ns = T * B, np = ns + B * B;
+  double S[16 * 8], M[8 * 8], Mi[8 * 8], N[8 * 8], X[8 * 8];
+  for (int e = 0; e < np; ++e) {
+    double v = 0.0;
+    for (int c = 0; c < nctas; ++c) v += partial[(int64_t)c * np + e];
+    if (e < ns) S[e] = v;
+    else M[e - ns] = v;
+  }
+  for (int e = 0; e < B * B; ++e) Mi[e] = (e / B == e % B) ? 1.0 : 0.0;
+  bool ok = true;
+  for (int c = 0; c < B && ok; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < B; ++r)
+      if (fabs(M[r * B + c]) > fabs(M[piv * B + c])) piv = r;
+    if (!(fabs(M[piv * B + c]) > 0.0)) { ok = false; break; }
+    for (int k = 0; k < B; ++k) {
+      double t = M[c * B + k]; M[c * B + k] = M[piv * B + k]; M[piv * B + k] = t;
+      t = Mi[c * B + k]; Mi[c * B + k] = Mi[piv * B + k]; Mi[piv * B + k] = t;
+    }
+    const double d = M[c * B + c];
+    for (int k = 0; k < B; ++k) { M[c * B + k] /= d; Mi[c * B + k] /= d; }
+    for (int r = 0; r < B; ++r) {
+      if (r == c) continue;
+      const double f = M[r * B + c];
+      for (int k = 0; k < B; ++k) { M[r * B + k] -= f * M[c * B + k]; Mi[r * B + k] -= f * Mi[c * B + k]; }
+    }
+  }
+  if (!ok) {
+    for (int e = 0; e < np; ++e) coef[e] = 0.0;
+    *loss = (double)B;
+    return;
+  }
+  for (int i = 0; i < B; ++i)                       // N = S^T S
+    for (int j = 0; j < B; ++j) {
+      double v = 0.0;
+      for (int t = 0; t < T; ++t) v += S[t * B + i] * S[t * B + j];
+      N[i * B + j] = v;
+    }
+  double tr = 0.0;
+  for (int i = 0; i < B; ++i)                       // X = Mi N, tr(Mi N)
+    for (int j = 0; j < B; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < B; ++k) v += Mi[i * B + k] * N[k * B + j];
+      X[i * B + j] = v;
+      if (i == j) tr += v;
+    }
+  for (int t = 0; t < T; ++t)                       // A = -2 S Mi
+    for (int j = 0; j < B; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < B; ++k) v += S[t * B + k] * Mi[k * B + j];
+      coef[t * B + j] = -2.0 * v;
+    }
+  for (int i = 0; i < B; ++i)                       // C = 2 (Mi N) Mi
+    for (int j = 0; j < B; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < B; ++k) v += X[i * B + k] * Mi[k * B + j];
+      coef[ns + i * B + j] = 2.0 * v;
+    }
+  *loss = (double)B - tr;
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -426,30 +537,32 @@ static int forward_hb(const float* F, int64_t n, const float* params, float* Z, 
   return FE_OK;
 }
 
-template <int H, int B>
+template <int H, int B, int TT = 0, bool SPAN = false>
 static int loss_grad_hb(const float* F, int64_t n, const float* params, const float* U,
                         float* grad, double* loss_host, cudaStream_t s) {
   using P = MlpParams<H, B>;
-  using S = GradSmem<H, B>;
+  using S = GradSmem<H, B, TT, SPAN>;
+  using SS = StatsShape<TT, B, SPAN>;
   const int sctas = std::max(1, (int)std::min<int64_t>(ceil_div(n, 256), 2 * num_sms()));
   const int gctas = std::max(1, (int)std::min<int64_t>(ceil_div(n, kTR), num_sms()));
-  double* part = small_scratch(15, (size_t)sctas * 2 * B + 2 * B + 1);
+  double* part = small_scratch(15, (size_t)sctas * SS::NP + SS::NP + 1);
   double* gpart = small_scratch(16, (size_t)gctas * P::COUNT);
   if (!part || !gpart) return FE_ERR_OOM;
-  double* coef = part + (size_t)sctas * 2 * B;
-  double* dloss = coef + 2 * B;
-  mlp_stats_kernel<H, B><<<sctas, 256, 0, s>>>(F, n, params, U, part);
+  double* coef = part + (size_t)sctas * SS::NP;
+  double* dloss = coef + SS::NP;
+  mlp_stats_kernel<H, B, TT, SPAN><<<sctas, 256, 0, s>>>(F, n, params, U, part);
   count_launch();
-  loss_coef_kernel<<<1, 32, 0, s>>>(part, sctas, B, coef, dloss);
+  if (SPAN) span_coef_kernel<<<1, 32, 0, s>>>(part, sctas, B, TT, coef, dloss);
+  else loss_coef_kernel<<<1, 32, 0, s>>>(part, sctas, B, TT, coef, dloss);
   count_launch();
   const size_t smem = sizeof(float) * S::TOTAL;
   FE_ARG(smem <= 220 * 1024, "mlp: hidden/b too large for the gradient kernel");
   static bool configured = false;
   if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(mlp_grad_kernel<H, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FE_CUDA(cudaFuncSetAttribute(mlp_grad_kernel<H, B, TT, SPAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;
   }
-  mlp_grad_kernel<H, B><<<gctas, kTR, smem, s>>>(F, n, params, U, coef, gpart);
+  mlp_grad_kernel<H, B, TT, SPAN><<<gctas, kTR, smem, s>>>(F, n, params, U, coef, gpart);
   count_launch();
   grad_reduce_kernel<<<(unsigned)ceil_div(P::COUNT, 256), 256, 0, s>>>(gpart, gctas, P::COUNT, grad);
   count_launch();
@@ -486,6 +599,33 @@ int mlp_loss_grad(const float* F, int64_t n, const float* params, int hidden, in
   if (hidden == 32) { FE_MLP_DISPATCH(32, LG) }
 #undef LG
   return set_error(FE_ERR_INVALID, "mlp: hidden must be 32 or 64 and b in {1,2,4,8,16} (got %d, %d)", hidden, b);
+}
+
+int mlp_subspace_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                           const float* U, int t, float* grad, double* loss, cudaStream_t s) {
+#define SLG(TT, B) loss_grad_hb<64, B, TT>(F, n, params, U, grad, loss, s)
+  if (hidden == 64 && (b == 4 || b == 8) && (t == 4 || t == 8 || t == 16)) {
+    if (b == 4) {
+      if (t == 4) return SLG(4, 4);
+      if (t == 8) return SLG(8, 4);
+      return SLG(16, 4);
+    }
+    if (t == 4) return SLG(4, 8);
+    if (t == 8) return SLG(8, 8);
+    return SLG(16, 8);
+  }
+#undef SLG
+  return set_error(FE_ERR_INVALID, "mlp subspace loss: needs hidden 64, b in {4, 8}, t in {4, 8, 16} (got %d, %d, %d)", hidden, b, t);
+}
+
+int mlp_span_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                       const float* U, int t, float* grad, double* loss, cudaStream_t s) {
+#define PLG(TT, B) loss_grad_hb<64, B, TT, true>(F, n, params, U, grad, loss, s)
+  if (hidden == 64 && b == 4 && t == 4) return PLG(4, 4);
+  if (hidden == 64 && b == 4 && t == 8) return PLG(8, 4);
+  if (hidden == 64 && b == 8 && t == 8) return PLG(8, 8);
+#undef PLG
+  return set_error(FE_ERR_INVALID, "mlp span loss: needs hidden 64 and (b, t) in {(4,4), (4,8), (8,8)} (got %d, %d, %d)", hidden, b, t);
 }
 
 // Start block for fe_eigs: features -> MLP -> FP64 row-major n x b (the solver orthonormalises).
@@ -527,6 +667,18 @@ int fe_mlp_loss_grad(const float* F, int64_t n, const float* params, int hidden,
                      const float* U, float* grad, double* loss) {
   FE_ARG(F && params && U && grad && n >= 1, "fe_mlp_loss_grad: bad argument");
   return mlp_loss_grad(F, n, params, hidden, b, U, grad, loss, cur_stream());
+}
+
+int fe_mlp_subspace_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                              const float* U, int t, float* grad, double* loss) {
+  FE_ARG(F && params && U && grad && n >= 1, "fe_mlp_subspace_loss_grad: bad argument");
+  return mlp_subspace_loss_grad(F, n, params, hidden, b, U, t, grad, loss, cur_stream());
+}
+
+int fe_mlp_span_loss_grad(const float* F, int64_t n, const float* params, int hidden, int b,
+                          const float* U, int t, float* grad, double* loss) {
+  FE_ARG(F && params && U && grad && n >= 1, "fe_mlp_span_loss_grad: bad argument");
+  return mlp_span_loss_grad(F, n, params, hidden, b, U, t, grad, loss, cur_stream());
 }
 
 int fe_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count, double lr,

@@ -24,6 +24,9 @@ namespace fe {
 int update_skip(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
                 const double* M, void* W, int bw, int ldw, fe_dtype dt, const int* skip,
                 cudaStream_t s);
+int update_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
+                const double* M, void* W, int b, fe_dtype dt, int gram_v, const int* skip,
+                double* G, cudaStream_t s);
 
 constexpr double kRelPivot = 1e-6;      // pivot below 1e-6 * column norm: nearly dependent
 constexpr double kAbsBreakdown = 1e-12; // remainder below 1e-12 * ||A||: breakdown
@@ -265,11 +268,18 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   vx.push_back(W);
   BlockSet Vx = blockset_of(vx, b, b);
   FE_ARG(V.nv == 0 || V.bv == b, "orth: V block width %d != b %d", V.bv, b);
-  // pass 1
+  // pass 1: [G1; S1] = [V W]^T W
   FE_TRY(gram(Vx, n, W, b, b, dt, 1.0, sG1, s));
+  // the fused update + Gram sweeps hold a b x b accumulator per lane: b = 16 keeps two kernels
+  const bool fused = b <= 8;
   if (V.nv > 0) {
-    FE_TRY(update(V, n, sG1, -1.0, 1.0, nullptr, W, b, b, dt, s));
-    FE_TRY(gram(Vx, n, W, b, b, dt, 1.0, sG2, s));
+    // W <- W - V G1 and [G2; S] = [V W]^T W in one sweep
+    if (fused) {
+      FE_TRY(update_gram(V, n, sG1, -1.0, 1.0, nullptr, W, b, dt, 1, nullptr, sG2, s));
+    } else {
+      FE_TRY(update(V, n, sG1, -1.0, 1.0, nullptr, W, b, b, dt, s));
+      FE_TRY(gram(Vx, n, W, b, b, dt, 1.0, sG2, s));
+    }
     orth_post2_kernel<<<1, 256, 0, s>>>(sG1, sG2, k, b, d_anorm, update_anorm, d_G, ldg, sRacc,
                                         sM, sC, status);
   } else {
@@ -278,10 +288,14 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   }
   count_launch();
   FE_CUDA(cudaGetLastError());
-  FE_TRY(update_skip(V, n, sC, 1.0, 1.0, sM, W, b, b, dt, status, s));
-  // pass 3
-  BlockSet Wonly = blockset_of({W}, b, b);
-  FE_TRY(gram(Wonly, n, W, b, b, dt, 1.0, sS2, s));
+  // W <- (W - V G2) R1^{-1} and S2 = W^T W in one sweep (skipped after a failed pivot check)
+  if (fused) {
+    FE_TRY(update_gram(V, n, sC, 1.0, 1.0, sM, W, b, dt, 0, status, sS2, s));
+  } else {
+    FE_TRY(update_skip(V, n, sC, 1.0, 1.0, sM, W, b, b, dt, status, s));
+    BlockSet Wonly = blockset_of({W}, b, b);
+    FE_TRY(gram(Wonly, n, W, b, b, dt, 1.0, sS2, s));
+  }
   orth_post3_kernel<<<1, 64, 0, s>>>(sS2, b, sRacc, sM, d_R, ldr, status);
   count_launch();
   FE_CUDA(cudaGetLastError());

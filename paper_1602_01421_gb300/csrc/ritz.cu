@@ -181,7 +181,9 @@ int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double
     FE_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     configured = true;
   }
-  ritz_kernel<<<1, 1024, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info);
+  // few threads: each of the ~3 barriers per rotation step is cheap, and a step is only
+  // m/2 x m updates
+  ritz_kernel<<<1, 128, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;
@@ -216,19 +218,23 @@ int launch_restart_h(double* H, int m, int b, int k, const double* theta, const 
 
 // ------------------------------------------------------------ sign of eigenvectors
 // For each column c of the column-major n x ncols matrix X: find the entry of largest
-// magnitude (first index on ties) and flip the column if it is negative.
+// magnitude (first index on ties) and flip the column if it is negative.  The partials carry
+// the signed value of each block's best entry, so the flip decision never re-reads X (which
+// other blocks of the flipping kernel may already have changed).
 __global__ void colmax_partial_kernel(const double* __restrict__ X, int64_t n, int ncols,
                                       double* __restrict__ pval, int64_t* __restrict__ pidx) {
   const int c = blockIdx.y;
-  double best = -1.0;
+  double best = -1.0, bval = 0.0;
   int64_t bi = INT64_MAX;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    const double a = fabs(X[(int64_t)c * n + r]);
-    if (a > best || (a == best && r < bi)) { best = a; bi = r; }
+    const double x = X[(int64_t)c * n + r];
+    const double a = fabs(x);
+    if (a > best || (a == best && r < bi)) { best = a; bi = r; bval = x; }
   }
-  __shared__ double sv[256];
+  __shared__ double sv[256], sx[256];
   __shared__ int64_t si[256];
   sv[threadIdx.x] = best;
+  sx[threadIdx.x] = bval;
   si[threadIdx.x] = bi;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -238,12 +244,13 @@ __global__ void colmax_partial_kernel(const double* __restrict__ X, int64_t n, i
       if (a > sv[threadIdx.x] || (a == sv[threadIdx.x] && i < si[threadIdx.x])) {
         sv[threadIdx.x] = a;
         si[threadIdx.x] = i;
+        sx[threadIdx.x] = sx[threadIdx.x + w];
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    pval[(int64_t)c * gridDim.x + blockIdx.x] = sv[0];
+    pval[(int64_t)c * gridDim.x + blockIdx.x] = sx[0];   // signed value of the best entry
     pidx[(int64_t)c * gridDim.x + blockIdx.x] = si[0];
   }
 }
@@ -253,14 +260,15 @@ __global__ void colsign_kernel(double* __restrict__ X, int64_t n, int ncols, int
   const int c = blockIdx.y;
   __shared__ double sgn;
   if (threadIdx.x == 0) {
-    double best = -1.0;
+    double best = -1.0, bval = 0.0;
     int64_t bi = INT64_MAX;
     for (int p = 0; p < nparts; ++p) {
-      const double a = pval[(int64_t)c * nparts + p];
+      const double x = pval[(int64_t)c * nparts + p];
+      const double a = fabs(x);
       const int64_t i = pidx[(int64_t)c * nparts + p];
-      if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+      if (a > best || (a == best && i < bi)) { best = a; bi = i; bval = x; }
     }
-    sgn = (bi < n && X[(int64_t)c * n + bi] < 0.0) ? -1.0 : 1.0;
+    sgn = bval < 0.0 ? -1.0 : 1.0;
   }
   __syncthreads();
   if (sgn > 0.0) return;

@@ -39,6 +39,7 @@ struct SemiExt {
   cudaStream_t copy = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr}, done = nullptr;
   int timeout_ms = 60000;
+  bool direct = false;   // kernels read the pinned panels through their device mapping
   bool pending = false;  // a previous call returned FE_ERR_TIMEOUT with work in flight
 };
 
@@ -88,6 +89,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
   h->sx = sx;
   h->semi_external = 1;
   sx->timeout_ms = o.copy_timeout_ms > 0 ? o.copy_timeout_ms : 60000;
+  sx->direct = o.semi_direct != 0;
   // cut panels: packed size <= target and nnz <= panel_nnz
   // hub partials + slack
   const size_t reserve = 16 * 8 * (size_t)std::min<int64_t>(max_hub_tasks, 1 << 20) + (64 << 10);
@@ -174,7 +176,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
   }
   plans.clear();
   sx->dbuf_bytes = maxbytes;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 2 && !sx->direct; ++k) {
     e = cudaMalloc(&sx->dbuf[k], maxbytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -183,7 +185,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
     }
   }
   FE_TRY(sx->partials.alloc(16 * 8 * (size_t)std::max<int64_t>(maxhub, 1)));
-  h->device_bytes = 2 * (int64_t)maxbytes + (int64_t)sx->partials.bytes;
+  h->device_bytes = (sx->direct ? 0 : 2 * (int64_t)maxbytes) + (int64_t)sx->partials.bytes;
   FE_CUDA(cudaStreamCreateWithFlags(&sx->copy, cudaStreamNonBlocking));
   for (int k = 0; k < 2; ++k) {
     FE_CUDA(cudaEventCreateWithFlags(&sx->copied[k], cudaEventDisableTiming));
@@ -202,12 +204,18 @@ int semiext_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStrea
   for (size_t p = 0; p < sx->panels.size(); ++p) {
     const PanelInfo& pi = sx->panels[p];
     const int k = (int)(p & 1);
-    // the buffer is free once the kernels of panel p-2 are done
-    FE_CUDA(cudaStreamWaitEvent(sx->copy, sx->consumed[k], 0));
-    FE_CUDA(cudaMemcpyAsync(sx->dbuf[k], sx->pinned + pi.host_off, pi.bytes, cudaMemcpyHostToDevice, sx->copy));
-    FE_CUDA(cudaEventRecord(sx->copied[k], sx->copy));
-    FE_CUDA(cudaStreamWaitEvent(s, sx->copied[k], 0));
-    const char* base = static_cast<const char*>(sx->dbuf[k]);
+    const char* base;
+    if (sx->direct) {
+      // pinned memory is mapped into the device address space (unified addressing)
+      base = sx->pinned + pi.host_off;
+    } else {
+      // the buffer is free once the kernels of panel p-2 are done
+      FE_CUDA(cudaStreamWaitEvent(sx->copy, sx->consumed[k], 0));
+      FE_CUDA(cudaMemcpyAsync(sx->dbuf[k], sx->pinned + pi.host_off, pi.bytes, cudaMemcpyHostToDevice, sx->copy));
+      FE_CUDA(cudaEventRecord(sx->copied[k], sx->copy));
+      FE_CUDA(cudaStreamWaitEvent(s, sx->copied[k], 0));
+      base = static_cast<const char*>(sx->dbuf[k]);
+    }
     PlanView v;
     memset(&v, 0, sizeof(v));
     v.colidx = reinterpret_cast<const int32_t*>(base + pi.off_colidx);

@@ -10,7 +10,8 @@ import time
 
 import numpy as np
 
-from . import Csr, eigs, mlp_adam, mlp_loss_grad, mlp_param_count, vertex_features
+from . import (Csr, eigs, mlp_adam, mlp_loss_grad, mlp_param_count, mlp_span_loss_grad,
+               mlp_subspace_loss_grad, vertex_features)
 
 NFEAT = 8
 
@@ -39,9 +40,22 @@ def make_example(graph, b: int, feature_seed: int = 1, tol: float = 1e-6, nblock
     return F, U
 
 
+def make_subspace_example(graph, nev: int = 8, block: int = 4, feature_seed: int = 1,
+                          tol: float = 1e-6, nblocks: int = 8, first: int = 0):
+    """(features, targets) with targets = the wanted Ritz vectors first .. nev-1 (an orthonormal
+    basis of part of the wanted invariant subspace), for the subspace and span losses."""
+    import torch
+    with Csr.from_graph(graph) as h:
+        F = vertex_features(h, feature_seed)
+        _, X, _ = eigs(h, nev, block, nblocks, tol, "LM", mode="mixed", seed=feature_seed)
+    return F, X[:, first:nev].to(torch.float32).contiguous()
+
+
 def train(examples, hidden: int = 64, b: int = 4, steps: int = 400, lr: float = 3e-3,
-          seed: int = 0, log_every: int = 0):
-    """Adam on the full-batch loss, cycling through the examples.  Returns (params, losses)."""
+          seed: int = 0, log_every: int = 0, loss: str = "column"):
+    """Adam on the full-batch loss, cycling through the examples.  Returns (params, losses).
+    loss = "column" (output j against target j), "subspace" (each output against span(U)) or
+    "span" (span(Z) against span(U))."""
     import torch
     p = torch.from_numpy(init_params(hidden, b, seed)).cuda()
     m = torch.zeros_like(p)
@@ -50,7 +64,12 @@ def train(examples, hidden: int = 64, b: int = 4, steps: int = 400, lr: float = 
     losses = []
     for t in range(1, steps + 1):
         F, U = examples[(t - 1) % len(examples)]
-        L, _ = mlp_loss_grad(F, p, hidden, b, U, g)
+        if loss == "subspace":
+            L, _ = mlp_subspace_loss_grad(F, p, hidden, b, U, g)
+        elif loss == "span":
+            L, _ = mlp_span_loss_grad(F, p, hidden, b, U, g)
+        else:
+            L, _ = mlp_loss_grad(F, p, hidden, b, U, g)
         losses.append(L)
         mlp_adam(p, g, m, v, t, lr=lr)
         if log_every and t % log_every == 0:

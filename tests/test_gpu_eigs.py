@@ -125,3 +125,51 @@ def test_eigs_rmat22_full_size():
     _check_pairs(g, ev, X, 1e-8, ev[0])
     _check_pairs(g, ev2, X2, 1e-8, ev2[0])
     assert np.allclose(ev, ev2, rtol=1e-8)
+
+
+@pytest.mark.parametrize("nev,b,nb,which", [(4, 1, 12, "LM"), (8, 8, 4, "LA"), (16, 16, 3, "LM"),
+                                            (3, 2, 9, "SA")])
+def test_eigs_block_sizes_match_dense(nev, b, nb, which):
+    g = graphgen.rmat(12, seed=7)
+    lam = np.linalg.eigvalsh(g.dense())
+    want = lam[bks.sort_order(lam, which)][:nev]
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, nev, b, nb, 1e-9, which, seed=2, max_restarts=3000)
+    scale = np.abs(lam).max()
+    assert np.allclose(ev, want, rtol=1e-8, atol=1e-10 * scale)
+    _check_pairs(g, ev, X, 1e-9, scale)
+
+
+def test_mixed_block8_subspace64_matches_oracle():
+    """The mixed-precision configuration's shape (block 8, 8 blocks) on a small graph."""
+    g = graphgen.rmat(13, seed=3)
+    ref = bks.block_krylov_schur(g.rowptr, g.colidx, 8, 8, 8, 1e-8, "LM", seed=1)
+    with fe.Csr.from_graph(g) as h:
+        ev, X, st = fe.eigs(h, 8, 8, 8, 1e-8, "LM", mode="mixed", seed=1)
+    assert st["converged"] and st["spmm_blocks_fp32"] > 0
+    assert np.allclose(ev, ref.evals, rtol=1e-8)
+    _check_pairs(g, ev, X, 1e-8, ref.evals[0])
+
+
+def test_mixed_on_semi_external_matrix():
+    g = graphgen.rmat(14, seed=1)
+    ref = bks.block_krylov_schur(g.rowptr, g.colidx, 8, 4, 8, 1e-8, "LM", seed=1)
+    with fe.Csr.from_graph(g, device_mem_cap_bytes=1 << 20) as hs:
+        ev, X, st = fe.eigs(hs, 8, 4, 8, 1e-8, "LM", mode="mixed", seed=1)
+    assert np.allclose(ev, ref.evals, rtol=1e-8)
+    _check_pairs(g, ev, X, 1e-8, ref.evals[0])
+
+
+def test_output_vectors_orthonormal_every_time():
+    """Regression: the sign normalisation must not race with its own flips (n = 32768 gives
+    64 reduction blocks per column); every output must be orthonormal with a positive
+    largest-magnitude entry, on repeated solves."""
+    g = graphgen.rmat(15, seed=2)
+    with fe.Csr.from_graph(g) as h:
+        for rep in range(4):
+            ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1 + rep, max_restarts=0,
+                                raise_on_noconverge=False)
+            Xh = X.cpu().numpy()
+            assert np.abs(Xh.T @ Xh - np.eye(8)).max() < 1e-12
+            idx = np.argmax(np.abs(Xh), axis=0)
+            assert np.all(Xh[idx, np.arange(8)] > 0)

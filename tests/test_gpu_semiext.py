@@ -17,14 +17,15 @@ def g16():
     return graphgen.rmat(16, seed=5)
 
 
+@pytest.mark.parametrize("direct", [False, True])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("b", [1, 4, 16])
-def test_semiext_equals_resident_and_oracle(g16, prec, b):
+def test_semiext_equals_resident_and_oracle(g16, prec, b, direct):
     X = graphgen.normal_block(g16.n, b, seed=b, dtype=np.float32 if prec == "f32" else np.float64)
     Xd = to_dev(X)
     with fe.Csr.from_graph(g16) as hr:
         Yr = fe.spmm(hr, Xd).cpu().numpy()
-    with fe.Csr.from_graph(g16, device_mem_cap_bytes=3 << 20) as hs:
+    with fe.Csr.from_graph(g16, device_mem_cap_bytes=3 << 20, semi_direct=direct) as hs:
         info = hs.info()
         Ys = fe.spmm(hs, Xd).cpu().numpy()
     assert info["semi_external"] == 1 and info["panels"] > 2
@@ -43,11 +44,12 @@ def test_semiext_small_panels_and_hubs():
     assert_spmm_close(g, X, Y, 1e-13)
 
 
-def test_semiext_eigs_matches_resident():
+@pytest.mark.parametrize("direct", [False, True])
+def test_semiext_eigs_matches_resident(direct):
     g = graphgen.rmat(14, seed=1)
     with fe.Csr.from_graph(g) as hr:
         ev_r, _, st_r = fe.eigs(hr, 8, 4, 8, 1e-8, "LM", seed=1)
-    with fe.Csr.from_graph(g, device_mem_cap_bytes=1 << 20) as hs:
+    with fe.Csr.from_graph(g, device_mem_cap_bytes=1 << 20, semi_direct=direct) as hs:
         assert hs.info()["semi_external"] == 1
         ev_s, X, st_s = fe.eigs(hs, 8, 4, 8, 1e-8, "LM", seed=1)
     assert np.allclose(ev_s, ev_r, rtol=1e-12) and st_s["restarts"] == st_r["restarts"]
@@ -81,3 +83,22 @@ def test_semiext_wait_bound_returns_timeout_then_result_completes():
         assert b"not done" in lib.fe_last_error()
         t.cuda.synchronize()
         assert_spmm_close(g, X, Y.cpu().numpy(), 1e-13)
+
+
+@pytest.mark.slow
+def test_semiext_full_size_sampled_rows():
+    """R-MAT scale 22 streamed in panels under a 256 MB cap (the bench's semi-external leg),
+    checked on sampled rows plus every hub row, and A 1 = degree exactly."""
+    t = torch()
+    g = graphgen.rmat(22, seed=1)
+    X = graphgen.normal_block(g.n, 4, seed=11, dtype=np.float32)
+    with fe.Csr.from_graph(g, device_mem_cap_bytes=256 << 20) as hs:
+        assert hs.info()["panels"] > 2
+        Y = fe.spmm(hs, to_dev(X)).cpu().numpy()
+        ones = t.ones((g.n, 1), dtype=t.float64, device="cuda")
+        deg = fe.spmm(hs, ones)[:, 0].cpu().numpy()
+    assert np.array_equal(deg, g.degrees().astype(np.float64))
+    d = g.degrees()
+    rows = np.unique(np.concatenate([np.random.default_rng(1).integers(0, g.n, 20000),
+                                     np.nonzero(d > 4096)[0]]))
+    assert_spmm_close(g, X, Y, 1e-6, rows=rows)
