@@ -265,6 +265,10 @@ typedef struct {
   int mlp_hidden;         /* hidden width of that MLP: 32 or 64 (64) */
   double mixed_tol;       /* FP32-phase tolerance in mixed mode (5e-6) */
   int max_sweeps;         /* Jacobi sweeps per Rayleigh-Ritz (60) */
+  int orth_pass1;         /* FP64 subspace, first Gram-Schmidt pass: 0 = its Gram in FP32
+                             arithmetic (the FP64 second pass restores full orthogonality, and
+                             the coefficients actually subtracted enter H, so the Krylov
+                             relation keeps FP64 accuracy), 1 = in FP64 (0) */
 } fe_eigs_opts;
 
 void fe_eigs_opts_default(fe_eigs_opts* opts);

@@ -172,9 +172,10 @@ def random_normal(n: int, b: int, dtype=None, seed: int = 1, stream: int = 4, of
 def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: str = "LM", *,
          mode: str = "fp64", start=None, seed: int = 1, max_restarts: int = 500,
          mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 5e-6,
-         return_vectors: bool = True, raise_on_noconverge: bool = True):
+         orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True):
     """Block Krylov-Schur (fe_eigs_ex).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
-    None, stats dict)."""
+    None, stats dict).  orth_pass1: "fp32" or "fp64" arithmetic for the first Gram-Schmidt
+    pass's Gram on an FP64 subspace."""
     torch = _torch()
     lib = load()
     o = _lib.EigsOpts()
@@ -183,6 +184,7 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
     o.max_restarts = int(max_restarts)
     o.mode = _lib.MODE[mode]
     o.mixed_tol = float(mixed_tol)
+    o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
     o.mlp_hidden = int(mlp_hidden)
     if start is not None:
         start = start.to(torch.float64).contiguous()

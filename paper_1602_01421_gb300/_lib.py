@@ -43,7 +43,8 @@ class EigsOpts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_restarts", ctypes.c_int), ("mode", ctypes.c_int),
                 ("start", ctypes.c_int), ("start_block", ctypes.c_void_p),
                 ("mlp_weights", ctypes.c_void_p), ("mlp_hidden", ctypes.c_int),
-                ("mixed_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int)]
+                ("mixed_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
+                ("orth_pass1", ctypes.c_int)]
 
 
 class EigsStats(ctypes.Structure):

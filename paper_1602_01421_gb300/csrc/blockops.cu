@@ -2,10 +2,11 @@
 //
 //   gram     MvTransMv ("op3"): G = alpha V^T W.  Two phases as in Section 3.4.2 (each CTA
 //            reduces its row ranges to a small partial matrix, then one pass adds the partials
-//            in CTA order -- deterministic, no atomics).  Inside a CTA a range of W rows is
-//            staged in shared memory once; each warp owns one (block j, column group) output
-//            tile and sweeps the range with lane = row, so every V element is read once,
-//            coalesced.
+//            in a fixed order -- deterministic, no atomics).  Inside a CTA a range of W rows is
+//            staged in shared memory once; each warp owns up to two (block j, column group)
+//            output tiles for the whole launch, sweeps every range with lane = row (four row
+//            loads in flight per lane) and reduces across lanes once at the end, so every V
+//            element is read once, coalesced.  The grid is as many CTAs as fit on the GPU.
 //   update   MvTimesMatAddMv ("op1") fused with MvScale1/2: W = beta W M + alpha V C; one
 //            thread per row, C and M in shared memory.
 //   combine  V_out = V Y (restart and Ritz vectors: n x m times m x k).
@@ -64,97 +65,204 @@ __device__ __forceinline__ void load_vrow(const T* __restrict__ base, int ld, in
 }
 
 // ---------------------------------------------------------------- gram
+// Rows [r, r + rows) of tile (j, q0) of V_j^T W from the staged W rows sW (lane = row, four
+// row loads in flight per lane when the block is narrow).  Products and sums in TC (T, or
+// float for FP64 blocks when only a first-pass estimate is wanted).
+template <typename T, typename TC, int BV, int NQ>
+__device__ __forceinline__ void gram_tile_rows(const T* __restrict__ vb, int ldv, int64_t r0, int rows,
+                                               const TC* sW, int bw, int q0, int lane, TC (&acc)[BV][NQ]) {
+  constexpr int U = BV >= 16 ? 1 : (BV >= 8 ? 2 : 4);
+  int r = lane;
+  for (; r + 32 * (U - 1) < rows; r += 32 * U) {
+    T v[U][BV];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_vrow<T, BV>(vb, ldv, r0 + r + 32 * u, v[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const TC* w = sW + (r + 32 * u) * bw + q0;
+#pragma unroll
+      for (int p = 0; p < BV; ++p)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[p][q] = fma((TC)v[u][p], w[q], acc[p][q]);
+    }
+  }
+  for (; r < rows; r += 32) {
+    T v[BV];
+    load_vrow<T, BV>(vb, ldv, r0 + r, v);
+    const TC* w = sW + r * bw + q0;
+#pragma unroll
+    for (int p = 0; p < BV; ++p)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[p][q] = fma((TC)v[p], w[q], acc[p][q]);
+  }
+}
+
 template <typename T, int BV, int NQ>
+__device__ __forceinline__ void gram_tile_flush(T (&acc)[BV][NQ], double* sP, int row0, int bw, int q0,
+                                                int lane) {
+#pragma unroll
+  for (int p = 0; p < BV; ++p)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double a = (double)acc[p][q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFullMask, a, off);
+      if (lane == 0) sP[(row0 + p) * bw + q0 + q] += a;
+      acc[p][q] = T(0);
+    }
+}
+
+// Output tiles are (block j, NQ columns of W).  TPW > 0: warp w owns tiles w + 8t (t < TPW) for
+// the whole launch and reduces its accumulators across lanes once, at the end; TPW == 0 (more
+// tiles than that): tiles are dealt out per staged range and reduced per range.
+template <typename T, int BV, int NQ, int TPW, typename TC = T>
 __global__ void __launch_bounds__(256) gram_kernel(const BlockSet V, const T* __restrict__ W,
                                                    int ldw, int bw, int64_t n, int R,
                                                    double* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sW = reinterpret_cast<T*>(smem_raw);
-  double* sP = reinterpret_cast<double*>(smem_raw + (((size_t)R * bw * sizeof(T) + 15) & ~(size_t)15));
+  TC* sW = reinterpret_cast<TC*>(smem_raw);
+  double* sP = reinterpret_cast<double*>(smem_raw + (((size_t)R * bw * sizeof(TC) + 15) & ~(size_t)15));
   const int nout = V.nv * BV * bw;
   for (int e = threadIdx.x; e < nout; e += blockDim.x) sP[e] = 0.0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarps = 8;
   const int qtiles = bw / NQ;
   const int ntiles = V.nv * qtiles;
+  constexpr int NT = TPW > 0 ? TPW : 1;
+  TC acc[NT][BV][NQ];
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+#pragma unroll
+    for (int p = 0; p < BV; ++p)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[t][p][q] = TC(0);
+  constexpr bool kSame = sizeof(T) == sizeof(TC);
+  const bool vec = kSame && ldw == bw && ((size_t)bw * sizeof(T)) % 16 == 0 &&
+                   (reinterpret_cast<uintptr_t>(W) & 15) == 0;
   for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < n; r0 += (int64_t)gridDim.x * R) {
     const int rows = (int)min((int64_t)R, n - r0);
     __syncthreads();
-    const int tot = rows * bw;
-    if (ldw == bw) {
-      const T* src = W + r0 * bw;
-      for (int e = threadIdx.x; e < tot; e += blockDim.x) sW[e] = src[e];
+    if (vec) {
+      const int4* src = reinterpret_cast<const int4*>(W + r0 * bw);
+      int4* dst = reinterpret_cast<int4*>(sW);
+      const int n16 = (int)(((size_t)rows * bw * sizeof(T)) / 16);
+      for (int e = threadIdx.x; e < n16; e += blockDim.x) dst[e] = src[e];
     } else {
-      for (int e = threadIdx.x; e < tot; e += blockDim.x) sW[e] = W[(r0 + e / bw) * ldw + e % bw];
+      const int tot = rows * bw;
+      for (int e = threadIdx.x; e < tot; e += blockDim.x) sW[e] = (TC)W[(r0 + e / bw) * ldw + e % bw];
     }
     __syncthreads();
-    for (int tile = warp; tile < ntiles; tile += nwarps) {
-      const int j = tile / qtiles, q0 = (tile % qtiles) * NQ;
-      const T* __restrict__ vb = reinterpret_cast<const T*>(V.blk[j]);
-      T acc[BV][NQ];
+    if (TPW > 0) {
 #pragma unroll
-      for (int p = 0; p < BV; ++p)
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[p][q] = T(0);
-      for (int r = lane; r < rows; r += 32) {
-        T v[BV];
-        load_vrow<T, BV>(vb, V.ld, r0 + r, v);
-        const T* w = sW + r * bw + q0;
-        T wq[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) wq[q] = w[q];
-#pragma unroll
-        for (int p = 0; p < BV; ++p)
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) acc[p][q] = fma(v[p], wq[q], acc[p][q]);
-      }
-#pragma unroll
-      for (int p = 0; p < BV; ++p)
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          double a = (double)acc[p][q];
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFullMask, a, off);
-          if (lane == 0) sP[(j * BV + p) * bw + q0 + q] += a;
+      for (int t = 0; t < NT; ++t) {
+        const int tile = warp + kWarps * t;
+        if (tile < ntiles) {
+          const int j = tile / qtiles, q0 = (tile % qtiles) * NQ;
+          gram_tile_rows<T, TC, BV, NQ>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r0, rows, sW, bw, q0, lane, acc[t]);
         }
+      }
+    } else {
+      for (int tile = warp; tile < ntiles; tile += kWarps) {
+        const int j = tile / qtiles, q0 = (tile % qtiles) * NQ;
+        gram_tile_rows<T, TC, BV, NQ>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r0, rows, sW, bw, q0, lane, acc[0]);
+        gram_tile_flush<TC, BV, NQ>(acc[0], sP, j * BV, bw, q0, lane);
+      }
+    }
+  }
+  if (TPW > 0) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int tile = warp + kWarps * t;
+      if (tile < ntiles) {
+        const int j = tile / qtiles, q0 = (tile % qtiles) * NQ;
+        gram_tile_flush<TC, BV, NQ>(acc[t], sP, j * BV, bw, q0, lane);
+      }
     }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nout; e += blockDim.x) partial[(int64_t)blockIdx.x * nout + e] = sP[e];
 }
 
+// G[e] = alpha * sum_c partial[c * nout + e]: one warp per output; lane l adds partials
+// l, l + 32, ... in order, then a fixed xor tree -- the same order on every call.
 __global__ void gram_reduce_kernel(const double* __restrict__ partial, int nctas, int nout,
                                    double alpha, double* __restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (e >= nout) return;
   double s = 0.0;
-  for (int c = 0; c < nctas; ++c) s += partial[(int64_t)c * nout + e];
-  G[e] = alpha * s;
+#pragma unroll 8
+  for (int c = lane; c < nctas; c += 32) s += partial[(int64_t)c * nout + e];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFullMask, s, off);
+  if (lane == 0) G[e] = alpha * s;
+}
+
+static int launch_gram_reduce(const double* part, int nctas, int nout, double alpha, double* G,
+                              cudaStream_t s) {
+  gram_reduce_kernel<<<(unsigned)ceil_div(nout, 8), 256, 0, s>>>(part, nctas, nout, alpha, G);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// Launches gram_kernel<T, BV, NQ, TPW> with as many CTAs as fit on the GPU at once (at most one
+// staged range each per pass), then the partial reduction.  scratch == nullptr: partials in
+// the pool's slot 0; otherwise in scratch (capacity doubles), the grid shrunk to fit.
+template <typename T, int BV, int NQ, int TPW, typename TC = T>
+static int launch_gram_tpw(const BlockSet& V, int64_t n, const T* W, int bw, int ldw, double alpha,
+                           double* G, double* scratch, size_t capacity, cudaStream_t s) {
+  const int nout = V.nv * BV * bw;
+  int R = (int)(16384 / ((size_t)bw * sizeof(TC)));
+  R = std::max(32, R - R % 32);
+  const size_t smem = (((size_t)R * bw * sizeof(TC) + 15) & ~(size_t)15) + (size_t)nout * sizeof(double);
+  FE_ARG(smem <= 200 * 1024, "gram: output too large (%d entries)", nout);
+  static int per_sm = 0;  // per instantiation (and per smem size class; re-queried when it grows)
+  static size_t per_sm_smem = 0;
+  static bool configured = false;
+  if (!configured) {
+    FE_CUDA(cudaFuncSetAttribute(gram_kernel<T, BV, NQ, TPW, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured = true;
+  }
+  if (per_sm == 0 || smem > per_sm_smem) {
+    int nb = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gram_kernel<T, BV, NQ, TPW, TC>, 256, smem));
+    per_sm = std::max(nb, 1);
+    per_sm_smem = smem;
+  }
+  int64_t nctas = std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm * num_sms());
+  nctas = std::max<int64_t>(nctas, 1);
+  double* part = scratch;
+  if (!part) {
+    part = small_scratch(0, (size_t)nctas * nout);
+    if (!part) return FE_ERR_OOM;
+  } else {
+    nctas = std::min<int64_t>(nctas, (int64_t)(capacity / (size_t)nout));
+    FE_ARG(nctas >= 1, "gram: scratch of %zu doubles cannot hold %d outputs", capacity, nout);
+  }
+  gram_kernel<T, BV, NQ, TPW, TC><<<(unsigned)nctas, 256, smem, s>>>(V, W, ldw, bw, n, R, part);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return launch_gram_reduce(part, (int)nctas, nout, alpha, G, s);
+}
+
+// Persistent accumulators when a warp's tiles fit in 32 32-bit registers.
+template <typename T, int BV, int NQ, typename TC = T>
+static int launch_gram_any(const BlockSet& V, int64_t n, const T* W, int bw, int ldw, double alpha,
+                           double* G, double* scratch, size_t capacity, cudaStream_t s) {
+  constexpr int kRegsPerTile = BV * NQ * (int)(sizeof(TC) / 4);
+  const int ntiles = V.nv * (bw / NQ);
+  if (ntiles <= 8 && kRegsPerTile <= 32)
+    return launch_gram_tpw<T, BV, NQ, (kRegsPerTile <= 32 ? 1 : 0), TC>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+  if (ntiles <= 16 && 2 * kRegsPerTile <= 32)
+    return launch_gram_tpw<T, BV, NQ, (2 * kRegsPerTile <= 32 ? 2 : 0), TC>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
+  return launch_gram_tpw<T, BV, NQ, 0, TC>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
 }
 
 template <typename T, int BV, int NQ>
 static int launch_gram(const BlockSet& V, int64_t n, const T* W, int bw, int ldw, double alpha,
                        double* G, cudaStream_t s) {
-  const int nout = V.nv * BV * bw;
-  int R = (int)(32768 / ((size_t)bw * sizeof(T)));
-  R = std::max(32, R - R % 32);
-  const size_t smem = (((size_t)R * bw * sizeof(T) + 15) & ~(size_t)15) + (size_t)nout * sizeof(double);
-  FE_ARG(smem <= 200 * 1024, "gram: output too large (%d entries)", nout);
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(gram_kernel<T, BV, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
-  int nctas = (int)std::min<int64_t>(ceil_div(n, R), 2 * num_sms());
-  nctas = std::max(nctas, 1);
-  double* part = small_scratch(0, (size_t)nctas * nout);
-  if (!part) return FE_ERR_OOM;
-  gram_kernel<T, BV, NQ><<<nctas, 256, smem, s>>>(V, W, ldw, bw, n, R, part);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
-  gram_reduce_kernel<<<(unsigned)ceil_div(nout, 128), 128, 0, s>>>(part, nctas, nout, alpha, G);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
-  return FE_OK;
+  return launch_gram_any<T, BV, NQ>(V, n, W, bw, ldw, alpha, G, nullptr, 0, s);
 }
 
 template <typename T, int BV>
@@ -196,6 +304,24 @@ int gram(const BlockSet& V, int64_t n, const void* W, int bw, int ldw, fe_dtype 
     }
   }
   return set_error(FE_ERR_INVALID, "gram: bv = %d not in {1,2,4,8,16}", V.bv);
+}
+
+// G = alpha V^T W for FP64 blocks with FP32 products and per-lane FP32 sums (partials combined in
+// FP64): an estimate with about 1e-6 relative error at HBM speed instead of the FP64 rate.  Only
+// for first-pass Gram-Schmidt coefficients, which a second FP64 pass corrects.  V blocks and W
+// are n x b with ld b.
+int gram_f32_arith(const BlockSet& V, int64_t n, const double* W, int b, double alpha, double* G,
+                   cudaStream_t s) {
+  FE_ARG(V.nv >= 1 && V.nv <= kMaxBlocks, "gram: nv = %d out of range", V.nv);
+  FE_ARG(V.bv == b, "gram: block width %d != %d", V.bv, b);
+  switch (b) {
+    case 1: return launch_gram_any<double, 1, 1, float>(V, n, W, b, b, alpha, G, nullptr, 0, s);
+    case 2: return launch_gram_any<double, 2, 2, float>(V, n, W, b, b, alpha, G, nullptr, 0, s);
+    case 4: return launch_gram_any<double, 4, 4, float>(V, n, W, b, b, alpha, G, nullptr, 0, s);
+    case 8: return launch_gram_any<double, 8, 4, float>(V, n, W, b, b, alpha, G, nullptr, 0, s);
+    case 16: return launch_gram_any<double, 16, 2, float>(V, n, W, b, b, alpha, G, nullptr, 0, s);
+  }
+  return set_error(FE_ERR_INVALID, "gram: b = %d not in {1,2,4,8,16}", b);
 }
 
 // ---------------------------------------------------------------- update
@@ -510,26 +636,8 @@ template <typename T, int BV, int NQ>
 static int launch_gram_scratch(const BlockSet& V, int64_t n, const T* W, int bw, int ldw,
                                double alpha, double* G, double* scratch, size_t capacity,
                                cudaStream_t s) {
-  const int nout = V.nv * BV * bw;
-  int R = (int)(32768 / ((size_t)bw * sizeof(T)));
-  R = std::max(32, R - R % 32);
-  const size_t smem = (((size_t)R * bw * sizeof(T) + 15) & ~(size_t)15) + (size_t)nout * sizeof(double);
-  FE_ARG(smem <= 200 * 1024, "gram: output too large (%d entries)", nout);
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(gram_kernel<T, BV, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
-  int64_t nctas = std::min<int64_t>(ceil_div(n, R), 2 * num_sms());
-  nctas = std::min<int64_t>(nctas, (int64_t)(capacity / (size_t)nout));
-  FE_ARG(nctas >= 1, "gram: scratch of %zu doubles cannot hold %d outputs", capacity, nout);
-  gram_kernel<T, BV, NQ><<<(unsigned)nctas, 256, smem, s>>>(V, W, ldw, bw, n, R, scratch);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
-  gram_reduce_kernel<<<(unsigned)ceil_div(nout, 128), 128, 0, s>>>(scratch, (int)nctas, nout, alpha, G);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
-  return FE_OK;
+  FE_ARG(scratch != nullptr, "gram: NULL scratch");
+  return launch_gram_any<T, BV, NQ>(V, n, W, bw, ldw, alpha, G, scratch, capacity, s);
 }
 
 template <typename T, int BV>
@@ -581,10 +689,12 @@ namespace fe {
 // ---------------------------------------------------------------- fused update + Gram
 // One sweep over the rows: W[r] = beta (W[r] M) + alpha sum_j V_j[r] C_j (thread per row, as
 // update_kernel), then the Gram partials of [V_0 .. V_{nv-1}, W_new]^T W_new (only of W_new^T
-// W_new when gram_v == 0), accumulated per CTA like gram_kernel.  Phase A leaves the tile's new
-// W rows in shared memory; phase B re-reads the tile's V rows, which phase A has just pulled
-// into L1, so V comes from DRAM once for both operations.
-template <typename T, int BV, int BW>
+// W_new when gram_v == 0), accumulated per CTA like gram_kernel.  Phase A leaves the range's
+// new W rows in shared memory (two buffers, so one barrier per range suffices); phase B re-reads
+// the range's V rows, which phase A has just pulled into L1, so V comes from DRAM once for both
+// operations.  Gram tiles are the V blocks then W_new; TPW > 0: warp w owns tiles w + 8t for the
+// whole launch and reduces once at the end; TPW == 0: tiles are reduced per range.
+template <typename T, int BV, int BW, int TPW>
 __global__ void __launch_bounds__(256) update_gram_kernel(const BlockSet V, const double* __restrict__ C,
                                                           double alpha, double beta,
                                                           const double* __restrict__ M,
@@ -593,132 +703,191 @@ __global__ void __launch_bounds__(256) update_gram_kernel(const BlockSet V, cons
                                                           double* __restrict__ partial) {
   if (skip && *skip) return;
   constexpr int R = 256;
+  constexpr int kWarps = 8;
+  constexpr int NR = BV > BW ? BV : BW;
+  constexpr int NT = TPW > 0 ? TPW : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k = V.nv * BV;
   T* sC = reinterpret_cast<T*>(smem_raw);
   T* sM = sC + (size_t)k * BW;
-  T* sW = sM + BW * BW;
-  double* sP = reinterpret_cast<double*>(smem_raw + ((((size_t)k * BW + BW * BW + (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15));
+  T* sW = sM + BW * BW;  // two buffers of R x BW
+  double* sP = reinterpret_cast<double*>(smem_raw + ((((size_t)k * BW + BW * BW + 2 * (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15));
   const int gblocks = gram_v ? V.nv + 1 : 1;  // Gram row blocks: the V blocks (if any), then W
   const int nout = (gram_v ? k : 0) * BW + BW * BW;
   for (int e = threadIdx.x; e < k * BW; e += blockDim.x) sC[e] = (T)(alpha * C[e]);
   if (M)
     for (int e = threadIdx.x; e < BW * BW; e += blockDim.x) sM[e] = (T)(beta * M[e]);
   for (int e = threadIdx.x; e < nout; e += blockDim.x) sP[e] = 0.0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < n; r0 += (int64_t)gridDim.x * R) {
-    __syncthreads();  // coefficients loaded / previous tile's sW consumed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T acc[NT][NR][BW];
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+#pragma unroll
+    for (int p = 0; p < NR; ++p)
+#pragma unroll
+      for (int q = 0; q < BW; ++q) acc[t][p][q] = T(0);
+  __syncthreads();  // coefficients loaded
+  int buf = 0;
+  for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < n; r0 += (int64_t)gridDim.x * R, buf ^= 1) {
     const int rows = (int)min((int64_t)R, n - r0);
-    // phase A: update (thread per row)
+    T* sWb = sW + buf * R * BW;
+    // phase A: update (thread per row), V rows four blocks at a time
     if ((int)threadIdx.x < rows) {
       const int64_t r = r0 + threadIdx.x;
-      T acc[BW];
+      T a[BW];
       if (beta == 0.0) {
 #pragma unroll
-        for (int q = 0; q < BW; ++q) acc[q] = T(0);
+        for (int q = 0; q < BW; ++q) a[q] = T(0);
       } else {
         T w[BW];
         ld_row_rw<T, BW>(W + r * BW, w);
         if (M) {
 #pragma unroll
           for (int q = 0; q < BW; ++q) {
-            T a = T(0);
+            T x = T(0);
 #pragma unroll
-            for (int p = 0; p < BW; ++p) a = fma(w[p], sM[p * BW + q], a);
-            acc[q] = a;
+            for (int p = 0; p < BW; ++p) x = fma(w[p], sM[p * BW + q], x);
+            a[q] = x;
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < BW; ++q) acc[q] = (T)beta * w[q];
+          for (int q = 0; q < BW; ++q) a[q] = (T)beta * w[q];
         }
       }
-      for (int j = 0; j < V.nv; ++j) {
-        T v[BV];
-        load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r, v);
-        const T* c = sC + j * BV * BW;
+      constexpr int UJ = BV >= 8 ? 2 : 4;
+      for (int j0 = 0; j0 < V.nv; j0 += UJ) {
+        T v[UJ][BV];
 #pragma unroll
-        for (int p = 0; p < BV; ++p)
+        for (int u = 0; u < UJ; ++u)
+          if (j0 + u < V.nv) load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j0 + u]), V.ld, r, v[u]);
 #pragma unroll
-          for (int q = 0; q < BW; ++q) acc[q] = fma(v[p], c[p * BW + q], acc[q]);
+        for (int u = 0; u < UJ; ++u) {
+          if (j0 + u < V.nv) {
+            const T* c = sC + (j0 + u) * BV * BW;
+#pragma unroll
+            for (int p = 0; p < BV; ++p)
+#pragma unroll
+              for (int q = 0; q < BW; ++q) a[q] = fma(v[u][p], c[p * BW + q], a[q]);
+          }
+        }
       }
-      st_row<T, BW>(W + r * BW, acc);
+      st_row<T, BW>(W + r * BW, a);
 #pragma unroll
-      for (int q = 0; q < BW; ++q) sW[threadIdx.x * BW + q] = acc[q];
+      for (int q = 0; q < BW; ++q) sWb[threadIdx.x * BW + q] = a[q];
     }
     __syncthreads();
-    // phase B: Gram tiles (warp per row block, lane = row)
-    for (int tile = warp; tile < gblocks; tile += nwarps) {
+    // phase B: Gram tiles (warp per tile, lane = row)
+    auto sweep = [&](int tile, T (&ac)[NR][BW]) {
       const bool isW = tile == gblocks - 1;
-      const int j = tile;
-      constexpr int NR = BV > BW ? BV : BW;
-      T acc[NR][BW];
+      if (isW) {
+        for (int r = lane; r < rows; r += 32) {
+          T wq[BW];
 #pragma unroll
-      for (int p = 0; p < NR; ++p)
-#pragma unroll
-        for (int q = 0; q < BW; ++q) acc[p][q] = T(0);
-      for (int r = lane; r < rows; r += 32) {
-        T wq[BW];
-#pragma unroll
-        for (int q = 0; q < BW; ++q) wq[q] = sW[r * BW + q];
-        if (isW) {
+          for (int q = 0; q < BW; ++q) wq[q] = sWb[r * BW + q];
 #pragma unroll
           for (int p = 0; p < BW; ++p)
 #pragma unroll
-            for (int q = 0; q < BW; ++q) acc[p][q] = fma(wq[p], wq[q], acc[p][q]);
-        } else {
+            for (int q = 0; q < BW; ++q) ac[p][q] = fma(wq[p], wq[q], ac[p][q]);
+        }
+      } else {
+        const T* vb = reinterpret_cast<const T*>(V.blk[tile]);
+        for (int r = lane; r < rows; r += 32) {
           T v[BV];
-          load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r0 + r, v);
+          load_vrow<T, BV>(vb, V.ld, r0 + r, v);
+          T wq[BW];
+#pragma unroll
+          for (int q = 0; q < BW; ++q) wq[q] = sWb[r * BW + q];
 #pragma unroll
           for (int p = 0; p < BV; ++p)
 #pragma unroll
-            for (int q = 0; q < BW; ++q) acc[p][q] = fma(v[p], wq[q], acc[p][q]);
+            for (int q = 0; q < BW; ++q) ac[p][q] = fma(v[p], wq[q], ac[p][q]);
         }
       }
+    };
+    auto flush = [&](int tile, T (&ac)[NR][BW]) {
+      const bool isW = tile == gblocks - 1;
       const int np = isW ? BW : BV;
-      const int rowoff = isW ? (gram_v ? k : 0) : j * BV;
+      const int rowoff = isW ? (gram_v ? k : 0) : tile * BV;
 #pragma unroll
       for (int p = 0; p < NR; ++p) {
         if (p >= np) break;
 #pragma unroll
         for (int q = 0; q < BW; ++q) {
-          double a = (double)acc[p][q];
+          double x = (double)ac[p][q];
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFullMask, a, off);
-          if (lane == 0) sP[(rowoff + p) * BW + q] += a;
+          for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFullMask, x, off);
+          if (lane == 0) sP[(rowoff + p) * BW + q] += x;
+          ac[p][q] = T(0);
         }
       }
+    };
+    if (TPW > 0) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (warp + kWarps * t < gblocks) sweep(warp + kWarps * t, acc[t]);
+    } else {
+      for (int tile = warp; tile < gblocks; tile += kWarps) {
+        sweep(tile, acc[0]);
+        flush(tile, acc[0]);
+      }
+    }
+    if (r0 + (int64_t)gridDim.x * R >= n && TPW > 0) {
+      // last range of this CTA: reduce the persistent accumulators
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (warp + kWarps * t < gblocks) flush(warp + kWarps * t, acc[t]);
     }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nout; e += blockDim.x) partial[(int64_t)blockIdx.x * nout + e] = sP[e];
 }
 
+template <typename T, int BV, int BW, int TPW>
+static int launch_update_gram_tpw(const BlockSet& V, int64_t n, const double* C, double alpha,
+                                  double beta, const double* M, T* W, int gram_v, const int* skip,
+                                  double* G, cudaStream_t s) {
+  constexpr int R = 256;
+  const int k = V.nv * BV;
+  const int nout = (gram_v ? k : 0) * BW + BW * BW;
+  const size_t smem = ((((size_t)k * BW + BW * BW + 2 * (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15) +
+                      (size_t)nout * sizeof(double);
+  FE_ARG(smem <= 200 * 1024, "update_gram: coefficient matrix too large");
+  static bool configured = false;
+  static int per_sm = 0;
+  static size_t per_sm_smem = 0;
+  if (!configured) {
+    FE_CUDA(cudaFuncSetAttribute(update_gram_kernel<T, BV, BW, TPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured = true;
+  }
+  if (per_sm == 0 || smem > per_sm_smem) {
+    int nb = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_gram_kernel<T, BV, BW, TPW>, 256, smem));
+    per_sm = std::max(nb, 1);
+    per_sm_smem = smem;
+  }
+  int nctas = (int)std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm * num_sms());
+  nctas = std::max(nctas, 1);
+  double* part = small_scratch(0, (size_t)nctas * nout);
+  if (!part) return FE_ERR_OOM;
+  update_gram_kernel<T, BV, BW, TPW><<<nctas, 256, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, part);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return launch_gram_reduce(part, nctas, nout, 1.0, G, s);
+}
+
+// Persistent accumulators when a warp's tiles fit in 32 32-bit registers.
 template <typename T, int BV, int BW>
 static int launch_update_gram(const BlockSet& V, int64_t n, const double* C, double alpha,
                               double beta, const double* M, T* W, int gram_v, const int* skip,
                               double* G, cudaStream_t s) {
-  constexpr int R = 256;
-  const int k = V.nv * BV;
-  const int nout = (gram_v ? k : 0) * BW + BW * BW;
-  const size_t smem = ((((size_t)k * BW + BW * BW + (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15) +
-                      (size_t)nout * sizeof(double);
-  FE_ARG(smem <= 200 * 1024, "update_gram: coefficient matrix too large");
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(update_gram_kernel<T, BV, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
-  int nctas = (int)std::min<int64_t>(ceil_div(n, R), 2 * num_sms());
-  nctas = std::max(nctas, 1);
-  double* part = small_scratch(0, (size_t)nctas * nout);
-  if (!part) return FE_ERR_OOM;
-  update_gram_kernel<T, BV, BW><<<nctas, 256, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, part);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
-  gram_reduce_kernel<<<(unsigned)ceil_div(nout, 128), 128, 0, s>>>(part, nctas, nout, 1.0, G);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
-  return FE_OK;
+  constexpr int NR = BV > BW ? BV : BW;
+  constexpr int kRegsPerTile = NR * BW * (int)(sizeof(T) / 4);
+  const int gblocks = gram_v ? V.nv + 1 : 1;
+  if (gblocks <= 8 && kRegsPerTile <= 32)
+    return launch_update_gram_tpw<T, BV, BW, (kRegsPerTile <= 32 ? 1 : 0)>(V, n, C, alpha, beta, M, W, gram_v, skip, G, s);
+  if (gblocks <= 16 && 2 * kRegsPerTile <= 32)
+    return launch_update_gram_tpw<T, BV, BW, (2 * kRegsPerTile <= 32 ? 2 : 0)>(V, n, C, alpha, beta, M, W, gram_v, skip, G, s);
+  return launch_update_gram_tpw<T, BV, BW, 0>(V, n, C, alpha, beta, M, W, gram_v, skip, G, s);
 }
 
 // W = beta W M + alpha V C; G = [V; W]^T W (gram_v) or W^T W, rows (j*b + p) then W's b rows.

@@ -33,7 +33,7 @@ namespace fe {
 
 int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
             int update_anorm, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
-            double* d_R, int ldr, int* replaced, cudaStream_t s);
+            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32);
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
                 double* theta, double* Y, double* rho, int* info, cudaStream_t s);
 int launch_restart_h(double* H, int m, int b, int k, const double* theta, const double* Y,
@@ -73,6 +73,7 @@ struct Phase {
   fe_dtype dt;
   uint64_t seed;
   int max_restarts, max_sweeps;
+  int pass1_f32 = 0;  // FP64 subspace: first Gram-Schmidt pass's Gram in FP32 arithmetic
   int stagnation_window = 0;  // > 0: stop when the worst wanted rho/scale has not improved
                               // by 10% over this many restarts (FP32 phase)
   cudaStream_t s;
@@ -130,7 +131,7 @@ struct Phase {
     BlockSet none = blockset_of({}, b, b);
     // the start block's column norms seed the ||A|| scale (update_anorm = 1)
     FE_TRY(orth_ex(none, n, slot[0], b, dt, anorm, 1, seed, &rng_counter, nullptr, b, gtmp, b,
-                   &replacements, s));
+                   &replacements, s, pass1_f32));
     return FE_OK;
   }
 
@@ -140,7 +141,7 @@ struct Phase {
       ++spmm_blocks;
       BlockSet V = slots(0, j + 1);
       FE_TRY(orth_ex(V, n, slot[j + 1], b, dt, anorm, 1, seed, &rng_counter, H + (size_t)j * b, m,
-                     H + (size_t)(j + 1) * b * m + (size_t)j * b, m, &replacements, s));
+                     H + (size_t)(j + 1) * b * m + (size_t)j * b, m, &replacements, s, pass1_f32));
     }
     return FE_OK;
   }
@@ -339,6 +340,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
   FE_ARG(o.start != FE_START_LEARNED || o.mlp_weights, "fe_eigs: FE_START_LEARNED needs mlp_weights");
   if (o.max_restarts < 0) o.max_restarts = 0;
   if (o.max_sweeps <= 0) o.max_sweeps = 60;
+  FE_ARG(o.orth_pass1 == 0 || o.orth_pass1 == 1, "fe_eigs: orth_pass1 = %d not 0 or 1", o.orth_pass1);
   cudaStream_t s = cur_stream();
   const int m = block * nblocks;
 
@@ -364,6 +366,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
   p1.seed = o.seed;
   p1.max_restarts = o.max_restarts;
   p1.max_sweeps = o.max_sweeps;
+  p1.pass1_f32 = o.orth_pass1 == 0;
   p1.s = s;
   int rc;
   double secs32 = 0.0;
@@ -425,6 +428,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
     p2.seed = o.seed;
     p2.max_restarts = o.max_restarts;
     p2.max_sweeps = o.max_sweeps;
+    p2.pass1_f32 = o.orth_pass1 == 0;
     p2.s = s;
     p2.tol = tol;
     p2.dt = FE_F64;

@@ -27,6 +27,8 @@ int update_skip(const BlockSet& V, int64_t n, const double* C, double alpha, dou
 int update_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
                 const double* M, void* W, int b, fe_dtype dt, int gram_v, const int* skip,
                 double* G, cudaStream_t s);
+int gram_f32_arith(const BlockSet& V, int64_t n, const double* W, int b, double alpha, double* G,
+                   cudaStream_t s);
 
 constexpr double kRelPivot = 1e-6;      // pivot below 1e-6 * column norm: nearly dependent
 constexpr double kAbsBreakdown = 1e-12; // remainder below 1e-12 * ||A||: breakdown
@@ -248,7 +250,7 @@ static int orth_fallback(const BlockSet& V, int64_t n, void* W, int b, fe_dtype 
 
 int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
             int update_anorm, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
-            double* d_R, int ldr, int* replaced, cudaStream_t s) {
+            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32) {
   FE_ARG(V.nv >= 0 && V.nv + 1 <= kMaxBlocks, "orth: too many blocks");
   FE_ARG(b >= 1 && b <= 16, "orth: b = %d", b);
   const int k = V.nv * b;
@@ -268,8 +270,12 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   vx.push_back(W);
   BlockSet Vx = blockset_of(vx, b, b);
   FE_ARG(V.nv == 0 || V.bv == b, "orth: V block width %d != b %d", V.bv, b);
-  // pass 1: [G1; S1] = [V W]^T W
-  FE_TRY(gram(Vx, n, W, b, b, dt, 1.0, sG1, s));
+  // pass 1: [G1; S1] = [V W]^T W (FP64 blocks: optionally in FP32 arithmetic -- G1 only steers
+  // the first subtraction; pass 2 is FP64, and H receives G1 + G2, what was actually subtracted)
+  if (pass1_f32 && dt == FE_F64)
+    FE_TRY(gram_f32_arith(Vx, n, static_cast<const double*>(W), b, 1.0, sG1, s));
+  else
+    FE_TRY(gram(Vx, n, W, b, b, dt, 1.0, sG1, s));
   // the fused update + Gram sweeps hold a b x b accumulator per lane: b = 16 keeps two kernels
   const bool fused = b <= 8;
   if (V.nv > 0) {
@@ -315,7 +321,7 @@ int orth(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_an
          double anorm_floor, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
          double* d_R, int ldr, int* replaced, cudaStream_t s) {
   (void)anorm_floor;
-  return orth_ex(V, n, W, b, dt, d_anorm, 0, seed, rng_counter, d_G, ldg, d_R, ldr, replaced, s);
+  return orth_ex(V, n, W, b, dt, d_anorm, 0, seed, rng_counter, d_G, ldg, d_R, ldr, replaced, s, 0);
 }
 
 }  // namespace fe

@@ -72,3 +72,31 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.CsrInfo) == 88
     assert ctypes.sizeof(_lib.EigsOpts) == 64
     assert ctypes.sizeof(_lib.EigsStats) == 72
+
+
+def test_struct_field_offsets_match_c_compiler(tmp_path):
+    """Every ctypes field sits at the offset gcc gives the same field of include/fe.h."""
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    structs = {"fe_csr_opts": _lib.CsrOpts, "fe_csr_info": _lib.CsrInfo,
+               "fe_eigs_opts": _lib.EigsOpts, "fe_eigs_stats": _lib.EigsStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fe.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

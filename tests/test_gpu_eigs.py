@@ -43,15 +43,16 @@ def test_eigs_closed_form_spectra(case):
     _check_pairs(g, ev, X, 1e-10, scale)
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_eigs_rmat14_matches_oracle(mode):
+@pytest.mark.parametrize("mode,pass1", [("fp64", "fp32"), ("fp64", "fp64"), ("mixed", "fp32")])
+def test_eigs_rmat14_matches_oracle(mode, pass1):
     """The benchmark's small configuration: R-MAT scale 14, nev 8 LM, block 4, 8 blocks,
-    tol 1e-8, counter-RNG start (seed 1)."""
+    tol 1e-8, counter-RNG start (seed 1); the FP64 subspace with the first Gram-Schmidt pass's
+    Gram in FP32 or FP64 arithmetic."""
     g = graphgen.rmat(14, seed=1)
     ref = bks.block_krylov_schur(g.rowptr, g.colidx, 8, 4, 8, 1e-8, "LM", seed=1)
     assert ref.converged
     with fe.Csr.from_graph(g) as h:
-        ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode=mode, seed=1)
+        ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode=mode, seed=1, orth_pass1=pass1)
     assert st["converged"] and st["nconv"] == 8
     assert np.allclose(ev, ref.evals, rtol=1e-8, atol=0)
     _check_pairs(g, ev, X, 1e-8, ref.evals[0])
@@ -118,8 +119,8 @@ def test_eigs_rmat22_full_size():
     g = graphgen.rmat(22, seed=1)
     deg = g.degrees()
     with fe.Csr.from_graph(g) as h:
-        ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1)
-        ev2, X2, st2 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode="mixed", seed=1)
+        ev, X, st = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1, max_restarts=5000)
+        ev2, X2, st2 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode="mixed", seed=1, max_restarts=5000)
     assert st["converged"] and st2["converged"]
     assert deg.mean() <= ev[0] <= deg.max() and ev[0] >= np.sqrt(deg.max())
     _check_pairs(g, ev, X, 1e-8, ev[0])
@@ -173,3 +174,19 @@ def test_output_vectors_orthonormal_every_time():
             assert np.abs(Xh.T @ Xh - np.eye(8)).max() < 1e-12
             idx = np.argmax(np.abs(Xh), axis=0)
             assert np.all(Xh[idx, np.arange(8)] > 0)
+
+
+def test_fp32_first_pass_keeps_the_krylov_relation():
+    """With the first pass's Gram in FP32 arithmetic the FP64 solve still reaches residuals of
+    tol * ||A|| on a graph whose spectrum has a tight cluster (R-MAT scale 16), in about the
+    same number of restarts as the all-FP64 pass, with orthonormal vectors."""
+    g = graphgen.rmat(16, seed=2)
+    out = {}
+    with fe.Csr.from_graph(g) as h:
+        for p1 in ("fp32", "fp64"):
+            out[p1] = fe.eigs(h, 8, 4, 8, 1e-9, "LM", seed=1, orth_pass1=p1, max_restarts=5000)
+    (e32, X32, s32), (e64, X64, s64) = out["fp32"], out["fp64"]
+    assert s32["converged"] and s64["converged"]
+    assert np.allclose(e32, e64, rtol=1e-9, atol=0)
+    _check_pairs(g, e32, X32, 1e-9, abs(e64[0]))
+    assert s32["restarts"] <= 1.2 * s64["restarts"] + 5
