@@ -168,6 +168,19 @@ def time_cuda(fn, reps, torch):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+UGRAM_NV = 7
+
+
+def ugram_inputs(fe, torch, n):
+    """Inputs of the roofline launch: V = 7 FP64 blocks of n x 4 (the second classical
+    Gram-Schmidt pass against 7 blocks), C (28 x 4, small), W (n x 4)."""
+    Vg = fe.random_normal(UGRAM_NV * n, 4, dtype=torch.float64, seed=5).view(UGRAM_NV, n, 4)
+    Wg = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+    Cg = 1e-3 * torch.randn(UGRAM_NV * 4, 4, dtype=torch.float64, device=Wg.device,
+                            generator=torch.Generator(device=Wg.device).manual_seed(7))
+    return Vg, Cg, Wg
+
+
 def cpu_baseline(g, gpu_blocks, cycles=1):
     from oracle import bks
     t0 = time.perf_counter()
@@ -217,6 +230,14 @@ def run_ours(args):
             fe.block_gram(Vg, Wg)
         torch.cuda.synchronize()
         print(json.dumps({"only": "gram1", "n": n, "nv": 7, "b": 4}))
+        return
+    if args.only == "ugram1":
+        # one fused update + Gram launch at the FP64 solve's shape (7 blocks of n x 4)
+        Vg, Cg, Wg = ugram_inputs(fe, torch, n)
+        for _ in range(args.warmup + args.steps):
+            fe.block_update_gram(Vg, Cg, Wg, alpha=-1.0, beta=1.0)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "ugram1", "n": n, "nv": UGRAM_NV, "b": 4}))
         return
     if args.only == "spmm1":
         # one SpMM launch (for a single-kernel profiler capture)
@@ -292,24 +313,26 @@ def run_ours(args):
                               "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                               "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
                               "bytes_per_launch": spmm_bytes(n, nnz, 4, es)}
-    # dominant kernel of the FP64 solve (launch list): gram_kernel<double,4,4> at the solve's
-    # mean shape, 7 blocks of n x 4 (k + b = 28 columns) against n x 4
-    nvg = 7
-    Vg = fe.random_normal(nvg * n, 4, dtype=torch.float64, seed=5).view(nvg, n, 4)
-    Wg = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+    # dominant kernel of the FP64 solve (launch list): update_gram_kernel<double,4,4,1>, the
+    # fused second Gram-Schmidt pass, at the solve's shape (7 blocks of n x 4): W = W - V C
+    # (2 n 28 4 flops) and G = [V; W]^T W (2 n 32 4 flops); reads V and W, writes W
+    Vg, Cg, Wg = ugram_inputs(fe, torch, n)
     for _ in range(3):
-        fe.block_gram(Vg, Wg)
-    tg = statistics.median(time_cuda(lambda: fe.block_gram(Vg, Wg), 10, torch))
-    flops = 2.0 * n * nvg * 4 * 4
+        fe.block_update_gram(Vg, Cg, Wg, alpha=-1.0, beta=1.0)
+    tg = statistics.median(time_cuda(lambda: fe.block_update_gram(Vg, Cg, Wg, alpha=-1.0, beta=1.0),
+                                     10, torch))
+    k = UGRAM_NV * 4
+    flops = 2.0 * n * k * 4 + 2.0 * n * (k + 4) * 4
+    ubytes = 8 * n * (k + 2 * 4)
     gflops = flops / (tg / 1000.0) / 1e9
-    roofline = {"kernel": "gram_kernel<double,4,4> + gram_reduce_kernel (MvTransMv, FP64)",
+    roofline = {"kernel": "update_gram_kernel<double,4,4,1> + gram_reduce_kernel (op1 + op3 fused, FP64)",
                 "bound": "alu", "achieved": round(gflops, 1), "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
                 "peak_kind": "nominal FP64 rate (unit count x clock)", "traffic": args.traffic,
-                "flops_per_launch": flops, "bytes_per_launch": 8 * n * (nvg * 4 + 4),
-                "ms_per_launch": round(tg, 4),
-                "hbm_frac": round(8 * n * (nvg * 4 + 4) / (tg / 1000.0) / 1e9 / hbm_peak, 4)}
-    del Vg, Wg
+                "flops_per_launch": flops, "bytes_per_launch": ubytes,
+                "ms_per_launch": round(tg, 4), "stream": "torch current stream",
+                "hbm_frac": round(ubytes / (tg / 1000.0) / 1e9 / hbm_peak, 4)}
+    del Vg, Wg, Cg
 
     # ---- mixed-precision solve on the same graph (time to 8 eigenpairs)
     t_mixed = None
@@ -522,15 +545,17 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-semi", action="store_true")
 
-    # dram__bytes_read.sum + dram__bytes_write.sum of gram_kernel<double,4,4> at the roofline
-    # shape, one ncu capture (profiles/gram_f64_rmat22.md); update when that kernel changes
-    ap.add_argument("--traffic", type=float, default=1.073789e9 + 3.321856e6,
+    # dram__bytes_read.sum + dram__bytes_write.sum of update_gram_kernel<double,4,4,1> at the
+    # roofline shape, one ncu capture (profiles/update_gram_f64_rmat22.md); update when that
+    # kernel changes
+    ap.add_argument("--traffic", type=float, default=1.074065e9 + 126.431744e6,
                     help="ncu DRAM bytes per launch of the roofline kernel")
     ap.add_argument("--ref-cycles", type=int, default=1)
     ap.add_argument("--ref-solve-blocks", type=int, default=150)
     ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
-    ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1"],
-                    help="solve: warm-up + timed solves only; spmm1: SpMM launches only")
+    ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1", "ugram1"],
+                    help="solve: warm-up + timed solves only; spmm1 / gram1 / ugram1: launches "
+                         "of one kernel only (profiler captures)")
     ap.add_argument("--b", type=int, default=4)
     ap.add_argument("--solve-mode", default="fp64", choices=["fp64", "mixed"],
                     help="--only solve: which solve to run")

@@ -10,6 +10,7 @@
  *   fe_spmm                                              Y = A X   (Section 3.3.3)
  *   fe_block_gram                                        MvTransMv  (Table 1, "op3")
  *   fe_block_update                                      MvTimesMatAddMv (Table 1, "op1")
+ *   fe_block_update_gram                                 op1 then op3 on the result, one sweep
  *   fe_block_orth                                        re-orthogonalisation (Section 3.1)
  *   fe_random_normal                                     MvRandom (Table 1)
  *   fe_eigs / fe_eigs_ex                                 Block Krylov-Schur (Sections 1, 3.1)
@@ -179,6 +180,19 @@ int fe_block_gram_noalloc(const void* V, int64_t n, int nv, int bv, const void* 
  */
 int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,
                     double beta, void* W, int bw, fe_dtype dt);
+
+/*
+ * MvTimesMatAddMv followed by MvTransMv on its result (Table 1 "op1" then "op3"), the pair the
+ * second classical Gram-Schmidt pass of Section 3.1 issues, fused into one sweep over the rows:
+ *     W <- beta * W + alpha * V C,      G = [V_0; ...; V_{nv-1}; W]^T W   (W after the update)
+ * V: DEVICE, nv blocks of n x b (block after block); C: DEVICE FP64 row-major (nv*b) x b;
+ * W: DEVICE n x b, updated in place; G: DEVICE FP64 row-major ((nv+1)*b) x b, rows j*b + p
+ * for block j's column p, then W's b rows.  0 <= nv <= 32 (nv = 0: W = beta W, G = W^T W),
+ * b in {1, 2, 4, 8}.  W must not alias V.  Deterministic (fixed summation order).
+ * Errors: FE_ERR_INVALID, FE_ERR_OOM, FE_ERR_CUDA.
+ */
+int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* C, double alpha,
+                         double beta, void* W, fe_dtype dt, double* G);
 
 /*
  * Re-orthogonalisation step of the block Krylov expansion (Section 3.1 step (1)): block

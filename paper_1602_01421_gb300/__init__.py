@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import FeError, check, load
 
-__all__ = ["Csr", "spmm", "block_gram", "block_update", "block_orth", "random_normal", "eigs",
+__all__ = ["Csr", "spmm", "block_gram", "block_update", "block_update_gram", "block_orth", "random_normal", "eigs",
            "FeError", "load", "library_path"]
 
 library_path = _lib.LIB_PATH
@@ -141,6 +141,24 @@ def block_update(V, C, W, alpha: float = 1.0, beta: float = 1.0):
     check(load().fe_block_update(vp, n, nv, bv, cp, float(alpha), float(beta), _dev(W, "W"), bw,
                                  _dt(W)))
     return W
+
+
+def block_update_gram(V, C, W, alpha: float = 1.0, beta: float = 1.0, G=None):
+    """W = beta W + alpha V C, then G = [V; W]^T W (fe_block_update_gram).  V: (nv, n, b) or
+    None; C: float64 (nv*b, b); G: float64 ((nv+1)*b, b)."""
+    torch = _torch()
+    n, b = W.shape
+    if V is None:
+        nv, vp, cp = 0, None, None
+    else:
+        nv = V.shape[0]
+        vp, cp = _dev(V, "V"), _dev(C, "C")
+    if G is None:
+        G = torch.empty(((nv + 1) * b, b), dtype=torch.float64, device=W.device)
+    _stream()
+    check(load().fe_block_update_gram(vp, n, nv, b, cp, float(alpha), float(beta), _dev(W, "W"),
+                                      _dt(W), _dev(G, "G")))
+    return G
 
 
 def block_orth(V, W, anorm: float, seed: int = 1):

@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
             "fe_spmm": (i32, [vp, vp, vp, i32, i32]),
             "fe_block_gram": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_block_update": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, i32]),
+            "fe_block_update_gram": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, vp]),
             "fe_block_orth": (i32, [vp, i64, i32, i32, vp, i32, dbl, ctypes.c_uint64, vp, vp,
                                     ctypes.POINTER(i32)]),
             "fe_random_normal": (i32, [vp, i64, i32, i32, ctypes.c_uint64, ctypes.c_uint64,

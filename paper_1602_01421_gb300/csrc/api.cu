@@ -271,6 +271,25 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
   return update(vs, n, C, alpha, beta, nullptr, W, bw, bw, dt, cur_stream());
 }
 
+int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* C, double alpha,
+                         double beta, void* W, fe_dtype dt, double* G) {
+  FE_ARG(W && G, "fe_block_update_gram: NULL W or G");
+  FE_ARG(n >= 1, "fe_block_update_gram: n < 1");
+  FE_ARG(nv >= 0 && nv <= 32, "fe_block_update_gram: nv = %d not in [0, 32]", nv);
+  FE_ARG(nv == 0 || (V && C), "fe_block_update_gram: NULL V or C");
+  FE_ARG(b == 1 || b == 2 || b == 4 || b == 8, "fe_block_update_gram: b = %d not in {1,2,4,8}", b);
+  FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_update_gram: bad dtype");
+  if (nv > 0) {
+    size_t es = dt == FE_F32 ? 4 : 8;
+    const char* va = (const char*)V;
+    const char* wa = (const char*)W;
+    FE_ARG(wa + n * b * es <= va || va + (size_t)nv * n * b * es <= wa,
+           "fe_block_update_gram: W aliases V");
+  }
+  BlockSet vs = make_blockset(V, nv, b, b, n * b, dt);
+  return update_gram(vs, n, C, alpha, beta, nullptr, W, b, dt, 1, nullptr, G, cur_stream());
+}
+
 int fe_block_orth(const void* V, int64_t n, int nv, int b, void* W, fe_dtype dt, double anorm,
                   uint64_t seed, double* G, double* R, int* replaced) {
   FE_ARG(W && R, "fe_block_orth: NULL W or R");

@@ -692,18 +692,19 @@ namespace fe {
 // W_new when gram_v == 0), accumulated per CTA like gram_kernel.  Phase A leaves the range's
 // new W rows in shared memory (two buffers, so one barrier per range suffices); phase B re-reads
 // the range's V rows, which phase A has just pulled into L1, so V comes from DRAM once for both
-// operations.  Gram tiles are the V blocks then W_new; TPW > 0: warp w owns tiles w + 8t for the
-// whole launch and reduces once at the end; TPW == 0: tiles are reduced per range.
+// operations.  Gram tiles are the V blocks then W_new; TPW > 0: warp w owns tiles w + nwarps t
+// for the whole launch and reduces once at the end (the block has one warp per tile, up to 16,
+// and a range is one row per thread); TPW == 0: 8 warps, tiles reduced per range.
 template <typename T, int BV, int BW, int TPW>
-__global__ void __launch_bounds__(256) update_gram_kernel(const BlockSet V, const double* __restrict__ C,
+__global__ void __launch_bounds__(TPW > 0 ? 512 : 256) update_gram_kernel(const BlockSet V, const double* __restrict__ C,
                                                           double alpha, double beta,
                                                           const double* __restrict__ M,
                                                           T* __restrict__ W, int64_t n, int gram_v,
                                                           const int* __restrict__ skip,
                                                           double* __restrict__ partial) {
   if (skip && *skip) return;
-  constexpr int R = 256;
-  constexpr int kWarps = 8;
+  const int R = blockDim.x;
+  const int kWarps = blockDim.x >> 5;
   constexpr int NR = BV > BW ? BV : BW;
   constexpr int NT = TPW > 0 ? TPW : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -845,37 +846,40 @@ __global__ void __launch_bounds__(256) update_gram_kernel(const BlockSet V, cons
 template <typename T, int BV, int BW, int TPW>
 static int launch_update_gram_tpw(const BlockSet& V, int64_t n, const double* C, double alpha,
                                   double beta, const double* M, T* W, int gram_v, const int* skip,
-                                  double* G, cudaStream_t s) {
-  constexpr int R = 256;
+                                  double* G, int threads, cudaStream_t s) {
+  const int R = threads;
   const int k = V.nv * BV;
   const int nout = (gram_v ? k : 0) * BW + BW * BW;
   const size_t smem = ((((size_t)k * BW + BW * BW + 2 * (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15) +
                       (size_t)nout * sizeof(double);
   FE_ARG(smem <= 200 * 1024, "update_gram: coefficient matrix too large");
   static bool configured = false;
-  static int per_sm = 0;
-  static size_t per_sm_smem = 0;
+  static int per_sm[17] = {0};  // by warps per block
+  static size_t per_sm_smem[17] = {0};
   if (!configured) {
     FE_CUDA(cudaFuncSetAttribute(update_gram_kernel<T, BV, BW, TPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     configured = true;
   }
-  if (per_sm == 0 || smem > per_sm_smem) {
+  const int wq = threads / 32;
+  FE_ARG(threads % 32 == 0 && wq >= 8 && wq <= 16, "update_gram: %d threads", threads);
+  if (per_sm[wq] == 0 || smem > per_sm_smem[wq]) {
     int nb = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_gram_kernel<T, BV, BW, TPW>, 256, smem));
-    per_sm = std::max(nb, 1);
-    per_sm_smem = smem;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_gram_kernel<T, BV, BW, TPW>, threads, smem));
+    per_sm[wq] = std::max(nb, 1);
+    per_sm_smem[wq] = smem;
   }
-  int nctas = (int)std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm * num_sms());
+  int nctas = (int)std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm[wq] * num_sms());
   nctas = std::max(nctas, 1);
   double* part = small_scratch(0, (size_t)nctas * nout);
   if (!part) return FE_ERR_OOM;
-  update_gram_kernel<T, BV, BW, TPW><<<nctas, 256, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, part);
+  update_gram_kernel<T, BV, BW, TPW><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, part);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return launch_gram_reduce(part, nctas, nout, 1.0, G, s);
 }
 
-// Persistent accumulators when a warp's tiles fit in 32 32-bit registers.
+// One warp per Gram tile with persistent accumulators (up to 16 tiles, 32 32-bit registers
+// per tile); otherwise 8 warps reducing per range.
 template <typename T, int BV, int BW>
 static int launch_update_gram(const BlockSet& V, int64_t n, const double* C, double alpha,
                               double beta, const double* M, T* W, int gram_v, const int* skip,
@@ -883,11 +887,10 @@ static int launch_update_gram(const BlockSet& V, int64_t n, const double* C, dou
   constexpr int NR = BV > BW ? BV : BW;
   constexpr int kRegsPerTile = NR * BW * (int)(sizeof(T) / 4);
   const int gblocks = gram_v ? V.nv + 1 : 1;
-  if (gblocks <= 8 && kRegsPerTile <= 32)
-    return launch_update_gram_tpw<T, BV, BW, (kRegsPerTile <= 32 ? 1 : 0)>(V, n, C, alpha, beta, M, W, gram_v, skip, G, s);
-  if (gblocks <= 16 && 2 * kRegsPerTile <= 32)
-    return launch_update_gram_tpw<T, BV, BW, (2 * kRegsPerTile <= 32 ? 2 : 0)>(V, n, C, alpha, beta, M, W, gram_v, skip, G, s);
-  return launch_update_gram_tpw<T, BV, BW, 0>(V, n, C, alpha, beta, M, W, gram_v, skip, G, s);
+  if (gblocks <= 16 && kRegsPerTile <= 32)
+    return launch_update_gram_tpw<T, BV, BW, (kRegsPerTile <= 32 ? 1 : 0)>(
+        V, n, C, alpha, beta, M, W, gram_v, skip, G, 32 * std::max(8, gblocks), s);
+  return launch_update_gram_tpw<T, BV, BW, 0>(V, n, C, alpha, beta, M, W, gram_v, skip, G, 256, s);
 }
 
 // W = beta W M + alpha V C; G = [V; W]^T W (gram_v) or W^T W, rows (j*b + p) then W's b rows.

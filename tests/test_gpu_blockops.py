@@ -67,6 +67,43 @@ def test_update_parity(prec, n, nv, bv, bw, alpha, beta):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n,nv,b", [(1, 0, 1), (999, 0, 4), (5003, 3, 4), (70001, 7, 4),
+                                    (4099, 8, 4), (33000, 12, 2), (20000, 17, 4), (7777, 5, 8),
+                                    (3000, 15, 1)])
+@pytest.mark.parametrize("alpha,beta", [(-1.0, 1.0), (0.5, -2.0)])
+def test_update_gram_parity(prec, n, nv, b, alpha, beta):
+    """fe_block_update_gram = op1 then op3 on the updated block (oracle: the two Table 1
+    operations one after the other, FP64).  Shapes span one warp per tile (<= 16 tiles: block
+    of 32 x tiles threads), the per-range reduction (17 blocks), ragged row tails."""
+    V = _blocks(max(nv, 1), n, b, 6, NP[prec])[:nv] if nv else None
+    C = np.random.default_rng(7).standard_normal((max(nv, 1) * b, b))[: nv * b]
+    W = graphgen.normal_block(n, b, seed=8, dtype=NP[prec])
+    Wd = to_dev(W)
+    G = fe.block_update_gram(None if V is None else to_dev(V), to_dev(C), Wd, alpha, beta)
+    got_w = Wd.cpu().numpy().astype(np.float64)
+    got_g = G.cpu().numpy()
+    W64 = W.astype(np.float64)
+    if nv:
+        Vt = _as_tall(V)
+        ref_w = blockops.mv_times_mat_add_mv(alpha, Vt, C, beta, W64)
+        mag = np.abs(alpha) * (np.abs(Vt) @ np.abs(C)) + np.abs(beta * W64)
+    else:
+        Vt = np.zeros((n, 0))
+        ref_w = blockops.mv_scale1(beta, W64)
+        mag = np.abs(beta * W64)
+    k = nv * b + b + 2
+    rel = {"f32": 6e-8, "f64": 1.2e-16}[prec] * k * 2
+    assert np.all(np.abs(got_w - ref_w) <= rel * mag + 1e-300)
+    # Gram of [V; W_new] against W_new, from the kernel's own W_new (the update's rounding is
+    # checked above): bound by |[V W]|^T |W| like the Gram test
+    VW = np.concatenate([Vt, got_w], axis=1)
+    ref_g = blockops.mv_trans_mv(1.0, VW, got_w)
+    bound = TOL[prec] * (np.abs(VW).T @ np.abs(got_w)) + 1e-300
+    assert got_g.shape == ((nv + 1) * b, b)
+    assert np.all(np.abs(got_g - ref_g) <= bound)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_random_normal_matches_oracle_generator(prec):
     t = torch()
     X = fe.random_normal(10007, 4, dtype=t.float32 if prec == "f32" else t.float64, seed=7,
