@@ -301,9 +301,13 @@ def run_ours(args):
             t = time_cuda(lambda: fe.spmm(h, Xs, Ys), args.sweep_reps, torch)
             med = statistics.median(t)
             gb = spmm_bytes(n, nnz, b, es) / (med / 1000.0) / 1e9
+            # secondary: gather-inclusive bytes (every nonzero's X row counted, as an SpMM with
+            # no X reuse in any cache would move them)
+            gather_b = spmm_bytes(n, nnz, b, es) - n * b * es + nnz * b * es
             sweep[f"{prec}_b{b}"] = {"ms": round(med, 4), "GBps": round(gb, 1),
                                      "frac_measured": round(gb / hbm_peak, 4),
-                                     "frac_nominal": round(gb / NOMINAL_HBM, 4)}
+                                     "frac_nominal": round(gb / NOMINAL_HBM, 4),
+                                     "gather_GBps": round(gather_b / (med / 1000.0) / 1e9, 1)}
             del Xs, Ys
     # SpMM roofline (the metric's kernel), FP32 b = 4 and the solve's FP64 b = 4
     spmm_roofline = {}
@@ -378,6 +382,17 @@ def run_ours(args):
                                      "loss": "span vs the 8 wanted Ritz vectors",
                                      "final_loss": float(np.mean(losses[-50:])),
                                      "s": round(t_train, 2)}}
+            # the learned start with the mixed-precision iteration
+            def run_learned_mixed():
+                out["rm"] = fe.eigs(h, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1, mlp_weights=params,
+                                    mlp_hidden=64, mode="mixed", max_restarts=MAX_RESTARTS)
+            run_learned_mixed()
+            tlm = time_cuda(run_learned_mixed, 1, torch)[0]
+            ev5, X5, st5 = out["rm"]
+            learned_res["mixed"] = {
+                "s": tlm / 1000.0, "spmm_blocks": st5["spmm_blocks"], "restarts": st5["restarts"],
+                "speedup_vs_fp64_random": ms_per_step / tlm,
+                "max_rel_eval_diff_vs_fp64": float(np.max(np.abs(ev5 - ev) / np.abs(ev)))}
         except Exception as e:
             learned_res = {"error": str(e)}
 
@@ -552,7 +567,8 @@ def main():
                     help="ncu DRAM bytes per launch of the roofline kernel")
     ap.add_argument("--ref-cycles", type=int, default=1)
     ap.add_argument("--ref-solve-blocks", type=int, default=150)
-    ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
+                    help="where the clock samples are written")
     ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1", "ugram1"],
                     help="solve: warm-up + timed solves only; spmm1 / gram1 / ugram1: launches "
                          "of one kernel only (profiler captures)")

@@ -1,7 +1,7 @@
 """Learned start block: vertex features, the MLP, its loss and gradients, FP64 numpy.
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Not in the paper; this is the benchmark spec's learned-start pattern.  A small MLP maps per-vertex
+Not in the paper; an extension of its random start block.  A small MLP maps per-vertex
 features computed with SpMM (Section 3.3) to an n x b block that starts the Block Krylov-Schur
 iteration instead of a random block (Table 1, MvRandom).
 

@@ -450,7 +450,10 @@ int update(const BlockSet& V, int64_t n, const double* C, double alpha, double b
 }
 
 // ---------------------------------------------------------------- combine (V Y)
-template <typename T, int BV>
+// Out_o[r] = sum_j V_j[r] Y[j-block rows, o-block columns], thread per row.  Up to OB output
+// blocks are accumulated in registers at once, so each V row is loaded once per group of OB
+// output blocks (one group for the solver's restarts), two or four rows in flight.
+template <typename T, int BV, int OB>
 __global__ void __launch_bounds__(256) combine_kernel(const BlockSet V, const double* __restrict__ Y,
                                                       int ldy, const BlockSet Out, int64_t n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -458,27 +461,44 @@ __global__ void __launch_bounds__(256) combine_kernel(const BlockSet V, const do
   const int k = V.nv * BV, kout = Out.nv * BV;
   for (int e = threadIdx.x; e < k * kout; e += blockDim.x) sY[e] = (T)Y[(e / kout) * ldy + e % kout];
   __syncthreads();
+  constexpr int UJ = BV >= 8 ? 2 : 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-    for (int o = 0; o < Out.nv; ++o) {
-      T acc[BV];
+    for (int o0 = 0; o0 < Out.nv; o0 += OB) {
+      T acc[OB][BV];
 #pragma unroll
-      for (int q = 0; q < BV; ++q) acc[q] = T(0);
-      for (int j = 0; j < V.nv; ++j) {
-        T v[BV];
-        load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j]), V.ld, r, v);
-        const T* y = sY + (size_t)(j * BV) * kout + o * BV;
+      for (int o = 0; o < OB; ++o)
 #pragma unroll
-        for (int p = 0; p < BV; ++p)
+        for (int q = 0; q < BV; ++q) acc[o][q] = T(0);
+      for (int j0 = 0; j0 < V.nv; j0 += UJ) {
+        T v[UJ][BV];
 #pragma unroll
-          for (int q = 0; q < BV; ++q) acc[q] = fma(v[p], y[p * kout + q], acc[q]);
+        for (int u = 0; u < UJ; ++u)
+          if (j0 + u < V.nv) load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j0 + u]), V.ld, r, v[u]);
+#pragma unroll
+        for (int u = 0; u < UJ; ++u) {
+          if (j0 + u >= V.nv) break;
+          const T* yj = sY + (size_t)((j0 + u) * BV) * kout + o0 * BV;
+#pragma unroll
+          for (int o = 0; o < OB; ++o) {
+            if (o0 + o >= Out.nv) break;
+#pragma unroll
+            for (int p = 0; p < BV; ++p)
+#pragma unroll
+              for (int q = 0; q < BV; ++q) acc[o][q] = fma(v[u][p], yj[p * kout + o * BV + q], acc[o][q]);
+          }
+        }
       }
-      T* dst = const_cast<T*>(reinterpret_cast<const T*>(Out.blk[o]));
-      if (Out.ld == BV) {
-        st_row<T, BV>(dst + r * BV, acc);
-      } else {
 #pragma unroll
-        for (int q = 0; q < BV; ++q) dst[r * Out.ld + q] = acc[q];
+      for (int o = 0; o < OB; ++o) {
+        if (o0 + o >= Out.nv) break;
+        T* dst = const_cast<T*>(reinterpret_cast<const T*>(Out.blk[o0 + o]));
+        if (Out.ld == BV) {
+          st_row<T, BV>(dst + r * BV, acc[o]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < BV; ++q) dst[r * Out.ld + q] = acc[o][q];
+        }
       }
     }
   }
@@ -487,16 +507,17 @@ __global__ void __launch_bounds__(256) combine_kernel(const BlockSet V, const do
 template <typename T, int BV>
 static int launch_combine(const BlockSet& V, int64_t n, const double* Y, int ldy,
                           const BlockSet& Out, cudaStream_t s) {
+  constexpr int OB = BV <= 4 ? 8 : (BV == 8 ? 4 : 2);
   const size_t smem = (size_t)V.nv * BV * Out.nv * BV * sizeof(T);
   FE_ARG(smem <= 200 * 1024, "combine: coefficient matrix too large");
   static bool configured = false;
   if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(combine_kernel<T, BV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    FE_CUDA(cudaFuncSetAttribute(combine_kernel<T, BV, OB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     configured = true;
   }
   int ctas = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
   ctas = std::max(ctas, 1);
-  combine_kernel<T, BV><<<ctas, 256, smem, s>>>(V, Y, ldy, Out, n);
+  combine_kernel<T, BV, OB><<<ctas, 256, smem, s>>>(V, Y, ldy, Out, n);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;

@@ -74,8 +74,9 @@ struct Phase {
   uint64_t seed;
   int max_restarts, max_sweeps;
   int pass1_f32 = 0;  // FP64 subspace: first Gram-Schmidt pass's Gram in FP32 arithmetic
-  int stagnation_window = 0;  // > 0: stop when the worst wanted rho/scale has not improved
-                              // by 10% over this many restarts (FP32 phase)
+  int stagnation_window = 0;  // > 0: stop when the worst wanted rho/scale has not halved
+                              // over this many restarts (FP32 phase: at its precision floor
+                              // the ratio only fluctuates)
   cudaStream_t s;
   // state
   DevBuf vmem, hmem, small, xmem;
@@ -242,7 +243,7 @@ struct Phase {
       int nc = 0;
       FE_TRY(ritz(&nc));
       nconv = nc;
-      if (worst_ratio < 0.9 * best) {
+      if (worst_ratio < 0.5 * best) {
         best = worst_ratio;
         best_at = restarts;
       }
@@ -255,6 +256,9 @@ struct Phase {
       if (nc == nev || restarts >= max_restarts) {
         bool good = false;
         FE_TRY(ritz_vectors_and_residuals(&good));
+        // FP32 phase: the Ritz estimates all pass but the explicit residuals do not -- the
+        // estimates have gone below what FP32 arithmetic can deliver; hand over to FP64
+        if (stagnation_window > 0 && nc == nev && !good) return kStagnated;
         if ((nc == nev && good) || restarts >= max_restarts) {
           if (!(nc == nev && good)) {
             int ok = 0;

@@ -1,4 +1,4 @@
-// Learned start block (not in the paper; the benchmark spec's learned-start pattern): vertex
+// Learned start block (not in the paper; an extension of its random start, Table 1 MvRandom):
 // features from SpMM powers (Section 3.3's operation), a 3-layer MLP that maps them to an
 // n x b block, its training kernels (loss, gradient, Adam), and the start block fe_eigs uses.
 //

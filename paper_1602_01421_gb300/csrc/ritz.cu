@@ -3,9 +3,10 @@
 //
 // ritz_kernel: T = (H_m + H_m^T) / 2 (m x m) is diagonalised by the cyclic Jacobi method in
 // parallel ("round-robin" ordering, Brent & Luk 1985: each of the m-1 steps of a sweep
-// rotates m/2 disjoint index pairs at once, so the row and column updates of different pairs
-// never touch the same entries).  Each rotation is the 2x2 symmetric Schur decomposition of
-// Golub & Van Loan Section 8.5.  The Ritz values are then ordered by `which`, and each Ritz
+// rotates m/2 disjoint index pairs at once).  Each rotation is the 2x2 symmetric Schur
+// decomposition of Golub & Van Loan Section 8.5; a step applies all of them at once as
+// J^T A J on independent 2x2 blocks (rows of one pair, columns of another), so a step costs
+// two barriers.  The Ritz values are then ordered by `which`, and each Ritz
 // pair gets its residual estimate rho_c = ||H[m:m+b, 0:m] y_c|| (the coupling of the last
 // block to the next basis block, since A V_m = V_m H_m + V_{NB} H[m:m+b, :]).
 #include <math.h>
@@ -14,23 +15,184 @@
 
 namespace fe {
 
-// smem layout: A[mp][mp+1], Q[mp][mp+1] (padded rows), plus pair rotations.
+// tan of the Jacobi angle that diagonalises [app apq; apq aqq] (Golub & Van Loan Section
+// 8.5.2), evaluated in FP32.  FP64 entries are first scaled by a power of two and the diagonal
+// difference is taken in FP64, so only the final quotient and square root are FP32.  Returns
+// 0 when apq is negligible at FP32 range.  Any t gives an exactly orthogonal rotation once c
+// and s are formed from it (jacobi_cs), so an inexact t only leaves a small (p,q) entry for
+// the next sweep.
+__device__ __forceinline__ float jacobi_tan(float app, float apq, float aqq) {
+  if (apq == 0.f) return 0.f;
+  const float tau = (aqq - app) / (2.f * apq);
+  if (fabsf(tau) > 1e18f) return 0.5f / tau;
+  return (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+}
+__device__ __forceinline__ float jacobi_tan(double app, double apq, double aqq) {
+  if (apq == 0.0) return 0.f;
+  const double mx = fmax(fmax(fabs(app), fabs(aqq)), fabs(apq));
+  int e;
+  frexp(mx, &e);
+  const double sc = ldexp(1.0, -e);
+  const float d = (float)((aqq - app) * sc), f = (float)(apq * sc);
+  if (f == 0.f) return 0.f;
+  const float tau = d / (2.f * f);
+  if (fabsf(tau) > 1e18f) return 0.5f / tau;
+  return (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+}
+// c = 1 / sqrt(1 + t^2), s = t c in T: FP32 estimate, then (FP64) two Newton steps for the
+// reciprocal square root, so that c^2 + s^2 = 1 to T's rounding.
+__device__ __forceinline__ void jacobi_cs(float t, float& c, float& s) {
+  c = rsqrtf(1.f + t * t);
+  s = t * c;
+}
+__device__ __forceinline__ void jacobi_cs(float t32, double& c, double& s) {
+  const double t = (double)t32, u = 1.0 + t * t;
+  double r = (double)rsqrtf((float)u);
+  r = r * (1.5 - 0.5 * u * r * r);
+  r = r * (1.5 - 0.5 * u * r * r);
+  c = r;
+  s = t * r;
+}
+
+// Sum over the block of one value per thread (all threads call it).
+__device__ double ritz_block_sum(double v, double* red) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (nth + 31) / 32; ++w) s += red[w];
+    red[0] = s;
+  }
+  __syncthreads();
+  const double s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Parallel cyclic Jacobi sweeps on the symmetric mp x mp matrix A (row stride ld), with
+// Q <- Q J accumulated, until the off-diagonal Frobenius norm squared is <= thresh or after
+// max_sweeps.  Returns the sweeps run; *conv tells whether the threshold was met.
+template <typename T>
+__device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, int max_sweeps,
+                             T* cs, T* sn, int* pp, int* pq, double* red, bool* conv) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int np = mp / 2;
+  int sweeps = 0;
+  while (true) {
+    double v = 0.0;
+    for (int e = tid; e < mp * mp; e += nth) {
+      const int i = e / mp, j = e - (e / mp) * mp;
+      if (i != j) v += (double)A[i * ld + j] * (double)A[i * ld + j];
+    }
+    const double off2 = ritz_block_sum(v, red);
+    if (off2 <= thresh || sweeps >= max_sweeps) {
+      *conv = off2 <= thresh;
+      return sweeps;
+    }
+    ++sweeps;
+    for (int step = 0; step < mp - 1; ++step) {
+      // circle method: position 0 fixed, positions 1..mp-1 rotate by `step`
+      for (int k = tid; k < np; k += nth) {
+        auto pos = [&](int i) { return i == 0 ? 0 : ((i - 1 + step) % (mp - 1)) + 1; };
+        int p = pos(k), q = pos(mp - 1 - k);
+        if (p > q) { int t = p; p = q; q = t; }
+        T c = T(1), sv = T(0);
+        if (q < m) {
+          const float t = jacobi_tan(A[p * ld + p], A[p * ld + q], A[q * ld + q]);
+          if (t != 0.f) jacobi_cs(t, c, sv);
+        }
+        pp[k] = p;
+        pq[k] = q;
+        cs[k] = c;
+        sn[k] = sv;
+      }
+      __syncthreads();
+      // A <- J^T A J as independent 2 x 2 blocks (rows of pair k, columns of pair k2, k <= k2,
+      // mirrored to the lower triangle), and Q <- Q J by column pairs: the step's pairs are
+      // disjoint, so no two work items touch the same entry and one barrier suffices.
+      const int nsq = np * np;
+      for (int e = tid; e < nsq + mp * np; e += nth) {
+        if (e < nsq) {
+          const int k = e / np, k2 = e - k * np;
+          if (k > k2) continue;
+          const T s1 = sn[k], s2 = sn[k2];
+          if (s1 == T(0) && s2 == T(0)) continue;
+          const T c1 = cs[k], c2 = cs[k2];
+          const int p1 = pp[k], q1 = pq[k];
+          if (k == k2) {
+            // the pair's own block: full transform (t need not be exact)
+            const T app = A[p1 * ld + p1], aqq = A[q1 * ld + q1], apq = A[p1 * ld + q1];
+            const T cc = c1 * c1, ss = s1 * s1, cs2 = c1 * s1;
+            A[p1 * ld + p1] = cc * app - T(2) * cs2 * apq + ss * aqq;
+            A[q1 * ld + q1] = ss * app + T(2) * cs2 * apq + cc * aqq;
+            const T npq = cs2 * (app - aqq) + (cc - ss) * apq;
+            A[p1 * ld + q1] = npq;
+            A[q1 * ld + p1] = npq;
+          } else {
+            const int p2 = pp[k2], q2 = pq[k2];
+            const T x00 = A[p1 * ld + p2], x01 = A[p1 * ld + q2];
+            const T x10 = A[q1 * ld + p2], x11 = A[q1 * ld + q2];
+            const T y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+            const T y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+            const T z00 = c2 * y00 - s2 * y01, z01 = s2 * y00 + c2 * y01;
+            const T z10 = c2 * y10 - s2 * y11, z11 = s2 * y10 + c2 * y11;
+            A[p1 * ld + p2] = z00;
+            A[p1 * ld + q2] = z01;
+            A[q1 * ld + p2] = z10;
+            A[q1 * ld + q2] = z11;
+            A[p2 * ld + p1] = z00;
+            A[q2 * ld + p1] = z01;
+            A[p2 * ld + q1] = z10;
+            A[q2 * ld + q1] = z11;
+          }
+        } else {
+          const int e2 = e - nsq;
+          const int i = e2 / np, k = e2 - i * np;
+          const T sk = sn[k];
+          if (sk == T(0)) continue;
+          const T ck = cs[k];
+          const int p = pp[k], q = pq[k];
+          const T vp = Q[i * ld + p], vq = Q[i * ld + q];
+          Q[i * ld + p] = ck * vp - sk * vq;
+          Q[i * ld + q] = sk * vp + ck * vq;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// smem layout (mp = m rounded up to even, ld = mp + 1, rows padded):
+//   A64[mp][ld], Q64[mp][ld]             FP64 matrix and eigenvectors
+//   U: A32[mp][ld] + Q32[mp][ld] (FP32)  later reused as W[mp][ld] (FP64 scratch)
+//   cs, sn (mp/2 doubles each), pp, pq (mp/2 ints each), order (mp ints)
+// Two precisions: FP32 Jacobi sweeps take the matrix to a relative off-diagonal norm of about
+// 1e-6 (FP32 rotations run at the FP32 rate of the SM, FP64 ones at 1/64 of it); the FP32
+// eigenvector matrix is made exactly orthogonal in FP64 (Cholesky QR), the FP64 matrix is
+// transformed by it (Q^T T Q, an exact orthogonal similarity), and FP64 sweeps finish from there
+// -- two or three, since Jacobi converges quadratically once the off-diagonal part is small.
 __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int which, int max_sweeps,
                             double tol, double* __restrict__ theta_out, double* __restrict__ Y_out,
                             double* __restrict__ rho_out, int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int mp = m + (m & 1);  // even size; index m (if odd) is a zero dummy never rotated
   const int ld = mp + 1;
+  const size_t mat = (size_t)mp * ld;
   double* A = reinterpret_cast<double*>(smem_raw);
-  double* Q = A + (size_t)mp * ld;
-  double* cs = Q + (size_t)mp * ld;
-  double* sn = cs + mp / 2;
-  int* pp = reinterpret_cast<int*>(sn + mp / 2);
-  int* pq = pp + mp / 2;
-  int* order = pq + mp / 2;
+  double* Q = A + mat;
+  double* W = Q + mat;
+  float* A32 = reinterpret_cast<float*>(W);
+  float* Q32 = A32 + mat;
+  const int np = mp / 2;  // rotation pairs per step
+  double* cs = W + mat;
+  double* sn = cs + np;
+  int* pp = reinterpret_cast<int*>(sn + np);
+  int* pq = pp + np;
+  int* order = pq + np;
   __shared__ double red[32];
-  __shared__ double fro2;
-  __shared__ int done;
+  __shared__ bool conv32, conv64;
   const int tid = threadIdx.x, nth = blockDim.x;
 
   for (int e = tid; e < mp * mp; e += nth) {
@@ -38,95 +200,77 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
     double a = 0.0;
     if (i < m && j < m) a = 0.5 * (H[i * m + j] + H[j * m + i]);
     A[i * ld + j] = a;
-    Q[i * ld + j] = (i == j) ? 1.0 : 0.0;
+    A32[i * ld + j] = (float)a;
+    Q32[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  auto block_sum = [&](double v) -> double {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (tid == 0) {
-      for (int w = 0; w < (nth + 31) / 32; ++w) s += red[w];
-      red[0] = s;
-    }
-    __syncthreads();
-    s = red[0];
-    __syncthreads();
-    return s;
-  };
+  double fro2;
   {
     double v = 0.0;
     for (int e = tid; e < mp * mp; e += nth) v += A[(e / mp) * ld + e % mp] * A[(e / mp) * ld + e % mp];
-    double s = block_sum(v);
-    if (tid == 0) fro2 = s;
+    fro2 = ritz_block_sum(v, red);
+  }
+  // FP32 sweeps
+  int sweeps = jacobi_sweeps<float>(A32, Q32, ld, m, mp, 1e-12 * fro2, 15, reinterpret_cast<float*>(cs),
+                                    reinterpret_cast<float*>(sn), pp, pq, red, &conv32);
+  // Q = chol-QR(Q32) in FP64: S = Q^T Q (in W after Q32 is copied out), S = R^T R, Q <- Q R^-1
+  for (int e = tid; e < mp * mp; e += nth) {
+    const int i = e / mp, j = e % mp;
+    Q[i * ld + j] = (double)Q32[i * ld + j];
   }
   __syncthreads();
-  int sweeps = 0;
-  bool converged = false;
-  while (true) {
-    double v = 0.0;
-    for (int e = tid; e < mp * mp; e += nth) {
-      const int i = e / mp, j = e % mp;
-      if (i != j) v += A[i * ld + j] * A[i * ld + j];
+  for (int e = tid; e < mp * mp; e += nth) {
+    const int i = e / mp, j = e % mp;
+    if (i > j) continue;
+    double s = 0.0;
+    for (int r = 0; r < mp; ++r) s += Q[r * ld + i] * Q[r * ld + j];
+    W[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int j = 0; j < mp; ++j) {
+    if (tid == 0) {
+      double d = W[j * ld + j];
+      for (int l = 0; l < j; ++l) d -= W[l * ld + j] * W[l * ld + j];
+      W[j * ld + j] = d > 0.0 ? sqrt(d) : 1.0;  // Q32 is orthogonal to ~1e-7: d ~ 1
     }
-    const double off2 = block_sum(v);
-    if (tid == 0) done = (off2 <= tol * tol * fro2) || sweeps >= max_sweeps;
     __syncthreads();
-    if (done) {
-      converged = off2 <= tol * tol * fro2;
-      break;
+    const double rjj = W[j * ld + j];
+    for (int i = j + 1 + tid; i < mp; i += nth) {
+      double s = W[j * ld + i];
+      for (int l = 0; l < j; ++l) s -= W[l * ld + j] * W[l * ld + i];
+      W[j * ld + i] = s / rjj;
     }
-    ++sweeps;
-    for (int step = 0; step < mp - 1; ++step) {
-      // circle method: position 0 fixed, positions 1..mp-1 rotate by `step`
-      for (int k = tid; k < mp / 2; k += nth) {
-        auto pos = [&](int i) { return i == 0 ? 0 : ((i - 1 + step) % (mp - 1)) + 1; };
-        int p = pos(k), q = pos(mp - 1 - k);
-        if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < m) {
-          const double apq = A[p * ld + q];
-          if (apq != 0.0) {
-            const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        pp[k] = p;
-        pq[k] = q;
-        cs[k] = c;
-        sn[k] = s;
-      }
-      __syncthreads();
-      // rows p, q  (A <- J^T A)
-      for (int e = tid; e < (mp / 2) * mp; e += nth) {
-        const int k = e / mp, j = e % mp;
-        const double c = cs[k], s = sn[k];
-        if (s == 0.0) continue;
-        const int p = pp[k], q = pq[k];
-        const double ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns p, q  (A <- A J, Q <- Q J)
-      for (int e = tid; e < (mp / 2) * mp; e += nth) {
-        const int k = e / mp, i = e % mp;
-        const double c = cs[k], s = sn[k];
-        if (s == 0.0) continue;
-        const int p = pp[k], q = pq[k];
-        const double ap = A[i * ld + p], aq = A[i * ld + q];
-        A[i * ld + p] = c * ap - s * aq;
-        A[i * ld + q] = s * ap + c * aq;
-        const double vp = Q[i * ld + p], vq = Q[i * ld + q];
-        Q[i * ld + p] = c * vp - s * vq;
-        Q[i * ld + q] = s * vp + c * vq;
-      }
-      __syncthreads();
+    __syncthreads();
+  }
+  for (int r = tid; r < mp; r += nth) {
+    for (int j = 0; j < mp; ++j) {
+      double x = Q[r * ld + j];
+      for (int l = 0; l < j; ++l) x -= Q[r * ld + l] * W[l * ld + j];
+      Q[r * ld + j] = x / W[j * ld + j];
     }
   }
+  __syncthreads();
+  // A <- Q^T A Q (W = A Q first; A is symmetric, the result is mirrored from its upper triangle)
+  for (int e = tid; e < mp * mp; e += nth) {
+    const int i = e / mp, j = e % mp;
+    double s = 0.0;
+    for (int l = 0; l < mp; ++l) s += A[i * ld + l] * Q[l * ld + j];
+    W[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < mp * mp; e += nth) {
+    const int i = e / mp, j = e % mp;
+    if (i > j) continue;
+    double s = 0.0;
+    for (int l = 0; l < mp; ++l) s += Q[l * ld + i] * W[l * ld + j];
+    A[i * ld + j] = s;
+    A[j * ld + i] = s;
+  }
+  __syncthreads();
+  // FP64 sweeps to the requested tolerance
+  sweeps += jacobi_sweeps<double>(A, Q, ld, m, mp, tol * tol * fro2, max_sweeps, cs, sn, pp, pq,
+                                  red, &conv64);
+  const bool converged = conv64;
   // order by `which` (stable insertion sort; 0 = LM: |x| desc, ties larger first;
   // 1 = LA: descending; 2 = SA: ascending)
   if (tid == 0) {
@@ -168,22 +312,22 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
 
 size_t ritz_smem_bytes(int m) {
   const int mp = m + (m & 1);
-  return (size_t)2 * mp * (mp + 1) * sizeof(double) + (size_t)mp * sizeof(double) +
+  return (size_t)3 * mp * (mp + 1) * sizeof(double) + (size_t)(mp / 2) * 2 * sizeof(double) +
          (size_t)(mp / 2) * 2 * sizeof(int) + (size_t)mp * sizeof(int) + 64;
 }
 
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
                 double* theta, double* Y, double* rho, int* info, cudaStream_t s) {
   const size_t smem = ritz_smem_bytes(m);
-  FE_ARG(smem <= 220 * 1024, "ritz: subspace m = %d too large", m);
+  FE_ARG(smem <= 225 * 1024, "ritz: subspace m = %d too large", m);
   static bool configured = false;
   if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    FE_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
     configured = true;
   }
-  // few threads: each of the ~3 barriers per rotation step is cheap, and a step is only
-  // m/2 x m updates
-  ritz_kernel<<<1, 128, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info);
+  // one CTA: a rotation step is (m/2)^2 / 2 2 x 2 blocks plus m^2 / 2 Q updates between two
+  // barriers; FP64 work on one SM runs at 2 DFMA per clock, hence the FP32 sweeps first
+  ritz_kernel<<<1, 256, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;

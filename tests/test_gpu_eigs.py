@@ -190,3 +190,18 @@ def test_fp32_first_pass_keeps_the_krylov_relation():
     assert np.allclose(e32, e64, rtol=1e-9, atol=0)
     _check_pairs(g, e32, X32, 1e-9, abs(e64[0]))
     assert s32["restarts"] <= 1.2 * s64["restarts"] + 5
+
+
+def test_mixed_tolerance_below_fp32_floor_hands_over():
+    """A mixed-mode FP32 tolerance below what FP32 can reach (1e-8 relative) must not keep the
+    FP32 phase running to max_restarts: it stops once its residual ratio stops halving, and the
+    FP64 phase reaches the same eigenpairs as the plain FP64 solve."""
+    g = graphgen.rmat(14, seed=1)
+    with fe.Csr.from_graph(g) as h:
+        ev0, _, st0 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1)
+        ev1, X1, st1 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", mode="mixed", mixed_tol=1e-8, seed=1,
+                               max_restarts=5000)
+    assert st1["converged"]
+    assert st1["restarts_fp32"] < 5000 and st1["restarts"] < 5000
+    assert np.allclose(ev1, ev0, rtol=1e-8)
+    _check_pairs(g, ev1, X1, 1e-8, abs(ev0[0]))

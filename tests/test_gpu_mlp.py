@@ -1,6 +1,6 @@
 """GPU parity of the learned-start kernels against oracle/mlp.py.
 
-Bars (the benchmark spec): forward within 1e-5 of the CPU forward (FP32), gradients within 1e-4
+Bars: forward within 1e-5 of the CPU forward (FP32), gradients within 1e-4
 relative; features within FP32 rounding of the FP64 oracle features.
 """
 import numpy as np
@@ -115,6 +115,21 @@ def test_learned_start_solve_is_correct():
     assert np.allclose(ev1, ev0, rtol=1e-8)
 
 
+def test_learned_start_with_mixed_precision():
+    """The learned start feeds the FP32 phase of the mixed iteration; the FP64 phase then
+    reaches the same eigenpairs as the plain FP64 solve from a random start."""
+    g = graphgen.rmat(13, seed=4)
+    p = to_dev(learned.init_params(64, 4, seed=1))
+    with fe.Csr.from_graph(g) as h:
+        ev0, _, st0 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1)
+        ev1, X1, st1 = fe.eigs(h, 8, 4, 8, 1e-8, "LM", seed=1, mlp_weights=p, mlp_hidden=64,
+                               mode="mixed")
+    assert st1["converged"] and st1["spmm_start"] == 7 and st1["spmm_blocks_fp32"] > 0
+    assert np.allclose(ev1, ev0, rtol=1e-8)
+    X = X1.cpu().numpy()
+    assert np.abs(X.T @ X - np.eye(8)).max() < 1e-10
+
+
 @pytest.mark.slow
 def test_trained_network_gain_on_a_fresh_graph():
     """What the trained network gains over the method without it (a random start): trained with
@@ -124,7 +139,7 @@ def test_trained_network_gain_on_a_fresh_graph():
     component there.  The solve from either start gives the same eigenpairs; the block-SpMM
     counts are printed, not asserted: the solve's cost is set by an eigenvalue cluster whose
     vectors the per-vertex network does not capture, so the count is within the random-start
-    spread (see DESIGN.md)."""
+    spread."""
     t = torch()
     specs = [(s, 100 + i) for i, s in enumerate([12, 13, 14, 15, 16, 17] * 3)]
     ex = [learned.make_subspace_example(graphgen.rmat(s, seed=gs)) for s, gs in specs]

@@ -1,6 +1,6 @@
 """GPU parity: fe_spmm against the oracle's plain-definition SpMM (Section 3.3).
 
-Tolerances (from BASELINE's SpMM requirement, read per entry against A|X|, the condition
+Tolerances (the SpMM accuracy requirement of 1e-6 relative, read per entry against A|X|, the condition
 number of a sum): FP64 |Y - Y*| <= 1e-13 (A|X|), FP32 <= 1e-6 (A|X|) with Y* the FP64 sum of
 the same FP32 inputs.  A 1 = degree must be exact in either precision.
 """
