@@ -306,7 +306,8 @@ typedef struct {
  * 0/1 matrix of h that come first in `which` order (FE_LM: |lambda| descending, ties ->
  * larger lambda first; FE_LA: descending; FE_SA: ascending).  block = b, nblocks = NB,
  * subspace m = b * NB; requires 1 <= nev <= m - b, m + b <= n, b in {1, 2, 4, 8, 16},
- * NB >= 2, m <= 96, NB <= 38.  A pair is converged when its Ritz residual estimate is at most
+ * NB >= 2, m <= 160, NB <= 38 (m > 96: the projected eigenproblem keeps its eigenvector matrix in
+ * a device workspace of 2 (m+1)^2 doubles that fe_eigs allocates).  A pair is converged when its Ritz residual estimate is at most
  * tol * max(|theta|, 1e-3 * max|theta|) and the explicit residual ||A x - theta x|| passes the
  * same test.  evals: HOST, nev doubles.  evecs: DEVICE, n x nev COLUMN-major FP64 (ConvLayout,
  * Table 1), may be NULL; each vector's largest-magnitude entry is positive.  Synchronous.

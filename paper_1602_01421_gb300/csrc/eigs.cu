@@ -35,7 +35,8 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
             int update_anorm, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
             double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32);
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
-                double* theta, double* Y, double* rho, int* info, cudaStream_t s);
+                double* theta, double* Y, double* rho, int* info, double* work, cudaStream_t s);
+size_t ritz_work_doubles(int m);
 int launch_restart_h(double* H, int m, int b, int k, const double* theta, const double* Y,
                      cudaStream_t s);
 int normalize_signs(double* X, int64_t n, int ncols, cudaStream_t s);
@@ -79,7 +80,7 @@ struct Phase {
                               // the ratio only fluctuates)
   cudaStream_t s;
   // state
-  DevBuf vmem, hmem, small, xmem;
+  DevBuf vmem, hmem, small, xmem, ritzwork;
   std::vector<void*> slot, spare, xblk, axblk;
   double *H = nullptr, *theta = nullptr, *Y = nullptr, *rho = nullptr, *anorm = nullptr,
          *Cdiag = nullptr, *gtmp = nullptr;
@@ -112,6 +113,7 @@ struct Phase {
     Cdiag = anorm + 4;
     gtmp = Cdiag + 256;
     info = reinterpret_cast<int*>(gtmp + 64 * 16);
+    if (ritz_work_doubles(m) > 0) FE_TRY(ritzwork.alloc(sizeof(double) * ritz_work_doubles(m)));
     theta_h.resize(m);
     rho_h.resize(m);
     resid_h.assign(nev, 0.0);
@@ -154,7 +156,8 @@ struct Phase {
 
   // Ritz values/vectors of the current H, convergence estimate; returns nconv
   int ritz(int* nconv_out) {
-    FE_TRY(launch_ritz(H, m, b, which, max_sweeps, 1e-15, theta, Y, rho, info, s));
+    FE_TRY(launch_ritz(H, m, b, which, max_sweeps, 1e-15, theta, Y, rho, info,
+                       ritzwork.as<double>(), s));
     double an = 0.0;
     FE_CUDA(cudaMemcpyAsync(theta_h.data(), theta, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaMemcpyAsync(rho_h.data(), rho, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
@@ -291,7 +294,7 @@ static int check_eigs_args(fe_csr h, int nev, int block, int nblocks, double tol
   FE_ARG(is_pow2_le16(block), "fe_eigs: block = %d not in {1,2,4,8,16}", block);
   FE_ARG(nblocks >= 2, "fe_eigs: nblocks = %d < 2", nblocks);
   const int m = block * nblocks;
-  FE_ARG(m <= 96, "fe_eigs: subspace block*nblocks = %d > 96", m);
+  FE_ARG(m <= kRitzMax, "fe_eigs: subspace block*nblocks = %d > %d", m, kRitzMax);
   FE_ARG(nblocks + 1 <= kMaxBlocks - 1, "fe_eigs: too many blocks");
   FE_ARG(nev >= 1 && nev <= m - block, "fe_eigs: need 1 <= nev <= block*(nblocks-1), got nev = %d", nev);
   FE_ARG((int64_t)m + block <= h->n, "fe_eigs: subspace (%d + %d) exceeds n = %lld", m, block, (long long)h->n);

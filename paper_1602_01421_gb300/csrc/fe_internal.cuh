@@ -51,6 +51,10 @@ int num_sms();
 // blk[j].  The eigensolver's subspace slots, a user's contiguous V and single columns of a
 // block (bv = 1, ld = b) are all described this way.
 constexpr int kMaxBlocks = 40;
+// Rayleigh-Ritz: subspaces up to kRitzSmallMax are diagonalised entirely in shared memory,
+// larger ones (up to kRitzMax) keep the FP64 eigenvector matrix in a global workspace.
+constexpr int kRitzSmallMax = 96;
+constexpr int kRitzMax = 160;
 struct BlockSet {
   const void* blk[kMaxBlocks];
   int nv, bv, ld;

@@ -164,29 +164,33 @@ __device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, i
   }
 }
 
-// smem layout (mp = m rounded up to even, ld = mp + 1, rows padded):
+// smem layout (mp = m rounded up to even, ld = mp + 1, rows padded), m <= kRitzSmallMax:
 //   A64[mp][ld], Q64[mp][ld]             FP64 matrix and eigenvectors
 //   U: A32[mp][ld] + Q32[mp][ld] (FP32)  later reused as W[mp][ld] (FP64 scratch)
 //   cs, sn (mp/2 doubles each), pp, pq (mp/2 ints each), order (mp ints)
+// Larger subspaces (BIG, m <= kRitzMax): the FP32 pair A32 + Q32 occupies the A64 region and
+// A64 is rebuilt from H once the FP32 sweeps are done; Q64 and W live in `gwork`
+// (2 mp ld doubles of global memory, L2-resident).
 // Two precisions: FP32 Jacobi sweeps take the matrix to a relative off-diagonal norm of about
 // 1e-6 (FP32 rotations run at the FP32 rate of the SM, FP64 ones at 1/64 of it); the FP32
 // eigenvector matrix is made exactly orthogonal in FP64 (Cholesky QR), the FP64 matrix is
 // transformed by it (Q^T T Q, an exact orthogonal similarity), and FP64 sweeps finish from there
 // -- two or three, since Jacobi converges quadratically once the off-diagonal part is small.
+template <bool BIG>
 __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int which, int max_sweeps,
                             double tol, double* __restrict__ theta_out, double* __restrict__ Y_out,
-                            double* __restrict__ rho_out, int* __restrict__ info) {
+                            double* __restrict__ rho_out, int* __restrict__ info, double* gwork) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int mp = m + (m & 1);  // even size; index m (if odd) is a zero dummy never rotated
   const int ld = mp + 1;
   const size_t mat = (size_t)mp * ld;
   double* A = reinterpret_cast<double*>(smem_raw);
-  double* Q = A + mat;
-  double* W = Q + mat;
-  float* A32 = reinterpret_cast<float*>(W);
+  double* Q = BIG ? gwork : A + mat;
+  double* W = BIG ? gwork + mat : Q + mat;
+  float* A32 = BIG ? reinterpret_cast<float*>(A) : reinterpret_cast<float*>(W);
   float* Q32 = A32 + mat;
   const int np = mp / 2;  // rotation pairs per step
-  double* cs = W + mat;
+  double* cs = BIG ? A + mat : W + mat;
   double* sn = cs + np;
   int* pp = reinterpret_cast<int*>(sn + np);
   int* pq = pp + np;
@@ -199,7 +203,7 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
     const int i = e / mp, j = e % mp;
     double a = 0.0;
     if (i < m && j < m) a = 0.5 * (H[i * m + j] + H[j * m + i]);
-    A[i * ld + j] = a;
+    if (!BIG) A[i * ld + j] = a;
     A32[i * ld + j] = (float)a;
     Q32[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
@@ -207,7 +211,11 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
   double fro2;
   {
     double v = 0.0;
-    for (int e = tid; e < mp * mp; e += nth) v += A[(e / mp) * ld + e % mp] * A[(e / mp) * ld + e % mp];
+    for (int e = tid; e < m * m; e += nth) {
+      const int i = e / m, j = e % m;
+      const double a = 0.5 * (H[i * m + j] + H[j * m + i]);
+      v += a * a;
+    }
     fro2 = ritz_block_sum(v, red);
   }
   // FP32 sweeps
@@ -250,6 +258,13 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
     }
   }
   __syncthreads();
+  if (BIG) {  // the FP32 pair is dead: A64 takes its region back
+    for (int e = tid; e < mp * mp; e += nth) {
+      const int i = e / mp, j = e % mp;
+      A[i * ld + j] = (i < m && j < m) ? 0.5 * (H[i * m + j] + H[j * m + i]) : 0.0;
+    }
+    __syncthreads();
+  }
   // A <- Q^T A Q (W = A Q first; A is symmetric, the result is mirrored from its upper triangle)
   for (int e = tid; e < mp * mp; e += nth) {
     const int i = e / mp, j = e % mp;
@@ -312,22 +327,35 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
 
 size_t ritz_smem_bytes(int m) {
   const int mp = m + (m & 1);
-  return (size_t)3 * mp * (mp + 1) * sizeof(double) + (size_t)(mp / 2) * 2 * sizeof(double) +
+  const size_t mats = m <= kRitzSmallMax ? 3 : 1;
+  return mats * mp * (mp + 1) * sizeof(double) + (size_t)(mp / 2) * 2 * sizeof(double) +
          (size_t)(mp / 2) * 2 * sizeof(int) + (size_t)mp * sizeof(int) + 64;
 }
 
+size_t ritz_work_doubles(int m) {
+  const int mp = m + (m & 1);
+  return m <= kRitzSmallMax ? 0 : (size_t)2 * mp * (mp + 1);
+}
+
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
-                double* theta, double* Y, double* rho, int* info, cudaStream_t s) {
+                double* theta, double* Y, double* rho, int* info, double* work, cudaStream_t s) {
   const size_t smem = ritz_smem_bytes(m);
+  FE_ARG(m >= 1 && m <= kRitzMax, "ritz: subspace m = %d not in [1, %d]", m, kRitzMax);
   FE_ARG(smem <= 225 * 1024, "ritz: subspace m = %d too large", m);
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
-    configured = true;
+  const bool big = m > kRitzSmallMax;
+  FE_ARG(!big || work != nullptr, "ritz: m = %d needs a global workspace", m);
+  static bool configured[2] = {false, false};
+  if (!configured[big]) {
+    FE_CUDA(cudaFuncSetAttribute(big ? ritz_kernel<true> : ritz_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
+    configured[big] = true;
   }
   // one CTA: a rotation step is (m/2)^2 / 2 2 x 2 blocks plus m^2 / 2 Q updates between two
   // barriers; FP64 work on one SM runs at 2 DFMA per clock, hence the FP32 sweeps first
-  ritz_kernel<<<1, 256, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info);
+  if (big)
+    ritz_kernel<true><<<1, 512, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, work);
+  else
+    ritz_kernel<false><<<1, 256, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, nullptr);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;
