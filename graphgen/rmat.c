@@ -10,7 +10,8 @@
  * The stand-in recipe for the paper's power-law graphs (Section 4, Table "graphs"): edge factor
  * 16, a/b/c/d = 0.57/0.19/0.19/0.05, a seeded random relabelling of the vertices (so hubs are
  * spread over the id range, as in real graphs whose vertex connection is nearly random), then
- * symmetrise, drop self-loops and duplicate edges, 0/1 pattern-only CSR.
+ * symmetrise, drop self-loops and duplicate edges, 0/1 pattern-only CSR.  Directed graphs
+ * (the SVD path; the paper's page graph, Section 4.3.2) keep the draws as out-edges.
  *
  * Randomness: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) used as a counter-based hash of
  * (seed, stream, counter), so the graph depends only on the seed, not on the thread count.
@@ -58,12 +59,14 @@ static void sort_small(int32_t* v, int64_t len) {
 }
 
 /*
- * Symmetrise a directed edge list (src[e] -> dst[e]), dropping self-loops and duplicates,
- * into a CSR with sorted column indices.  Returns 0 on success, -1 on allocation failure.
- * *rowptr_out (n+1 int64) and *colidx_out (nnz int32) are malloc'ed; free with fe_gen_free.
+ * CSR of a directed edge list (src[e] -> dst[e]) with self-loops and duplicate edges
+ * dropped and sorted column indices.  symmetric != 0 stores every edge in both directions
+ * (an undirected graph); otherwise row u holds the out-neighbours of u.  Returns 0 on
+ * success, -1 on allocation failure.  *rowptr_out (n+1 int64) and *colidx_out (nnz int32)
+ * are malloc'ed; free with fe_gen_free.
  */
-int fe_gen_symmetrize(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                      int64_t** rowptr_out, int32_t** colidx_out, int64_t* nnz_out) {
+static int build_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int symmetric,
+                     int64_t** rowptr_out, int32_t** colidx_out, int64_t* nnz_out) {
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
   if (!cnt) return -1;
   #pragma omp parallel for schedule(static)
@@ -72,8 +75,10 @@ int fe_gen_symmetrize(int64_t n, int64_t m, const int32_t* src, const int32_t* d
     if (u == v) continue;
     #pragma omp atomic
     cnt[u + 1]++;
-    #pragma omp atomic
-    cnt[v + 1]++;
+    if (symmetric) {
+      #pragma omp atomic
+      cnt[v + 1]++;
+    }
   }
   for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
   int64_t total = cnt[n];
@@ -85,13 +90,16 @@ int fe_gen_symmetrize(int64_t n, int64_t m, const int32_t* src, const int32_t* d
   for (int64_t e = 0; e < m; ++e) {
     int32_t u = src[e], v = dst[e];
     if (u == v) continue;
-    int64_t pu, pv;
+    int64_t pu;
     #pragma omp atomic capture
     pu = cur[u]++;
-    #pragma omp atomic capture
-    pv = cur[v]++;
     tmp[pu] = v;
-    tmp[pv] = u;
+    if (symmetric) {
+      int64_t pv;
+      #pragma omp atomic capture
+      pv = cur[v]++;
+      tmp[pv] = u;
+    }
   }
   free(cur);
   /* sort + unique each row in place, record unique counts */
@@ -123,13 +131,26 @@ int fe_gen_symmetrize(int64_t n, int64_t m, const int32_t* src, const int32_t* d
   return 0;
 }
 
+/* Undirected graph of an edge list (both directions stored). */
+int fe_gen_symmetrize(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      int64_t** rowptr_out, int32_t** colidx_out, int64_t* nnz_out) {
+  return build_csr(n, m, src, dst, 1, rowptr_out, colidx_out, nnz_out);
+}
+
+/* Directed graph of an edge list (row u = out-neighbours of u). */
+int fe_gen_directed(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                    int64_t** rowptr_out, int32_t** colidx_out, int64_t* nnz_out) {
+  return build_csr(n, m, src, dst, 0, rowptr_out, colidx_out, nnz_out);
+}
+
 /*
- * Generate a symmetrised R-MAT graph with n = 2^scale vertices and edge_factor * n
- * directed draws.  permute != 0 applies the seeded vertex relabelling.
+ * Generate an R-MAT graph with n = 2^scale vertices and edge_factor * n directed draws.
+ * permute != 0 applies the seeded vertex relabelling; directed != 0 keeps the draws as
+ * directed edges (row u = out-neighbours), otherwise the graph is symmetrised.
  */
-int fe_gen_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
-                int permute, int64_t* n_out, int64_t** rowptr_out, int32_t** colidx_out,
-                int64_t* nnz_out) {
+int fe_gen_rmat_ex(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
+                   int permute, int directed, int64_t* n_out, int64_t** rowptr_out,
+                   int32_t** colidx_out, int64_t* nnz_out) {
   if (scale < 1 || scale > 30 || edge_factor < 1) return -2;
   int64_t n = (int64_t)1 << scale;
   int64_t m = edge_factor * n;
@@ -156,11 +177,19 @@ int fe_gen_rmat(int scale, int64_t edge_factor, double a, double b, double c, ui
     dst[e] = permute ? perm[v] : (int32_t)v;
   }
   free(perm);
-  int rc = fe_gen_symmetrize(n, m, src, dst, rowptr_out, colidx_out, nnz_out);
+  int rc = build_csr(n, m, src, dst, directed ? 0 : 1, rowptr_out, colidx_out, nnz_out);
   free(src);
   free(dst);
   if (rc == 0) *n_out = n;
   return rc;
+}
+
+/* Symmetrised R-MAT graph (see fe_gen_rmat_ex). */
+int fe_gen_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
+                int permute, int64_t* n_out, int64_t** rowptr_out, int32_t** colidx_out,
+                int64_t* nnz_out) {
+  return fe_gen_rmat_ex(scale, edge_factor, a, b, c, seed, permute, 0, n_out, rowptr_out,
+                        colidx_out, nnz_out);
 }
 
 void fe_gen_free(void* p) { free(p); }

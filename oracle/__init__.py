@@ -9,6 +9,7 @@ Contents (each function cites the passage it follows):
   core.jacobi                  projected m x m eigenproblem, Algorithm 1 step (2)
   blockops                     the dense operations of Table 1 (MvTransMv, MvTimesMatAddMv, ...)
   bks.block_krylov_schur       the Block Krylov-Schur eigensolver (Sections 3.1, 1, 4.3)
+  svd.svds / svd.transpose     singular triplets of a directed graph via A^T A (Section 4.3.2)
   rng                          the counter-based start/replacement block generator
   mlp                          the learned start block's network (forward, backward)
 """
