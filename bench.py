@@ -422,6 +422,44 @@ def run_ours(args):
         except Exception as e:
             many = {"error": str(e)}
 
+    # ---- SVD of a directed graph (the paper's page-graph method): directed R-MAT of the same
+    # scale, 8 singular values through A^T A, block 2 and 2 x 8 blocks (the paper's setting)
+    svd_res = None
+    if not args.no_svd:
+        try:
+            out = {}
+            gd = graphgen.rmat(args.scale, seed=1, directed=True)
+            svd_res = {"graph": f"directed rmat{args.scale}-ef16", "n": gd.n, "nnz": gd.nnz,
+                       "nsv": 8, "block": 2, "nblocks": 16}
+            with fe.Csr.from_graph(gd) as hd:
+                for key, fn in (("spmm", fe.spmm), ("spmm_t", fe.spmm_t)):
+                    Xs = fe.random_normal(gd.n, 2, dtype=torch.float32, seed=3)
+                    Ys = torch.empty_like(Xs)
+                    fn(hd, Xs, Ys)
+                    ts = statistics.median(time_cuda(lambda: fn(hd, Xs, Ys), 10, torch))
+                    svd_res[f"{key}_f32_b2"] = {
+                        "ms": round(ts, 4),
+                        "GBps": round(spmm_bytes(gd.n, gd.nnz, 2, 4) / (ts / 1000.0) / 1e9, 1)}
+                sv0 = None
+                for mode in ("fp64", "mixed"):
+                    def run_svd():
+                        out["s"] = fe.svds(hd, 8, 2, 16, TOL, seed=1, mode=mode,
+                                           max_restarts=MAX_RESTARTS)
+                    run_svd()
+                    tsv = time_cuda(run_svd, 1, torch)[0]
+                    sv, Vr, Ul, sts = out["s"]
+                    svd_res[mode] = {"s": tsv / 1000.0, "restarts": sts["restarts"],
+                                     "ata_applications": sts["spmm_blocks"],
+                                     "converged": sts["converged"]}
+                    if sv0 is None:
+                        sv0 = sv
+                        svd_res["svals_head"] = [float(x) for x in sv[:3]]
+                    else:
+                        svd_res[mode]["max_rel_sval_diff_vs_fp64"] = float(np.max(np.abs(sv - sv0) / sv0))
+            del gd
+        except Exception as e:
+            svd_res = {"error": str(e)}
+
     # ---- semi-external: the same SpMM with the CSR streamed from pinned host memory
     semi = None
     if not args.no_semi:
@@ -468,7 +506,7 @@ def run_ours(args):
             "time_to_8_eigenpairs_s": ms_per_step / 1000.0,
             "eigs": {"restarts": stats[-1]["restarts"], "spmm_blocks": blocks,
                      "evals_head": [float(x) for x in ev[:3]], "max_resid": stats[-1]["max_resid"]},
-            "mixed": t_mixed, "learned": learned_res, "many_eigs": many, "semi_external": semi,
+            "mixed": t_mixed, "learned": learned_res, "many_eigs": many, "svd": svd_res, "semi_external": semi,
             "spmm_sweep": sweep, "spmm_roofline": spmm_roofline, "roofline": roofline,
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": int(launches),
@@ -585,6 +623,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-many", action="store_true", help="skip the nev 32 (m = 128) leg")
+    ap.add_argument("--no-svd", action="store_true", help="skip the directed-graph SVD leg")
     ap.add_argument("--no-semi", action="store_true")
 
     # dram__bytes_read.sum + dram__bytes_write.sum of update_gram_kernel<double,4,4,1> at the

@@ -98,6 +98,10 @@ typedef struct {
    * buffers, copies overlapped with the previous panel's kernels); 1 = direct (the kernels read
    * the packed panels in pinned host memory through its device mapping, with no copies). */
   int semi_direct;
+  /* 1 = also build the transposed pattern A^T (host counting sort at create, then its own
+   * SpMM plan), needed by fe_spmm_t and fe_svds: a directed graph's adjacency matrix is not
+   * symmetric (Section 4.3.2).  Resident handles only.  Default 0. */
+  int transpose;
 } fe_csr_opts;
 
 /* Fill *opts with the defaults. */
@@ -114,6 +118,7 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the handle */
   int semi_external;    /* 1 if the CSR streams from pinned host memory */
   int64_t panels;       /* semi-external row panels (0 when resident) */
+  int has_transpose;    /* 1 if A^T was built (fe_csr_opts.transpose) */
 } fe_csr_info;
 
 /*
@@ -143,6 +148,15 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info);
  * FE_ERR_CUDA, FE_ERR_TIMEOUT (semi-external copy wait).  Asynchronous when resident.
  */
 int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
+
+/*
+ * Transposed SpMM: Y = A^T X, i.e. Y[j, :] = sum over the non-zeros (i, j) of X[i, :] -- the
+ * second half of the operator A^T A that the SVD of a directed graph's adjacency matrix
+ * iterates with (Section 4.3.2).  Same arguments, layout and errors as fe_spmm; the handle
+ * must have been created with fe_csr_opts.transpose = 1 (else FE_ERR_INVALID).  It runs the
+ * fe_spmm kernels on the transposed pattern built at create.  Asynchronous.
+ */
+int fe_spmm_t(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
 
 /*
  * MvTransMv (Table 1, "op3"): G = alpha * V^T W.
@@ -318,6 +332,22 @@ int fe_eigs(fe_csr h, int nev, int block, int nblocks, double tol, fe_which whic
             double* evals, double* evecs);
 int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
                const fe_eigs_opts* opts, double* evals, double* evecs, fe_eigs_stats* stats);
+
+/*
+ * Singular value decomposition of a (directed graph's) 0/1 matrix A, Section 4.3.2: the nsv
+ * largest singular values sigma_1 >= ... >= sigma_nsv with right and left singular vectors.
+ * The Block Krylov-Schur iteration of fe_eigs_ex runs on the symmetric positive semidefinite
+ * operator A^T A (one fe_spmm and one fe_spmm_t per block), largest eigenvalues first; then
+ * sigma_i = sqrt(theta_i), v_i = the Ritz vectors, u_i = A v_i / sigma_i (0 if sigma_i = 0).
+ * The convergence test is fe_eigs_ex's, applied to A^T A (tol relative to theta = sigma^2).
+ * The handle needs fe_csr_opts.transpose = 1 and must be resident.  block, nblocks, opts as
+ * for fe_eigs_ex (modes FP64 and MIXED; starts RANDOM and USER; FE_START_LEARNED is rejected).
+ * svals: HOST, nsv doubles.  right, left: DEVICE, n x nsv COLUMN-major FP64, each may be
+ * NULL; each v_i has its largest-magnitude entry positive.  stats->spmm_blocks counts
+ * applications of A^T A (two SpMMs each).  Synchronous.  Errors as fe_eigs_ex.
+ */
+int fe_svds(fe_csr h, int nsv, int block, int nblocks, double tol, const fe_eigs_opts* opts,
+            double* svals, double* right, double* left, fe_eigs_stats* stats);
 
 #ifdef __cplusplus
 }

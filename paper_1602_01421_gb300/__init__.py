@@ -14,6 +14,7 @@ from . import _lib
 from ._lib import FeError, check, load
 
 __all__ = ["Csr", "spmm", "block_gram", "block_update", "block_update_gram", "block_orth", "random_normal", "eigs",
+           "spmm_t", "svds",
            "FeError", "load", "library_path"]
 
 library_path = _lib.LIB_PATH
@@ -52,7 +53,7 @@ class Csr:
     def __init__(self, rowptr: np.ndarray, colidx: np.ndarray, *, validate: bool = True,
                  check_symmetric: bool = False, device_mem_cap_bytes: int = 0,
                  tail_max: int = 0, hub_min: int = 0, hub_chunk: int = 0, panel_nnz: int = 0,
-                 copy_timeout_ms: int = 0, semi_direct: bool = False):
+                 copy_timeout_ms: int = 0, semi_direct: bool = False, transpose: bool = False):
         lib = load()
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(colidx, dtype=np.int32)
@@ -65,6 +66,7 @@ class Csr:
         o.tail_max, o.hub_min, o.hub_chunk = int(tail_max), int(hub_min), int(hub_chunk)
         o.panel_nnz, o.copy_timeout_ms = int(panel_nnz), int(copy_timeout_ms)
         o.semi_direct = int(semi_direct)
+        o.transpose = int(transpose)
         h = ctypes.c_void_p()
         check(lib.fe_csr_create_ex(self.n, self._rowptr.ctypes.data_as(ctypes.c_void_p),
                                    self._colidx.ctypes.data_as(ctypes.c_void_p),
@@ -74,6 +76,9 @@ class Csr:
 
     @classmethod
     def from_graph(cls, g, **kw):
+        """Handle of graph g's adjacency pattern; a directed graph also gets A^T (for spmm_t
+        and svds) unless `transpose` is given."""
+        kw.setdefault("transpose", bool(getattr(g, "directed", False)))
         return cls(g.rowptr, g.colidx, **kw)
 
     @property
@@ -113,6 +118,17 @@ def spmm(h: Csr, X, Y=None):
     b = 1 if X.dim() == 1 else X.shape[1]
     _stream()
     check(load().fe_spmm(h.handle, _dev(X, "X"), _dev(Y, "Y"), b, _dt(X)))
+    return Y
+
+
+def spmm_t(h: Csr, X, Y=None):
+    """Y = A^T X (fe_spmm_t); the handle needs transpose=True."""
+    torch = _torch()
+    if Y is None:
+        Y = torch.empty_like(X)
+    b = 1 if X.dim() == 1 else X.shape[1]
+    _stream()
+    check(load().fe_spmm_t(h.handle, _dev(X, "X"), _dev(Y, "Y"), b, _dt(X)))
     return Y
 
 
@@ -224,6 +240,43 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
     if rc != _lib.FE_OK and not (rc == _lib.FE_ERR_NOCONVERGE and not raise_on_noconverge):
         check(rc)
     return evals, (None if evecs_cm is None else evecs_cm.t()), stats
+
+
+def svds(h: Csr, nsv: int, block: int, nblocks: int, tol: float = 1e-8, *, mode: str = "fp64",
+         start=None, seed: int = 1, max_restarts: int = 500, mixed_tol: float = 5e-6,
+         orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True):
+    """Largest singular triplets of the handle's matrix (fe_svds; needs transpose=True).
+    Returns (svals numpy, right (n, nsv) CUDA float64 or None, left (n, nsv) or None, stats)."""
+    torch = _torch()
+    lib = load()
+    o = _lib.EigsOpts()
+    lib.fe_eigs_opts_default(ctypes.byref(o))
+    o.seed = int(seed)
+    o.max_restarts = int(max_restarts)
+    o.mode = _lib.MODE[mode]
+    o.mixed_tol = float(mixed_tol)
+    o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
+    if start is not None:
+        start = start.to(torch.float64).contiguous()
+        o.start = _lib.START["user"]
+        o.start_block = start.data_ptr()
+    svals = np.zeros(nsv, dtype=np.float64)
+    right = left = None
+    if return_vectors:
+        right = torch.empty((nsv, h.n), dtype=torch.float64, device="cuda")
+        left = torch.empty((nsv, h.n), dtype=torch.float64, device="cuda")
+    st = _lib.EigsStats()
+    _stream()
+    rc = lib.fe_svds(h.handle, nsv, block, nblocks, float(tol), ctypes.byref(o),
+                     svals.ctypes.data_as(ctypes.c_void_p),
+                     None if right is None else ctypes.c_void_p(right.data_ptr()),
+                     None if left is None else ctypes.c_void_p(left.data_ptr()), ctypes.byref(st))
+    stats = {f: getattr(st, f) for f, _ in _lib.EigsStats._fields_}
+    stats["converged"] = rc == _lib.FE_OK
+    if rc != _lib.FE_OK and not (rc == _lib.FE_ERR_NOCONVERGE and not raise_on_noconverge):
+        check(rc)
+    return (svals, None if right is None else right.t(), None if left is None else left.t(),
+            stats)
 
 
 # ---------------------------------------------------------------- learned start block

@@ -28,7 +28,7 @@ class CsrOpts(ctypes.Structure):
                 ("check_symmetric", ctypes.c_int), ("tail_max", ctypes.c_int),
                 ("hub_min", ctypes.c_int), ("hub_chunk", ctypes.c_int),
                 ("panel_nnz", ctypes.c_int64), ("copy_timeout_ms", ctypes.c_int),
-                ("semi_direct", ctypes.c_int)]
+                ("semi_direct", ctypes.c_int), ("transpose", ctypes.c_int)]
 
 
 class CsrInfo(ctypes.Structure):
@@ -36,7 +36,8 @@ class CsrInfo(ctypes.Structure):
                 ("rows_tail", ctypes.c_int64), ("rows_mid", ctypes.c_int64),
                 ("rows_hub", ctypes.c_int64), ("hub_chunks", ctypes.c_int64),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("semi_external", ctypes.c_int), ("panels", ctypes.c_int64)]
+                ("semi_external", ctypes.c_int), ("panels", ctypes.c_int64),
+                ("has_transpose", ctypes.c_int)]
 
 
 class EigsOpts(ctypes.Structure):
@@ -83,6 +84,9 @@ def load(build_if_missing: bool = True):
             "fe_csr_destroy": (i32, [vp]),
             "fe_csr_get_info": (i32, [vp, ctypes.POINTER(CsrInfo)]),
             "fe_spmm": (i32, [vp, vp, vp, i32, i32]),
+            "fe_spmm_t": (i32, [vp, vp, vp, i32, i32]),
+            "fe_svds": (i32, [vp, i32, i32, i32, dbl, ctypes.POINTER(EigsOpts), vp, vp, vp,
+                              ctypes.POINTER(EigsStats)]),
             "fe_block_gram": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_block_update": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, i32]),
             "fe_block_update_gram": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, vp]),

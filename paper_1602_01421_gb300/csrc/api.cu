@@ -129,6 +129,20 @@ static int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx)
   return FE_OK;
 }
 
+// Pattern of A^T: the non-zero (i, j) becomes (j, i).  Counting sort by column; rows of A are
+// visited in order, so every row of A^T comes out sorted.
+static void transpose_pattern(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                              std::vector<int64_t>& trp, std::vector<int32_t>& tci) {
+  const int64_t nnz = rowptr[n];
+  trp.assign(n + 1, 0);
+  for (int64_t p = 0; p < nnz; ++p) trp[colidx[p] + 1]++;
+  for (int64_t i = 0; i < n; ++i) trp[i + 1] += trp[i];
+  tci.resize(nnz > 0 ? nnz : 1);
+  std::vector<int64_t> cur(trp.begin(), trp.end() - 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) tci[cur[colidx[p]]++] = (int32_t)i;
+}
+
 static int check_symmetric(int64_t n, const int64_t* rowptr, const int32_t* colidx) {
   // transpose by counting sort, then compare the sorted rows of A and A^T
   int64_t nnz = rowptr[n];
@@ -165,6 +179,7 @@ int fe_csr_create(int64_t n, const int64_t* rowptr, const int32_t* colidx, fe_cs
 int fe_csr_destroy(fe_csr h) {
   if (!h) return FE_OK;
   cudaDeviceSynchronize();
+  if (h->t) fe_csr_destroy(h->t);
   if (h->semi_external) semiext_destroy(h);
   for (void* p : h->allocations) cudaFree(p);
   delete h;
@@ -185,6 +200,8 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   FE_ARG(nnz == 0 || colidx != nullptr, "fe_csr_create: colidx is NULL");
   if (o.validate) FE_TRY(validate_csr(n, rowptr, colidx));
   if (o.check_symmetric) FE_TRY(check_symmetric(n, rowptr, colidx));
+  FE_ARG(!o.transpose || o.device_mem_cap_bytes <= 0,
+         "fe_csr_create: transpose needs a resident handle (device_mem_cap_bytes = 0)");
   fe_csr h = new fe_csr_s();
   h->n = n;
   h->nnz = nnz;
@@ -198,6 +215,16 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
     rc = semiext_create(h, rowptr, colidx, o);
   } else {
     rc = spmm_build_plan(h, rowptr, colidx, tail_max, hub_min, hub_chunk);
+  }
+  if (rc == FE_OK && o.transpose) {
+    std::vector<int64_t> trp;
+    std::vector<int32_t> tci;
+    transpose_pattern(n, rowptr, colidx, trp, tci);
+    fe_csr_opts ot = o;
+    ot.transpose = 0;
+    ot.validate = 0;
+    ot.check_symmetric = 0;
+    rc = fe_csr_create_ex(n, trp.data(), tci.data(), &ot, &h->t);
   }
   if (rc != FE_OK) {
     std::string msg = fe_last_error();
@@ -220,10 +247,17 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info) {
   info->rows_hub = h->rows_hub;
   info->hub_chunks = h->plan.nhub_tasks;
   info->max_degree = h->max_degree;
-  info->device_bytes = h->device_bytes;
+  info->device_bytes = h->device_bytes + (h->t ? h->t->device_bytes : 0);
   info->semi_external = h->semi_external;
   info->panels = h->semi_external ? semiext_panels(h) : 0;
+  info->has_transpose = h->t != nullptr;
   return FE_OK;
+}
+
+int fe_spmm_t(fe_csr h, const void* X, void* Y, int b, fe_dtype dt) {
+  FE_ARG(h != nullptr, "fe_spmm_t: NULL handle");
+  FE_ARG(h->t != nullptr, "fe_spmm_t: the handle has no transpose (create it with transpose = 1)");
+  return fe_spmm(h->t, X, Y, b, dt);
 }
 
 int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt) {

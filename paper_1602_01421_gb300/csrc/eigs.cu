@@ -75,12 +75,13 @@ struct Phase {
   uint64_t seed;
   int max_restarts, max_sweeps;
   int pass1_f32 = 0;  // FP64 subspace: first Gram-Schmidt pass's Gram in FP32 arithmetic
+  int op_ata = 0;  // 1: iterate with A^T A (SVD of a directed graph's matrix, Section 4.3.2)
   int stagnation_window = 0;  // > 0: stop when the worst wanted rho/scale has not halved
                               // over this many restarts (FP32 phase: at its precision floor
                               // the ratio only fluctuates)
   cudaStream_t s;
   // state
-  DevBuf vmem, hmem, small, xmem, ritzwork;
+  DevBuf vmem, hmem, small, xmem, ritzwork, opbuf;
   std::vector<void*> slot, spare, xblk, axblk;
   double *H = nullptr, *theta = nullptr, *Y = nullptr, *rho = nullptr, *anorm = nullptr,
          *Cdiag = nullptr, *gtmp = nullptr;
@@ -114,6 +115,7 @@ struct Phase {
     gtmp = Cdiag + 256;
     info = reinterpret_cast<int*>(gtmp + 64 * 16);
     if (ritz_work_doubles(m) > 0) FE_TRY(ritzwork.alloc(sizeof(double) * ritz_work_doubles(m)));
+    if (op_ata) FE_TRY(opbuf.alloc(blk));
     theta_h.resize(m);
     rho_h.resize(m);
     resid_h.assign(nev, 0.0);
@@ -149,7 +151,12 @@ struct Phase {
     return FE_OK;
   }
 
+  // Yb = Op X: A X, or A^T (A X) for the SVD operator
   int spmm_dispatch(const void* X, void* Yb) {
+    if (op_ata) {
+      FE_TRY(spmm_resident(h, X, opbuf.p, b, dt, s));
+      return spmm_resident(h->t, opbuf.p, Yb, b, dt, s);
+    }
     if (h->semi_external) return semiext_spmm(h, X, Yb, b, dt, s);
     return spmm_resident(h, X, Yb, b, dt, s);
   }
@@ -334,8 +341,15 @@ int fe_eigs(fe_csr h, int nev, int block, int nblocks, double tol, fe_which whic
   return fe_eigs_ex(h, nev, block, nblocks, tol, which, &o, evals, evecs, nullptr);
 }
 
-int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
-               const fe_eigs_opts* opts, double* evals, double* evecs, fe_eigs_stats* stats) {
+}  // extern "C"
+
+namespace fe {
+
+// The Block Krylov-Schur driver behind fe_eigs_ex (op_ata = 0: A) and fe_svds (op_ata = 1:
+// A^T A); evecs is the column-major output of the Ritz vectors.
+static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
+                 const fe_eigs_opts* opts, int op_ata, double* evals, double* evecs,
+                 fe_eigs_stats* stats) {
   const auto t0 = std::chrono::steady_clock::now();
   FE_TRY(check_eigs_args(h, nev, block, nblocks, tol, which));
   FE_ARG(evals != nullptr, "fe_eigs: evals is NULL");
@@ -374,6 +388,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
   p1.max_restarts = o.max_restarts;
   p1.max_sweeps = o.max_sweeps;
   p1.pass1_f32 = o.orth_pass1 == 0;
+  p1.op_ata = op_ata;
   p1.s = s;
   int rc;
   double secs32 = 0.0;
@@ -436,6 +451,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
     p2.max_restarts = o.max_restarts;
     p2.max_sweeps = o.max_sweeps;
     p2.pass1_f32 = o.orth_pass1 == 0;
+    p2.op_ata = op_ata;
     p2.s = s;
     p2.tol = tol;
     p2.dt = FE_F64;
@@ -464,6 +480,64 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
   }
   if (rc == FE_ERR_NOCONVERGE)
     return set_error(FE_ERR_NOCONVERGE, "fe_eigs: not converged after %d restarts", o.max_restarts);
+  return FE_OK;
+}
+
+// U[:, c] *= inv[c] for the column-major n x k matrix U
+__global__ void scale_cols_kernel(double* __restrict__ U, int64_t n, int k, const double* __restrict__ inv) {
+  const int c = blockIdx.y;
+  const double f = inv[c];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    U[(int64_t)c * n + r] *= f;
+}
+
+}  // namespace fe
+
+extern "C" {
+
+int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
+               const fe_eigs_opts* opts, double* evals, double* evecs, fe_eigs_stats* stats) {
+  return solve(h, nev, block, nblocks, tol, which, opts, 0, evals, evecs, stats);
+}
+
+int fe_svds(fe_csr h, int nsv, int block, int nblocks, double tol, const fe_eigs_opts* opts,
+            double* svals, double* right, double* left, fe_eigs_stats* stats) {
+  FE_ARG(h != nullptr, "fe_svds: NULL handle");
+  FE_ARG(h->t != nullptr, "fe_svds: the handle has no transpose (create it with transpose = 1)");
+  FE_ARG(!h->semi_external, "fe_svds: the handle must be resident");
+  FE_ARG(svals != nullptr, "fe_svds: svals is NULL");
+  FE_ARG(!opts || opts->start != FE_START_LEARNED, "fe_svds: FE_START_LEARNED is not supported");
+  cudaStream_t s = cur_stream();
+  const int64_t n = h->n;
+  DevBuf vtmp;
+  double* V = right;
+  if (!V && left) {
+    FE_TRY(vtmp.alloc(sizeof(double) * (size_t)n * nsv));
+    V = vtmp.as<double>();
+  }
+  std::vector<double> theta(nsv);
+  const int rc = solve(h, nsv, block, nblocks, tol, FE_LA, opts, 1, theta.data(), V, stats);
+  if (rc != FE_OK && rc != FE_ERR_NOCONVERGE) return rc;
+  std::vector<double> inv(nsv);
+  for (int c = 0; c < nsv; ++c) {
+    svals[c] = sqrt(std::max(theta[c], 0.0));
+    inv[c] = svals[c] > 0.0 ? 1.0 / svals[c] : 0.0;
+  }
+  if (left) {
+    // u_c = A v_c / sigma_c, one column at a time (b = 1 SpMMs on the column-major V)
+    for (int c = 0; c < nsv; ++c)
+      FE_TRY(spmm_resident(h, V + (size_t)c * n, left + (size_t)c * n, 1, FE_F64, s));
+    DevBuf dinv;
+    FE_TRY(dinv.alloc(sizeof(double) * nsv));
+    FE_CUDA(cudaMemcpyAsync(dinv.p, inv.data(), sizeof(double) * nsv, cudaMemcpyHostToDevice, s));
+    const int parts = (int)std::min<int64_t>(ceil_div(n, 256), 4 * num_sms());
+    scale_cols_kernel<<<dim3(parts, nsv), 256, 0, s>>>(left, n, nsv, dinv.as<double>());
+    count_launch();
+    FE_CUDA(cudaGetLastError());
+    FE_CUDA(cudaStreamSynchronize(s));
+  }
+  if (rc == FE_ERR_NOCONVERGE)
+    return set_error(FE_ERR_NOCONVERGE, "fe_svds: not converged");
   return FE_OK;
 }
 

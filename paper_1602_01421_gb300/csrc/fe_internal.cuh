@@ -133,6 +133,7 @@ struct fe_csr_s {
   int semi_external = 0;
   fe::SemiExt* sx = nullptr;
   std::vector<void*> allocations;
+  fe_csr_s* t = nullptr;   // A^T (fe_csr_opts.transpose), owned
 };
 
 namespace fe {

@@ -58,6 +58,8 @@ def test_asymmetric_pattern_rejected_when_checked():
 def test_null_and_bad_arguments():
     lib = fe.load()
     assert lib.fe_spmm(None, None, None, 4, 0) == _lib.FE_ERR_INVALID
+    assert lib.fe_spmm_t(None, None, None, 4, 0) == _lib.FE_ERR_INVALID
+    assert lib.fe_svds(None, 8, 2, 16, 1e-8, None, None, None, None, None) == _lib.FE_ERR_INVALID
     assert lib.fe_eigs(None, 8, 4, 8, 1e-8, 0, None, None) == _lib.FE_ERR_INVALID
     assert lib.fe_block_gram(None, 10, 1, 4, None, 4, 0, 1.0, None) == _lib.FE_ERR_INVALID
     assert lib.fe_block_update(None, 10, 1, 3, None, 1.0, 0.0, ctypes.c_void_p(16), 4, 0) == _lib.FE_ERR_INVALID
@@ -68,8 +70,8 @@ def test_null_and_bad_arguments():
 
 def test_struct_layouts_match_header():
     # field offsets the C compiler gives the structs (x86-64 and aarch64 share the LP64 ABI)
-    assert ctypes.sizeof(_lib.CsrOpts) == 48  # semi_direct fits the tail padding
-    assert ctypes.sizeof(_lib.CsrInfo) == 88
+    assert ctypes.sizeof(_lib.CsrOpts) == 56
+    assert ctypes.sizeof(_lib.CsrInfo) == 96
     assert ctypes.sizeof(_lib.EigsOpts) == 64
     assert ctypes.sizeof(_lib.EigsStats) == 72
 
