@@ -82,7 +82,8 @@ typedef struct {
   /* 1 = additionally check that the pattern is symmetric and free of self-loops
    * (O(nnz log deg) on the host).  Default 0. */
   int check_symmetric;
-  /* Rows with degree <= tail_max go to the degree-sorted slice format (0 = default 16);
+  /* Rows with degree <= tail_max (at most 128) go to the degree-sorted slice format, one row
+   * per lane (0 = default 128);
    * rows with degree > hub_min are split into chunks of hub_chunk non-zeros
    * (0 = defaults 4096 / 4096).  Tuning knobs only; results do not depend on them beyond
    * floating-point summation order. */
@@ -119,6 +120,8 @@ typedef struct {
   int semi_external;    /* 1 if the CSR streams from pinned host memory */
   int64_t panels;       /* semi-external row panels (0 when resident) */
   int has_transpose;    /* 1 if A^T was built (fe_csr_opts.transpose) */
+  int tail_max;         /* the degree cutoff of the slice format in use (semi-external handles
+                         * with the default may use a smaller one than resident ones) */
 } fe_csr_info;
 
 /*

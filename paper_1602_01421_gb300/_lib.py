@@ -37,7 +37,7 @@ class CsrInfo(ctypes.Structure):
                 ("rows_hub", ctypes.c_int64), ("hub_chunks", ctypes.c_int64),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("semi_external", ctypes.c_int), ("panels", ctypes.c_int64),
-                ("has_transpose", ctypes.c_int)]
+                ("has_transpose", ctypes.c_int), ("tail_max", ctypes.c_int)]
 
 
 class EigsOpts(ctypes.Structure):

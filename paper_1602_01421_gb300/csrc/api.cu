@@ -206,7 +206,7 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   h->n = n;
   h->nnz = nnz;
   cudaGetDevice(&h->device);
-  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, 32) : 16;
+  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, kMaxTailDegree) : kDefaultTailMax;
   int hub_min = o.hub_min > 0 ? o.hub_min : 4096;
   int hub_chunk = o.hub_chunk > 0 ? o.hub_chunk : 4096;
   if (hub_min < tail_max) hub_min = tail_max;
@@ -251,6 +251,7 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info) {
   info->semi_external = h->semi_external;
   info->panels = h->semi_external ? semiext_panels(h) : 0;
   info->has_transpose = h->t != nullptr;
+  info->tail_max = h->plan.tail_max;
   return FE_OK;
 }
 

@@ -51,6 +51,10 @@ int num_sms();
 // blk[j].  The eigensolver's subspace slots, a user's contiguous V and single columns of a
 // block (bv = 1, ld = b) are all described this way.
 constexpr int kMaxBlocks = 40;
+// SpMM plan: rows of degree <= tail_max (at most kMaxTailDegree) go to degree-bucketed slices.
+constexpr int kMaxTailDegree = 128;
+constexpr int kDefaultTailMax = 128;
+constexpr int kMaxBuckets = kMaxTailDegree + 1;
 // Rayleigh-Ritz: subspaces up to kRitzSmallMax are diagonalised entirely in shared memory,
 // larger ones (up to kRitzMax) keep the FP64 eigenvector matrix in a global workspace.
 constexpr int kRitzSmallMax = 96;
@@ -107,9 +111,9 @@ struct fe_spmm_plan {
   int64_t nslices = 0;
   int32_t* d_slice_rows = nullptr;   // nslices * 32 row ids (-1 = padding)
   int32_t* d_ell = nullptr;          // slice-major transposed column indices
-  int32_t deg_slice_begin[34];       // first slice of degree d-bucket, in bucket order
-  int64_t deg_ell_base[34];          // ELL offset of that bucket's first slice
-  int32_t deg_of_bucket[34];
+  int32_t deg_slice_begin[fe::kMaxBuckets];  // first slice of degree d-bucket, in bucket order
+  int64_t deg_ell_base[fe::kMaxBuckets];     // ELL offset of that bucket's first slice
+  int32_t deg_of_bucket[fe::kMaxBuckets];
   int nbuckets = 0;
   // warp tasks: hub chunks first (partial slots 0..nhub_tasks-1), then mid rows by degree
   int64_t ntasks = 0, nhub_tasks = 0, nhub = 0;
@@ -124,8 +128,7 @@ struct fe_csr_s {
   int device = 0;
   int64_t max_degree = 0;
   int64_t rows_empty = 0, rows_tail = 0, rows_mid = 0, rows_hub = 0;
-  int64_t* d_rowptr = nullptr;
-  int32_t* d_colidx = nullptr;
+  int32_t* d_colidx = nullptr;   // column indices of the warp-task rows (tail rows: in the ELL)
   fe_spmm_plan plan;
   fe::DevBuf partials;     // hub partial sums (nhub_tasks * 16 * 8 bytes)
   int64_t device_bytes = 0;
@@ -146,11 +149,12 @@ struct Task {
 struct HostPlan {
   int64_t max_degree = 0, rows_empty = 0, rows_tail = 0, rows_mid = 0, rows_hub = 0;
   int nbuckets = 0;
-  int32_t deg_of_bucket[34], deg_slice_begin[34];
-  int64_t deg_ell_base[34];
-  int64_t nslices = 0, ell_total = 0, ntasks = 0, nhub_tasks = 0, nhub = 0;
+  int32_t deg_of_bucket[kMaxBuckets], deg_slice_begin[kMaxBuckets];
+  int64_t deg_ell_base[kMaxBuckets];
+  int64_t nslices = 0, ell_total = 0, ntasks = 0, nhub_tasks = 0, nhub = 0, tcol_total = 0;
   std::vector<int32_t> slice_rows, ell, hub_rows, hub_task_begin;
-  std::vector<Task> tasks;
+  std::vector<int32_t> tcol;  // column indices of the task rows (mid and hub), in row order
+  std::vector<Task> tasks;    // start: offset into tcol
 };
 // Device pointers of a plan (the resident handle's, or one streamed panel's).
 struct PlanView {
@@ -161,8 +165,8 @@ struct PlanView {
   const int32_t* ell;
   int64_t nslices;
   int nbuckets;
-  int32_t deg_of_bucket[34], deg_slice_begin[34];
-  int64_t deg_ell_base[34];
+  int32_t deg_of_bucket[kMaxBuckets], deg_slice_begin[kMaxBuckets];
+  int64_t deg_ell_base[kMaxBuckets];
   const int32_t* hub_rows;
   const int32_t* hub_task_begin;
   int64_t nhub;

@@ -24,8 +24,8 @@ struct PanelInfo {
   size_t off_colidx, off_slice_rows, off_ell, off_tasks, off_hub_rows, off_hub_begin, bytes;
   size_t host_off;  // offset of the packed panel in the pinned arena
   int nbuckets;
-  int32_t deg_of_bucket[34], deg_slice_begin[34];
-  int64_t deg_ell_base[34];
+  int32_t deg_of_bucket[kMaxBuckets], deg_slice_begin[kMaxBuckets];
+  int64_t deg_ell_base[kMaxBuckets];
   int64_t nslices, ntasks, nhub_tasks, nhub;
 };
 
@@ -47,8 +47,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Bytes a row adds to a packed panel (estimate used to cut panels).
 static size_t row_bytes(int64_t d, int tail_max, int hub_min, int hub_chunk) {
-  size_t b = 4 * (size_t)d;
-  if (d <= tail_max) b += 4 * (size_t)d + 4;
+  size_t b = 4 * (size_t)d;                  // ELL (tail rows) or task column indices
+  if (d <= tail_max) b += 4;
   else if (d <= hub_min) b += sizeof(Task);
   else b += sizeof(Task) * (size_t)ceil_div(d, hub_chunk) + 8;
   return b;
@@ -67,15 +67,26 @@ static int wait_event(cudaEvent_t e, int timeout_ms) {
   }
 }
 
+// Worst-case padding of one panel's slices: every degree bucket's last 32-row slice may hold a
+// single row, so 31 padded lanes of ELL indices plus 31 row ids per bucket.
+static size_t slice_padding(int tail_max) {
+  return (size_t)4 * 31 * ((size_t)tail_max * (tail_max + 1) / 2 + (size_t)tail_max + 1);
+}
+
 int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const fe_csr_opts& o) {
   const int64_t n = h->n;
-  const int tail_max = o.tail_max > 0 ? std::min(o.tail_max, 32) : 16;
+  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, kMaxTailDegree) : kDefaultTailMax;
+  if (o.tail_max <= 0) {
+    // default cutoff: keep the slice padding below 1/8 of a panel buffer
+    const size_t half = o.device_mem_cap_bytes > 0 ? (size_t)o.device_mem_cap_bytes / 2 : 0;
+    while (tail_max > 4 && slice_padding(tail_max) * 8 > half) tail_max /= 2;
+  }
   int hub_min = o.hub_min > 0 ? o.hub_min : 4096;
   const int hub_chunk = o.hub_chunk > 0 ? o.hub_chunk : 4096;
   if (hub_min < tail_max) hub_min = tail_max;
   const int64_t cap = o.device_mem_cap_bytes;
-  // resident size: rowptr + colidx + plan; if it fits, stay resident
-  size_t resident = 8 * (size_t)(n + 1) + 64 * 1024;
+  // resident size: the plan (task column indices, ELL slices, tasks); if it fits, stay resident
+  size_t resident = 64 * 1024;
   int64_t max_hub_tasks = 0;
   for (int64_t i = 0; i < n; ++i) {
     const int64_t d = rowptr[i + 1] - rowptr[i];
@@ -87,6 +98,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
 
   SemiExt* sx = new SemiExt();
   h->sx = sx;
+  h->plan.tail_max = tail_max;
   h->semi_external = 1;
   sx->timeout_ms = o.copy_timeout_ms > 0 ? o.copy_timeout_ms : 60000;
   sx->direct = o.semi_direct != 0;
@@ -94,7 +106,10 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
   // hub partials + slack
   const size_t reserve = 16 * 8 * (size_t)std::min<int64_t>(max_hub_tasks, 1 << 20) + (64 << 10);
   FE_ARG(cap > (int64_t)reserve + (1 << 16), "device_mem_cap_bytes = %lld is too small", (long long)cap);
-  const size_t target = ((size_t)cap - reserve) / 2;
+  const size_t pad = slice_padding(tail_max);
+  FE_ARG((size_t)cap > reserve + 2 * pad + (1 << 16),
+         "device_mem_cap_bytes = %lld is too small for tail_max = %d", (long long)cap, tail_max);
+  const size_t target = ((size_t)cap - reserve) / 2 - pad;
   const int64_t panel_nnz = o.panel_nnz > 0 ? o.panel_nnz : ((int64_t)64 << 20);
   std::vector<std::pair<int64_t, int64_t>> ranges;
   {
@@ -125,7 +140,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
     pi.r1 = ranges[p].second;
     pi.nnz = rowptr[pi.r1] - rowptr[pi.r0];
     size_t off = 0;
-    pi.off_colidx = off; off = align256(off + 4 * (size_t)pi.nnz);
+    pi.off_colidx = off; off = align256(off + 4 * (size_t)hp.tcol_total);
     pi.off_slice_rows = off; off = align256(off + 4 * hp.slice_rows.size());
     pi.off_ell = off; off = align256(off + 4 * (size_t)hp.ell_total);
     pi.off_tasks = off; off = align256(off + sizeof(Task) * (size_t)hp.ntasks);
@@ -167,7 +182,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
     const PanelInfo& pi = sx->panels[p];
     const HostPlan& hp = plans[p];
     char* base = sx->pinned + pi.host_off;
-    memcpy(base + pi.off_colidx, colidx + rowptr[pi.r0], 4 * (size_t)pi.nnz);
+    memcpy(base + pi.off_colidx, hp.tcol.data(), 4 * (size_t)hp.tcol_total);
     memcpy(base + pi.off_slice_rows, hp.slice_rows.data(), 4 * hp.slice_rows.size());
     memcpy(base + pi.off_ell, hp.ell.data(), 4 * (size_t)hp.ell_total);
     memcpy(base + pi.off_tasks, hp.tasks.data(), sizeof(Task) * (size_t)hp.ntasks);

@@ -28,19 +28,22 @@ namespace fe {
 
 static_assert(sizeof(Task) == 16, "Task must be 16 bytes");
 
-// Per (type, b) geometry: a lane moves NE elements (<= 16 bytes) per load; an X row of
-// b elements spans C lanes in a warp task (P = 32 / C rows gathered per warp instruction)
-// and NCH = C chunks in a tail lane.
-template <typename T, int B>
+// Per (type, b, fragment width) geometry: a lane moves NE elements (<= FB bytes: 16, or 32
+// with 256-bit loads when X is 32-byte aligned) per load; an X row of b elements spans C lanes
+// in a warp task (P = 32 / C rows gathered per warp instruction) and C chunks in a tail lane.
+template <typename T, int B, bool V32>
 struct Geo {
+  static constexpr int FB = V32 ? 32 : 16;
   static constexpr int ROWB = B * (int)sizeof(T);
-  static constexpr int NE = ROWB <= 16 ? B : 16 / (int)sizeof(T);
+  static constexpr int NE = ROWB <= FB ? B : FB / (int)sizeof(T);
   static constexpr int C = B / NE;
   static constexpr int P = 32 / C;
   static constexpr int UNROLL = C >= 4 ? 1 : 4 / C;
+  static constexpr int LNE = NE >= 8 ? 3 : NE >= 4 ? 2 : NE >= 2 ? 1 : 0;  // log2(NE)
+  // lane bits summed by the plain butterfly levels after the scatter levels (C .. 16 >> LNE)
+  static constexpr int PLAIN_MASK = (16 >> LNE) >= C ? ((16 >> LNE) << 1) - C : 0;
 };
 
-constexpr int kMaxBuckets = 34;
 struct SpmmParams {
   const int32_t* colidx;
   const Task* tasks;
@@ -57,10 +60,10 @@ struct SpmmParams {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
 
-template <typename T, int B>
+template <typename T, int B, bool V32>
 __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const T* __restrict__ X,
                                          T* __restrict__ Y, T* __restrict__ partial, int lane) {
-  using G = Geo<T, B>;
+  using G = Geo<T, B, V32>;
   const int4 raw = __ldg(reinterpret_cast<const int4*>(p.tasks + ti));
   const int64_t start = (int64_t)(uint32_t)raw.x | ((int64_t)raw.y << 32);
   const int row = raw.z;
@@ -82,33 +85,56 @@ __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const 
     for (int u = 0; u < G::UNROLL; ++u) {
 #pragma unroll
       for (int g = 0; g < 32; g += G::P) {
-        int col = __shfl_sync(kFull, cols[u], g + slot);
-        if (col >= 0) {
-          T f[G::NE];
-          ld_frag<T, G::NE>(X + (int64_t)col * B + chunk * G::NE, f);
+        // rounds whose P slots all lie past the row's end are skipped (warp-uniform test)
+        if (base + u * 32 + g < len) {
+          int col = __shfl_sync(kFull, cols[u], g + slot);
+          if (col >= 0) {
+            T f[G::NE];
+            ld_frag<T, G::NE>(X + (int64_t)col * B + chunk * G::NE, f);
 #pragma unroll
-          for (int e = 0; e < G::NE; ++e) acc[e] += f[e];
+            for (int e = 0; e < G::NE; ++e) acc[e] += f[e];
+          }
         }
       }
     }
   }
-  // tree-reduce the P slot partials of each chunk (lanes that differ above the chunk bits)
+  // Sum the P slot partials of each chunk.  The first LNE butterfly levels (offsets 16, 8, ..)
+  // also scatter the NE elements -- a lane keeps half of what it holds and adds its partner's
+  // copy of that half -- so every level after them adds one value per lane.
+  int ebase = 0;
 #pragma unroll
-  for (int off = G::C; off < 32; off <<= 1)
+  for (int lvl = 0; lvl < G::LNE; ++lvl) {
+    const int h = G::NE >> (lvl + 1);
+    const int off = 16 >> lvl;
+    const bool up = (lane & off) != 0;
 #pragma unroll
-    for (int e = 0; e < G::NE; ++e) acc[e] += __shfl_xor_sync(kFull, acc[e], off);
-  if (slot == 0) {
+    for (int i = 0; i < (G::NE >> (lvl + 1)); ++i) {
+      const T send = up ? acc[i] : acc[i + h];
+      const T keep = up ? acc[i + h] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+    if (up) ebase += h;
+  }
+#pragma unroll
+  for (int off = 16 >> G::LNE; off >= G::C; off >>= 1) acc[0] += __shfl_xor_sync(kFull, acc[0], off);
+  if ((lane & G::PLAIN_MASK) == 0) {
     T* dst = ti < p.nhub_tasks ? partial + ti * B : Y + (int64_t)row * B;
-    st_frag<T, G::NE>(dst + chunk * G::NE, acc);
+    dst[chunk * G::NE + ebase] = acc[0];
   }
 }
 
-template <typename T, int B>
+template <typename T, int B, bool V32>
 __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const T* __restrict__ X,
                                           T* __restrict__ Y, int lane) {
-  using G = Geo<T, B>;
-  int bkt = 0;
-  while (bkt + 1 < p.nbuckets && si >= p.bucket_slice_begin[bkt + 1]) ++bkt;
+  using G = Geo<T, B, V32>;
+  // bucket = last one whose first slice is <= si (buckets are non-empty, so strictly increasing)
+  int lo = 0, hi = p.nbuckets - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.bucket_slice_begin[mid] <= si) lo = mid;
+    else hi = mid - 1;
+  }
+  const int bkt = lo;
   const int deg = p.bucket_deg[bkt];
   const int64_t off = p.bucket_ell_base[bkt] + (si - p.bucket_slice_begin[bkt]) * 32 * (int64_t)deg;
   const int row = __ldcs(p.slice_rows + si * 32 + lane);
@@ -142,21 +168,22 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
     }
   }
   if (row >= 0) {
+    using F = FragOf<T, B>;  // stores in 16-byte pieces
 #pragma unroll
-    for (int ch = 0; ch < G::C; ++ch) st_frag<T, G::NE>(Y + (int64_t)row * B + ch * G::NE, acc + ch * G::NE);
+    for (int ch = 0; ch < F::NCH; ++ch) st_frag<T, F::NE>(Y + (int64_t)row * B + ch * F::NE, acc + ch * F::NE);
   }
 }
 
-template <typename T, int B>
+template <typename T, int B, bool V32>
 __global__ void __launch_bounds__(256) spmm_main_kernel(const SpmmParams p, const T* __restrict__ X,
                                                         T* __restrict__ Y, T* __restrict__ partial) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if ((int64_t)blockIdx.x < p.task_ctas) {
     const int64_t ti = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-    if (ti < p.ntasks) run_task<T, B>(p, ti, X, Y, partial, lane);
+    if (ti < p.ntasks) run_task<T, B, V32>(p, ti, X, Y, partial, lane);
   } else {
     const int64_t si = ((int64_t)blockIdx.x - p.task_ctas) * kWarpsPerCta + warp;
-    if (si < p.nslices) run_slice<T, B>(p, si, X, Y, lane);
+    if (si < p.nslices) run_slice<T, B, V32>(p, si, X, Y, lane);
   }
 }
 
@@ -195,7 +222,15 @@ static int launch_spmm(const PlanView& pv, const T* X, T* Y, T* partial, cudaStr
   p.task_ctas = ceil_div(pv.ntasks, kWarpsPerCta);
   const int64_t ctas = p.task_ctas + ceil_div(pv.nslices, kWarpsPerCta);
   if (ctas > 0) {
-    spmm_main_kernel<T, B><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+    // 256-bit gathers when an X row spans at least 32 bytes and X is 32-byte aligned
+    bool v32 = false;
+    if constexpr (B * sizeof(T) >= 32) v32 = ((uintptr_t)X % 32) == 0;
+    if (v32) {
+      if constexpr (B * sizeof(T) >= 32)
+        spmm_main_kernel<T, B, true><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+    } else {
+      spmm_main_kernel<T, B, false><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+    }
     count_launch();
     FE_CUDA(cudaGetLastError());
   }
@@ -281,11 +316,11 @@ static int dev_upload(fe_csr h, void** dst, const void* src, size_t bytes) {
   return FE_OK;
 }
 
-// Plan of rows [r0, r1): task starts are offsets from rowptr[r0]; row ids are global.
+// Plan of rows [r0, r1): task starts are offsets into hp.tcol, the column indices of the
+// panel's task rows only (tail rows are read from the ELL slices); row ids are global.
 int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
                     int tail_max, int hub_min, int hub_chunk, HostPlan& hp) {
   hp = HostPlan();
-  const int64_t base = rowptr[r0];
   std::vector<int64_t> tail_cnt(tail_max + 1, 0);
   std::vector<int64_t> mid_cnt(hub_min + 1, 0);
   int64_t nhub = 0, nhub_tasks = 0;
@@ -333,21 +368,34 @@ int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, in
   hp.tasks.resize(hp.ntasks);
   hp.hub_rows.resize(nhub);
   hp.hub_task_begin.resize(nhub + 1);
-  int64_t ht = 0, hi = 0;
+  int64_t ht = 0, hi = 0, tpos = 0;
+  {
+    int64_t tnnz = 0;
+    for (int64_t i = r0; i < r1; ++i) {
+      const int64_t d = rowptr[i + 1] - rowptr[i];
+      if (d > tail_max) tnnz += d;
+    }
+    hp.tcol.resize(tnnz > 0 ? tnnz : 1);
+  }
   for (int64_t i = r0; i < r1; ++i) {
     const int64_t d = rowptr[i + 1] - rowptr[i];
     if (d <= tail_max) {
       hp.slice_rows[cursor[d]++] = (int32_t)i;
-    } else if (d <= hub_min) {
-      hp.tasks[mid_pos[d]++] = Task{rowptr[i] - base, (int32_t)i, (int32_t)d};
+      continue;
+    }
+    memcpy(hp.tcol.data() + tpos, colidx + rowptr[i], sizeof(int32_t) * (size_t)d);
+    if (d <= hub_min) {
+      hp.tasks[mid_pos[d]++] = Task{tpos, (int32_t)i, (int32_t)d};
     } else {
       hp.hub_rows[hi] = (int32_t)i;
       hp.hub_task_begin[hi] = (int32_t)ht;
       for (int64_t c = 0; c < d; c += hub_chunk)
-        hp.tasks[ht++] = Task{rowptr[i] - base + c, (int32_t)i, (int32_t)std::min<int64_t>(hub_chunk, d - c)};
+        hp.tasks[ht++] = Task{tpos + c, (int32_t)i, (int32_t)std::min<int64_t>(hub_chunk, d - c)};
       ++hi;
     }
+    tpos += d;
   }
+  hp.tcol_total = tpos;
   hp.hub_task_begin[nhub] = (int32_t)ht;
   // ELL fill (transposed per slice; padding lanes read column 0 and are not written)
   hp.ell.assign(ell_total > 0 ? ell_total : 1, 0);
@@ -397,8 +445,7 @@ int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx_raw, 
   pl.ntasks = hp.ntasks;
   pl.nhub_tasks = hp.nhub_tasks;
   pl.nhub = hp.nhub;
-  FE_TRY(dev_upload(h, (void**)&h->d_rowptr, rowptr, sizeof(int64_t) * (n + 1)));
-  FE_TRY(dev_upload(h, (void**)&h->d_colidx, colidx, sizeof(int32_t) * h->nnz));
+  FE_TRY(dev_upload(h, (void**)&h->d_colidx, hp.tcol.data(), sizeof(int32_t) * hp.tcol_total));
   FE_TRY(dev_upload(h, (void**)&pl.d_slice_rows, hp.slice_rows.data(), sizeof(int32_t) * hp.slice_rows.size()));
   FE_TRY(dev_upload(h, (void**)&pl.d_ell, hp.ell.data(), sizeof(int32_t) * hp.ell_total));
   FE_TRY(dev_upload(h, &pl.d_tasks, hp.tasks.data(), sizeof(Task) * hp.ntasks));

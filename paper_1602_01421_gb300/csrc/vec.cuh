@@ -27,6 +27,21 @@ __device__ __forceinline__ void ld_frag(const T* p, T* f) {
   for (int i = 0; i < NE; ++i) f[i] = xs[i];
 }
 
+// 32-byte fragments (one 256-bit load per lane; sm_100 and later).  The address must be
+// 32-byte aligned.  Read-only (non-coherent) path, like __ldg.
+template <>
+__device__ __forceinline__ void ld_frag<float, 8>(const float* p, float* f) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]), "=f"(f[7])
+      : "l"(p));
+}
+template <>
+__device__ __forceinline__ void ld_frag<double, 4>(const double* p, double* f) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+      : "=d"(f[0]), "=d"(f[1]), "=d"(f[2]), "=d"(f[3])
+      : "l"(p));
+}
+
 // plain (coherent) load: for data written earlier in the same kernel or aliasing a store
 template <typename T, int NE>
 __device__ __forceinline__ void ld_frag_rw(const T* p, T* f) {

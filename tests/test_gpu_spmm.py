@@ -21,7 +21,8 @@ GRAPHS = {
     "rmat14": lambda: graphgen.rmat(14, seed=1),
     "rmat13-noperm": lambda: graphgen.rmat(13, seed=2, permute=False),
     "star9000": lambda: graphgen.star(9000),              # one hub split into 3 chunks
-    "complete70": lambda: graphgen.complete(70),          # all rows mid (deg 69)
+    "complete70": lambda: graphgen.complete(70),          # all rows in one slice bucket (deg 69)
+    "complete300": lambda: graphgen.complete(300),        # all rows warp tasks (deg 299)
     "cycle1001": lambda: graphgen.cycle(1001),            # all rows tail (deg 2), ragged slice
     "er3000": lambda: graphgen.erdos_renyi(3000, 12.0, seed=5),
     "union-isolated": lambda: graphgen.disjoint_union(graphgen.star(5000), graphgen.path(33),
@@ -48,7 +49,8 @@ def test_spmm_parity(graphs, name, b, prec):
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("knobs", [dict(tail_max=1, hub_min=8, hub_chunk=8),
                                    dict(tail_max=32, hub_min=40, hub_chunk=64),
-                                   dict(tail_max=4, hub_min=64, hub_chunk=4096)])
+                                   dict(tail_max=4, hub_min=64, hub_chunk=4096),
+                                   dict(tail_max=128, hub_min=200, hub_chunk=100)])
 def test_spmm_parity_all_paths_small(prec, knobs):
     """Tiny thresholds push most rows through the hub split and the partial reduce."""
     g = graphgen.rmat(13, seed=9)
@@ -59,6 +61,46 @@ def test_spmm_parity_all_paths_small(prec, knobs):
             Y = fe.spmm(h, to_dev(X)).cpu().numpy()
         assert info["rows_hub"] > 0
         assert_spmm_close(g, X, Y, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("tail_max", [64, 128])
+def test_spmm_parity_wide_tail(graphs, prec, tail_max):
+    """Rows up to degree 64 / 128 in the thread-per-row slices (exact-degree buckets)."""
+    for name in ("rmat14", "complete70", "er3000"):
+        g = graphs[name]
+        for b in (1, 4, 8, 16):
+            X = graphgen.normal_block(g.n, b, seed=b + 7, dtype=NP[prec])
+            with fe.Csr.from_graph(g, tail_max=tail_max) as h:
+                info = h.info()
+                Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+            deg = g.degrees()
+            assert info["rows_tail"] == ((deg >= 1) & (deg <= tail_max)).sum()
+            assert_spmm_close(g, X, Y, TOL[prec])
+
+
+@pytest.mark.parametrize("prec,b", [("f32", 8), ("f32", 16), ("f64", 4), ("f64", 8), ("f64", 16)])
+def test_spmm_parity_16_byte_aligned_blocks(graphs, prec, b):
+    """X and Y 16-byte but not 32-byte aligned: the 16-byte gather path (32-byte rows are
+    otherwise gathered with one 256-bit load per lane)."""
+    t = torch()
+    g = graphs["rmat14"]
+    dt = t.float32 if prec == "f32" else t.float64
+    shift = 16 // (4 if prec == "f32" else 8)
+    X = graphgen.normal_block(g.n, b, seed=3, dtype=NP[prec])
+    xbuf = t.zeros(g.n * b + 64, dtype=dt, device="cuda")
+    ybuf = t.zeros(g.n * b + 64, dtype=dt, device="cuda")
+    assert xbuf.data_ptr() % 32 == 0
+    xv = xbuf[shift:shift + g.n * b].view(g.n, b)
+    yv = ybuf[shift:shift + g.n * b].view(g.n, b)
+    assert xv.data_ptr() % 32 == 16
+    xv.copy_(to_dev(X))
+    with fe.Csr.from_graph(g, tail_max=64) as h:
+        fe.spmm(h, xv, yv)
+        Y16 = yv.cpu().numpy()
+        Y32 = fe.spmm(h, to_dev(X)).cpu().numpy()
+    assert_spmm_close(g, X, Y16, TOL[prec])
+    assert_spmm_close(g, X, Y32, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
@@ -91,8 +133,8 @@ def test_handle_info_bins(graphs):
     deg = g.degrees()
     assert i["n"] == g.n and i["nnz"] == g.nnz and i["max_degree"] == deg.max()
     assert i["rows_empty"] == (deg == 0).sum()
-    assert i["rows_tail"] == ((deg >= 1) & (deg <= 16)).sum()
-    assert i["rows_mid"] == ((deg > 16) & (deg <= 4096)).sum()
+    assert i["rows_tail"] == ((deg >= 1) & (deg <= 128)).sum()
+    assert i["rows_mid"] == ((deg > 128) & (deg <= 4096)).sum()
     assert i["rows_empty"] + i["rows_tail"] + i["rows_mid"] + i["rows_hub"] == g.n
 
 
