@@ -64,6 +64,22 @@ __device__ __forceinline__ void load_vrow(const T* __restrict__ base, int ld, in
   }
 }
 
+// FP64 -> FP32 by truncating the significand (IEEE 754 binary64 -> binary32 field by field:
+// sign, exponent rebiased from 1023 to 127, top 23 of the 52 fraction bits), on the integer
+// units so that the FP64 pipe is not touched.  Relative error below 2^-23; magnitudes below
+// 2^-126 become signed zero, above the binary32 range infinity.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned bits = sign | ((unsigned)e << 23) | frac;
+  if (e <= 0) bits = sign;
+  if (e >= 255) bits = sign | 0x7f800000u;
+  return __uint_as_float(bits);
+}
+
 // ---------------------------------------------------------------- gram
 // Rows [r, r + rows) of tile (j, q0) of V_j^T W from the staged W rows sW (lane = row, four
 // row loads in flight per lane when the block is narrow).  Products and sums in TC (T, or
@@ -716,14 +732,21 @@ namespace fe {
 // operations.  Gram tiles are the V blocks then W_new; TPW > 0: warp w owns tiles w + nwarps t
 // for the whole launch and reduces once at the end (the block has one warp per tile, up to 16,
 // and a range is one row per thread); TPW == 0: 8 warps, tiles reduced per range.
+//
+// vc32 (FP64 only): when *vc32 != 0 the sum alpha sum_j V_j[r] C_j is formed in FP32 arithmetic
+// (V converted by f64_to_f32_trunc, FP32 coefficients, FP32 accumulation) and added to the FP64
+// W[r] M.  The caller sets the flag only when the coefficients are tiny corrections (the second
+// Gram-Schmidt pass), so that the FP32 rounding stays far below FP64 rounding of W.
 template <typename T, int BV, int BW, int TPW>
 __global__ void __launch_bounds__(TPW > 0 ? 512 : 256) update_gram_kernel(const BlockSet V, const double* __restrict__ C,
                                                           double alpha, double beta,
                                                           const double* __restrict__ M,
                                                           T* __restrict__ W, int64_t n, int gram_v,
                                                           const int* __restrict__ skip,
+                                                          const int* __restrict__ vc32,
                                                           double* __restrict__ partial) {
   if (skip && *skip) return;
+  const bool use32 = sizeof(T) == 8 && vc32 != nullptr && *vc32 != 0;
   const int R = blockDim.x;
   const int kWarps = blockDim.x >> 5;
   constexpr int NR = BV > BW ? BV : BW;
@@ -736,7 +759,10 @@ __global__ void __launch_bounds__(TPW > 0 ? 512 : 256) update_gram_kernel(const 
   double* sP = reinterpret_cast<double*>(smem_raw + ((((size_t)k * BW + BW * BW + 2 * (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15));
   const int gblocks = gram_v ? V.nv + 1 : 1;  // Gram row blocks: the V blocks (if any), then W
   const int nout = (gram_v ? k : 0) * BW + BW * BW;
+  float* sC32 = reinterpret_cast<float*>(sP + nout);  // FP32 coefficients (vc32 launches)
   for (int e = threadIdx.x; e < k * BW; e += blockDim.x) sC[e] = (T)(alpha * C[e]);
+  if (vc32)
+    for (int e = threadIdx.x; e < k * BW; e += blockDim.x) sC32[e] = (float)(alpha * C[e]);
   if (M)
     for (int e = threadIdx.x; e < BW * BW; e += blockDim.x) sM[e] = (T)(beta * M[e]);
   for (int e = threadIdx.x; e < nout; e += blockDim.x) sP[e] = 0.0;
@@ -777,19 +803,45 @@ __global__ void __launch_bounds__(TPW > 0 ? 512 : 256) update_gram_kernel(const 
         }
       }
       constexpr int UJ = BV >= 8 ? 2 : 4;
-      for (int j0 = 0; j0 < V.nv; j0 += UJ) {
-        T v[UJ][BV];
+      if (use32) {
+        float a32[BW];
 #pragma unroll
-        for (int u = 0; u < UJ; ++u)
-          if (j0 + u < V.nv) load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j0 + u]), V.ld, r, v[u]);
+        for (int q = 0; q < BW; ++q) a32[q] = 0.f;
+        for (int j0 = 0; j0 < V.nv; j0 += UJ) {
+          T v[UJ][BV];
 #pragma unroll
-        for (int u = 0; u < UJ; ++u) {
-          if (j0 + u < V.nv) {
-            const T* c = sC + (j0 + u) * BV * BW;
+          for (int u = 0; u < UJ; ++u)
+            if (j0 + u < V.nv) load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j0 + u]), V.ld, r, v[u]);
 #pragma unroll
-            for (int p = 0; p < BV; ++p)
+          for (int u = 0; u < UJ; ++u) {
+            if (j0 + u < V.nv) {
+              const float* c = sC32 + (j0 + u) * BV * BW;
 #pragma unroll
-              for (int q = 0; q < BW; ++q) a[q] = fma(v[u][p], c[p * BW + q], a[q]);
+              for (int p = 0; p < BV; ++p) {
+                const float vp = f64_to_f32_trunc((double)v[u][p]);
+#pragma unroll
+                for (int q = 0; q < BW; ++q) a32[q] = fmaf(vp, c[p * BW + q], a32[q]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < BW; ++q) a[q] += (T)a32[q];
+      } else {
+        for (int j0 = 0; j0 < V.nv; j0 += UJ) {
+          T v[UJ][BV];
+#pragma unroll
+          for (int u = 0; u < UJ; ++u)
+            if (j0 + u < V.nv) load_vrow<T, BV>(reinterpret_cast<const T*>(V.blk[j0 + u]), V.ld, r, v[u]);
+#pragma unroll
+          for (int u = 0; u < UJ; ++u) {
+            if (j0 + u < V.nv) {
+              const T* c = sC + (j0 + u) * BV * BW;
+#pragma unroll
+              for (int p = 0; p < BV; ++p)
+#pragma unroll
+                for (int q = 0; q < BW; ++q) a[q] = fma(v[u][p], c[p * BW + q], a[q]);
+            }
           }
         }
       }
@@ -867,12 +919,12 @@ __global__ void __launch_bounds__(TPW > 0 ? 512 : 256) update_gram_kernel(const 
 template <typename T, int BV, int BW, int TPW>
 static int launch_update_gram_tpw(const BlockSet& V, int64_t n, const double* C, double alpha,
                                   double beta, const double* M, T* W, int gram_v, const int* skip,
-                                  double* G, int threads, cudaStream_t s) {
+                                  const int* vc32, double* G, int threads, cudaStream_t s) {
   const int R = threads;
   const int k = V.nv * BV;
   const int nout = (gram_v ? k : 0) * BW + BW * BW;
   const size_t smem = ((((size_t)k * BW + BW * BW + 2 * (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15) +
-                      (size_t)nout * sizeof(double);
+                      (size_t)nout * sizeof(double) + (vc32 ? (size_t)k * BW * sizeof(float) : 0);
   FE_ARG(smem <= 200 * 1024, "update_gram: coefficient matrix too large");
   static bool configured = false;
   static int per_sm[17] = {0};  // by warps per block
@@ -893,7 +945,7 @@ static int launch_update_gram_tpw(const BlockSet& V, int64_t n, const double* C,
   nctas = std::max(nctas, 1);
   double* part = small_scratch(0, (size_t)nctas * nout);
   if (!part) return FE_ERR_OOM;
-  update_gram_kernel<T, BV, BW, TPW><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, part);
+  update_gram_kernel<T, BV, BW, TPW><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, gram_v, skip, vc32, part);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return launch_gram_reduce(part, nctas, nout, 1.0, G, s);
@@ -904,24 +956,25 @@ static int launch_update_gram_tpw(const BlockSet& V, int64_t n, const double* C,
 template <typename T, int BV, int BW>
 static int launch_update_gram(const BlockSet& V, int64_t n, const double* C, double alpha,
                               double beta, const double* M, T* W, int gram_v, const int* skip,
-                              double* G, cudaStream_t s) {
+                              const int* vc32, double* G, cudaStream_t s) {
   constexpr int NR = BV > BW ? BV : BW;
   constexpr int kRegsPerTile = NR * BW * (int)(sizeof(T) / 4);
   const int gblocks = gram_v ? V.nv + 1 : 1;
   if (gblocks <= 16 && kRegsPerTile <= 32)
     return launch_update_gram_tpw<T, BV, BW, (kRegsPerTile <= 32 ? 1 : 0)>(
-        V, n, C, alpha, beta, M, W, gram_v, skip, G, 32 * std::max(8, gblocks), s);
-  return launch_update_gram_tpw<T, BV, BW, 0>(V, n, C, alpha, beta, M, W, gram_v, skip, G, 256, s);
+        V, n, C, alpha, beta, M, W, gram_v, skip, vc32, G, 32 * std::max(8, gblocks), s);
+  return launch_update_gram_tpw<T, BV, BW, 0>(V, n, C, alpha, beta, M, W, gram_v, skip, vc32, G, 256, s);
 }
 
 // W = beta W M + alpha V C; G = [V; W]^T W (gram_v) or W^T W, rows (j*b + p) then W's b rows.
 // V blocks and W must all be n x b with ld b (the solver's subspace blocks).
 int update_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
                 const double* M, void* W, int b, fe_dtype dt, int gram_v, const int* skip,
-                double* G, cudaStream_t s) {
+                double* G, cudaStream_t s, const int* vc32) {
   FE_ARG(V.nv >= 0 && V.nv <= kMaxBlocks, "update_gram: nv = %d", V.nv);
   FE_ARG(V.nv == 0 || (V.bv == b && V.ld == b), "update_gram: blocks must be n x b");
-#define UG(T, B) return launch_update_gram<T, B, B>(V, n, C, alpha, beta, M, static_cast<T*>(W), gram_v, skip, G, s)
+  if (dt != FE_F64) vc32 = nullptr;
+#define UG(T, B) return launch_update_gram<T, B, B>(V, n, C, alpha, beta, M, static_cast<T*>(W), gram_v, skip, vc32, G, s)
   if (dt == FE_F32) {
     switch (b) { case 1: UG(float, 1); case 2: UG(float, 2); case 4: UG(float, 4); case 8: UG(float, 8); }
   } else {

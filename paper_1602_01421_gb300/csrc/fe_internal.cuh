@@ -92,9 +92,11 @@ int to_colmajor_f64(const BlockSet& X, int64_t n, int ncols, fe_dtype dt, double
 
 // Orthonormalise W (n x b, ld b) against V and itself; see fe_block_orth.  Synchronous.
 struct OrthWork;
+// vc32 (FP64, may be null): device flag; when set, V C is formed in FP32 arithmetic (for tiny
+// correction coefficients only, see orth.cu).
 int update_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
                 const double* M, void* W, int b, fe_dtype dt, int gram_v, const int* skip,
-                double* G, cudaStream_t s);
+                double* G, cudaStream_t s, const int* vc32 = nullptr);
 int orth(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
          double anorm_floor, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
          double* d_R, int ldr, int* replaced, cudaStream_t s);

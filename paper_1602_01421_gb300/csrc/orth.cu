@@ -24,14 +24,15 @@ namespace fe {
 int update_skip(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
                 const double* M, void* W, int bw, int ldw, fe_dtype dt, const int* skip,
                 cudaStream_t s);
-int update_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
-                const double* M, void* W, int b, fe_dtype dt, int gram_v, const int* skip,
-                double* G, cudaStream_t s);
 int gram_f32_arith(const BlockSet& V, int64_t n, const double* W, int b, double alpha, double* G,
                    cudaStream_t s);
 
 constexpr double kRelPivot = 1e-6;      // pivot below 1e-6 * column norm: nearly dependent
 constexpr double kAbsBreakdown = 1e-12; // remainder below 1e-12 * ||A||: breakdown
+// Second-pass correction coefficients C = -G2 R1^{-1} at most this large (W's columns have unit
+// scale after R1^{-1}) are applied in FP32 arithmetic: the FP32 rounding of V C is then below
+// 2^-23 * 1e-5 * (sum_j |V_j[r]|), under 1e-12 of W even in the worst case and ~1e-15 typically.
+constexpr double kSmallCorrection = 1e-5;
 
 // Upper-triangular R (row-major b x b) with R^T R = S; false if a pivot check fails.
 __device__ bool chol_upper_dev(const double* S, int b, double rel, double absthr, double* R) {
@@ -66,7 +67,7 @@ __device__ void inv_upper_dev(const double* R, int b, double* Ri) {
 
 // After pass 2.  G1x = [G1; S1] ((k+b) x b), G2x = [G2; S] ((k+b) x b); k may be 0 (then
 // G2x = S).  Writes G (k x b, ldg), Racc = R1, M = R1^{-1}, C = -G2 R1^{-1}; on a failed check
-// sets *status = 1, G = G1, Racc = I.
+// sets *status = 1, G = G1, Racc = I.  status[1] = 1 when max |C| <= kSmallCorrection.
 __global__ void orth_post2_kernel(const double* __restrict__ G1x, const double* __restrict__ G2x,
                                   int k, int b, double* __restrict__ anorm, int update_anorm,
                                   double* __restrict__ G, int ldg, double* __restrict__ Racc,
@@ -111,6 +112,13 @@ __global__ void orth_post2_kernel(const double* __restrict__ G1x, const double* 
     } else {
       Racc[e] = (e / b == e % b) ? 1.0 : 0.0;
     }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double cmax = 0.0;
+    if (ok)
+      for (int e = 0; e < k * b; ++e) cmax = fmax(cmax, fabs(C[e]));
+    status[1] = (ok && cmax <= kSmallCorrection) ? 1 : 0;
   }
 }
 
@@ -265,7 +273,7 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   if (!sG1 || !sG2 || !sM || !sC || !sRacc || !sS2 || !sStat || !gdummy) return FE_ERR_OOM;
   int* status = reinterpret_cast<int*>(sStat);
   if (!d_G) d_G = gdummy;  // k == 0: nothing is written to G
-  FE_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+  FE_CUDA(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
   std::vector<const void*> vx(V.blk, V.blk + V.nv);
   vx.push_back(W);
   BlockSet Vx = blockset_of(vx, b, b);
@@ -296,7 +304,9 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   FE_CUDA(cudaGetLastError());
   // W <- (W - V G2) R1^{-1} and S2 = W^T W in one sweep (skipped after a failed pivot check)
   if (fused) {
-    FE_TRY(update_gram(V, n, sC, 1.0, 1.0, sM, W, b, dt, 0, status, sS2, s));
+    // the correction V C in FP32 arithmetic when it is tiny (FP64 subspace, pass1_f32 mode)
+    FE_TRY(update_gram(V, n, sC, 1.0, 1.0, sM, W, b, dt, 0, status, sS2, s,
+                       (pass1_f32 && dt == FE_F64) ? status + 1 : nullptr));
   } else {
     FE_TRY(update_skip(V, n, sC, 1.0, 1.0, sM, W, b, b, dt, status, s));
     BlockSet Wonly = blockset_of({W}, b, b);
