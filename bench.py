@@ -629,7 +629,7 @@ def main():
     # dram__bytes_read.sum + dram__bytes_write.sum of update_gram_kernel<double,4,4,1> at the
     # roofline shape, one ncu capture (profiles/update_gram_f64_rmat22.md); update when that
     # kernel changes
-    ap.add_argument("--traffic", type=float, default=1.074065e9 + 126.431744e6,
+    ap.add_argument("--traffic", type=float, default=1.073919e9 + 126.096384e6,
                     help="ncu DRAM bytes per launch of the roofline kernel")
     ap.add_argument("--ref-cycles", type=int, default=1)
     ap.add_argument("--ref-solve-blocks", type=int, default=150)
