@@ -492,7 +492,9 @@ def run_ours(args):
         if i > 0:
             e2e_times.append(time.perf_counter() - t0)
     e2e = {"value": 1.0 / statistics.mean(e2e_times), "unit": "solves/s",
-           "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
+           # the SpMM plan fe_csr_create uploads (the handle's device bytes minus the hub
+           # partial-sum buffer, 16 doubles per hub chunk, which is allocated, not copied)
+           "h2d_bytes_per_step": int(info["device_bytes"] - 128 * info["hub_chunks"]),
            "d2h_bytes_per_step": int(host.nbytes) + 8 * NEV}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
