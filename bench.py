@@ -466,17 +466,22 @@ def run_ours(args):
         try:
             cap = 256 << 20
             semi = {"cap_bytes": cap}
-            for mode in ("staged", "direct"):
-                with fe.Csr.from_graph(g, device_mem_cap_bytes=cap, semi_direct=mode == "direct") as hs:
+            # staged copies or direct reads of the pinned panels; packed (default) or plain
+            # column indices
+            for mode, direct, fmt in (("staged", False, "auto"), ("staged_plain", False, "plain"),
+                                      ("direct", True, "auto")):
+                with fe.Csr.from_graph(g, device_mem_cap_bytes=cap, semi_direct=direct,
+                                       index_format=fmt) as hs:
                     si = hs.info()
                     Xs = fe.random_normal(n, 4, dtype=torch.float32, seed=3)
                     Ys = torch.empty_like(Xs)
                     fe.spmm(hs, Xs, Ys)
                     ts = statistics.median(time_cuda(lambda: fe.spmm(hs, Xs, Ys), 5, torch))
                 semi[mode] = {"panels": si["panels"], "device_bytes": si["device_bytes"],
-                              "f32_b4_ms": round(ts, 3),
+                              "index_format": "packed" if si["index_format"] == 2 else "plain",
+                              "index_bytes": si["index_bytes"], "f32_b4_ms": round(ts, 3),
                               "GBps": round(spmm_bytes(n, nnz, 4, 4) / (ts / 1000.0) / 1e9, 1),
-                              "host_read_GBps": round((4 * nnz + 16 * si["rows_mid"]) / (ts / 1000.0) / 1e9, 1)}
+                              "index_read_GBps": round(si["index_bytes"] / (ts / 1000.0) / 1e9, 1)}
         except Exception as e:
             semi = {"error": str(e)}
 
@@ -591,10 +596,12 @@ def run_config(args):
         out.update(n=g.n, nnz=g.nnz, gen_s=round(time.perf_counter() - t0, 1))
         cap = 6 << 30
         t0 = time.perf_counter()
-        h = fe.Csr.from_graph(g, device_mem_cap_bytes=cap, semi_direct=args.semi_direct)
+        h = fe.Csr.from_graph(g, device_mem_cap_bytes=cap, semi_direct=args.semi_direct,
+                              index_format=args.index_format)
         info = h.info()
         out.update(create_s=round(time.perf_counter() - t0, 1), cap_bytes=cap, panels=info["panels"],
-                   device_bytes=info["device_bytes"])
+                   device_bytes=info["device_bytes"], index_bytes=info["index_bytes"],
+                   index_format="packed" if info["index_format"] == 2 else "plain")
         for prec, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
             X = fe.random_normal(g.n, 4, dtype=tdt, seed=3)
             Y = torch.empty_like(X)
@@ -605,9 +612,29 @@ def run_config(args):
             err = float(np.max(np.abs(Y.cpu().numpy()[rows] - ref) /
                                (core.spmm_rows(g.rowptr, g.colidx, np.abs(X.cpu().numpy()), rows) + 1e-300)))
             out[f"spmm_{prec}_b4"] = {"ms": round(tt, 2), "GBps": round(spmm_bytes(g.n, g.nnz, 4, es) / tt / 1e6, 1),
-                                      "h2d_GBps": round(4 * g.nnz / tt / 1e6, 1),
+                                      "index_read_GBps": round(info["index_bytes"] / tt / 1e6, 1),
                                       "max_rel_err_sampled_rows": err}
             del X, Y
+        # the configuration's solve: 8 eigenpairs at tol 1e-8, block 4, 8 blocks, FP64 subspace in
+        # HBM while the CSR streams; explicit residuals checked with the oracle's SpMM
+        for mode in args.semi_modes.split(","):
+            if not mode:
+                continue
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ev, X, st = fe.eigs(h, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1, mode=mode,
+                                max_restarts=MAX_RESTARTS, raise_on_noconverge=False)
+            torch.cuda.synchronize()
+            ts = time.perf_counter() - t
+            Xh = X.cpu().numpy()
+            R = core.spmm(g.rowptr, g.colidx, Xh) - Xh * ev
+            out[f"solve_{mode}"] = {"s": round(ts, 2), "converged": st["converged"],
+                                    "restarts": st["restarts"], "spmm_blocks": st["spmm_blocks"],
+                                    "max_rel_resid_cpu": float((np.linalg.norm(R, axis=0) / np.abs(ev)).max()),
+                                    "orth": float(np.abs(Xh.T @ Xh - np.eye(NEV)).max()),
+                                    "evals": [float(x) for x in ev]}
+            del X, Xh, R
+            print(json.dumps({"progress": f"solve_{mode}", **out[f"solve_{mode}"]}), flush=True)
         h.close()
     print(json.dumps(out), flush=True)
 
@@ -627,6 +654,10 @@ def main():
     ap.add_argument("--no-many", action="store_true", help="skip the nev 32 (m = 128) leg")
     ap.add_argument("--no-svd", action="store_true", help="skip the directed-graph SVD leg")
     ap.add_argument("--no-semi", action="store_true")
+    ap.add_argument("--index-format", default="auto", choices=["auto", "plain", "packed"],
+                    help="semiext27: column-index format of the streamed CSR")
+    ap.add_argument("--semi-modes", default="mixed,fp64",
+                    help="semiext27: solve modes to time on the semi-external handle ('' = none)")
 
     # dram__bytes_read.sum + dram__bytes_write.sum of update_gram_kernel<double,4,4,1> at the
     # roofline shape, one ncu capture (profiles/update_gram_f64_rmat22.md); update when that

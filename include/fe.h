@@ -70,6 +70,8 @@ void* fe_get_stream(void);
 
 /* ------------------------------------------------------------------ sparse matrix */
 
+typedef enum { FE_INDEX_AUTO = 0, FE_INDEX_PLAIN = 1, FE_INDEX_PACKED = 2 } fe_index_format;
+
 typedef struct {
   /* Cap, in bytes, on the device memory the CSR may occupy.  0 = no cap (the matrix is
    * resident in HBM).  When the resident layout would exceed it, the matrix stays in pinned
@@ -99,6 +101,14 @@ typedef struct {
    * buffers, copies overlapped with the previous panel's kernels); 1 = direct (the kernels read
    * the packed panels in pinned host memory through its device mapping, with no copies). */
   int semi_direct;
+  /* Storage of the column indices of rows handled by warp tasks (degree > tail_max):
+   * FE_INDEX_AUTO (0, default) = bit-packed gaps for semi-external handles, where the streamed
+   * bytes bound the SpMM, plain int32 for resident ones; FE_INDEX_PLAIN = int32 indices;
+   * FE_INDEX_PACKED = each row (each chunk of hub_chunk entries of a hub row) sorted and stored
+   * as gaps to the previous column in fields of the row's largest gap width (the paper's
+   * compressed-index idea, Section 3.3.1, in a GPU-decodable form: a warp reads 32 fields and
+   * adds them up with a prefix sum).  Packed plans default to tail_max = 16. */
+  int index_format;
   /* 1 = also build the transposed pattern A^T (host counting sort at create, then its own
    * SpMM plan), needed by fe_spmm_t and fe_svds: a directed graph's adjacency matrix is not
    * symmetric (Section 4.3.2).  Resident handles only.  Default 0. */
@@ -122,6 +132,8 @@ typedef struct {
   int has_transpose;    /* 1 if A^T was built (fe_csr_opts.transpose) */
   int tail_max;         /* the degree cutoff of the slice format in use (semi-external handles
                          * with the default may use a smaller one than resident ones) */
+  int index_format;     /* FE_INDEX_PLAIN or FE_INDEX_PACKED, as in use */
+  int64_t index_bytes;  /* bytes of column-index data in the plan (resident or streamed) */
 } fe_csr_info;
 
 /*

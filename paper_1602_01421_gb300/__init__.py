@@ -53,7 +53,8 @@ class Csr:
     def __init__(self, rowptr: np.ndarray, colidx: np.ndarray, *, validate: bool = True,
                  check_symmetric: bool = False, device_mem_cap_bytes: int = 0,
                  tail_max: int = 0, hub_min: int = 0, hub_chunk: int = 0, panel_nnz: int = 0,
-                 copy_timeout_ms: int = 0, semi_direct: bool = False, transpose: bool = False):
+                 copy_timeout_ms: int = 0, semi_direct: bool = False, transpose: bool = False,
+                 index_format: str = "auto"):
         lib = load()
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(colidx, dtype=np.int32)
@@ -67,6 +68,7 @@ class Csr:
         o.panel_nnz, o.copy_timeout_ms = int(panel_nnz), int(copy_timeout_ms)
         o.semi_direct = int(semi_direct)
         o.transpose = int(transpose)
+        o.index_format = _lib.INDEX_FORMAT[index_format]
         h = ctypes.c_void_p()
         check(lib.fe_csr_create_ex(self.n, self._rowptr.ctypes.data_as(ctypes.c_void_p),
                                    self._colidx.ctypes.data_as(ctypes.c_void_p),

@@ -21,6 +21,7 @@ FE_F32, FE_F64 = 0, 1
 WHICH = {"LM": 0, "LA": 1, "SA": 2}
 MODE = {"fp64": 0, "mixed": 1}
 START = {"random": 0, "user": 1, "learned": 2}
+INDEX_FORMAT = {"auto": 0, "plain": 1, "packed": 2}
 
 
 class CsrOpts(ctypes.Structure):
@@ -28,7 +29,8 @@ class CsrOpts(ctypes.Structure):
                 ("check_symmetric", ctypes.c_int), ("tail_max", ctypes.c_int),
                 ("hub_min", ctypes.c_int), ("hub_chunk", ctypes.c_int),
                 ("panel_nnz", ctypes.c_int64), ("copy_timeout_ms", ctypes.c_int),
-                ("semi_direct", ctypes.c_int), ("transpose", ctypes.c_int)]
+                ("semi_direct", ctypes.c_int), ("index_format", ctypes.c_int),
+                ("transpose", ctypes.c_int)]
 
 
 class CsrInfo(ctypes.Structure):
@@ -37,7 +39,8 @@ class CsrInfo(ctypes.Structure):
                 ("rows_hub", ctypes.c_int64), ("hub_chunks", ctypes.c_int64),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("semi_external", ctypes.c_int), ("panels", ctypes.c_int64),
-                ("has_transpose", ctypes.c_int), ("tail_max", ctypes.c_int)]
+                ("has_transpose", ctypes.c_int), ("tail_max", ctypes.c_int),
+                ("index_format", ctypes.c_int), ("index_bytes", ctypes.c_int64)]
 
 
 class EigsOpts(ctypes.Structure):

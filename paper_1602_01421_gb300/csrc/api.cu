@@ -206,7 +206,11 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   h->n = n;
   h->nnz = nnz;
   cudaGetDevice(&h->device);
-  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, kMaxTailDegree) : kDefaultTailMax;
+  FE_ARG(o.index_format >= FE_INDEX_AUTO && o.index_format <= FE_INDEX_PACKED,
+         "fe_csr_create: index_format = %d", o.index_format);
+  const bool packed = o.index_format == FE_INDEX_PACKED;  // resident: plain unless asked
+  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, kMaxTailDegree)
+                                : (packed ? kDefaultTailMaxPacked : kDefaultTailMax);
   int hub_min = o.hub_min > 0 ? o.hub_min : 4096;
   int hub_chunk = o.hub_chunk > 0 ? o.hub_chunk : 4096;
   if (hub_min < tail_max) hub_min = tail_max;
@@ -214,7 +218,7 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   if (o.device_mem_cap_bytes > 0) {
     rc = semiext_create(h, rowptr, colidx, o);
   } else {
-    rc = spmm_build_plan(h, rowptr, colidx, tail_max, hub_min, hub_chunk);
+    rc = spmm_build_plan(h, rowptr, colidx, tail_max, hub_min, hub_chunk, packed);
   }
   if (rc == FE_OK && o.transpose) {
     std::vector<int64_t> trp;
@@ -252,6 +256,8 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info) {
   info->panels = h->semi_external ? semiext_panels(h) : 0;
   info->has_transpose = h->t != nullptr;
   info->tail_max = h->plan.tail_max;
+  info->index_format = h->plan.packed ? FE_INDEX_PACKED : FE_INDEX_PLAIN;
+  info->index_bytes = h->plan.index_bytes;
   return FE_OK;
 }
 

@@ -54,6 +54,7 @@ constexpr int kMaxBlocks = 40;
 // SpMM plan: rows of degree <= tail_max (at most kMaxTailDegree) go to degree-bucketed slices.
 constexpr int kMaxTailDegree = 128;
 constexpr int kDefaultTailMax = 128;
+constexpr int kDefaultTailMaxPacked = 16;  // packed plans: most rows in the compressed tasks
 constexpr int kMaxBuckets = kMaxTailDegree + 1;
 // Rayleigh-Ritz: subspaces up to kRitzSmallMax are diagonalised entirely in shared memory,
 // larger ones (up to kRitzMax) keep the FP64 eigenvector matrix in a global workspace.
@@ -119,7 +120,10 @@ struct fe_spmm_plan {
   int nbuckets = 0;
   // warp tasks: hub chunks first (partial slots 0..nhub_tasks-1), then mid rows by degree
   int64_t ntasks = 0, nhub_tasks = 0, nhub = 0;
-  void* d_tasks = nullptr;           // struct Task[ntasks]
+  void* d_tasks = nullptr;           // struct Task[ntasks] (PTask when packed)
+  uint32_t* d_tbits = nullptr;       // packed: the task rows' gap bit stream
+  int packed = 0;
+  int64_t index_bytes = 0;           // bytes of column-index data in the plan
   int32_t* d_hub_rows = nullptr;     // nhub
   int32_t* d_hub_task_begin = nullptr;  // nhub + 1
   int hub_min = 4096, hub_chunk = 4096;
@@ -147,6 +151,15 @@ struct Task {
   int32_t row;    // output row
   int32_t len;    // non-zeros
 };
+// Warp task over bit-packed column gaps (index_format packed): the segment's sorted columns
+// c_0 <= c_1 <= ... are stored as len fields of w bits, g_0 = 0 and g_k = c_k - c_{k-1},
+// starting at word woff of the plan's bit stream (LSB first); c_k = base + g_0 + ... + g_k.
+struct PTask {
+  int64_t woff;
+  int32_t row, len;
+  int32_t base, w;
+  int32_t pad0, pad1;
+};
 // Host-side SpMM plan of a row range (built at create; uploaded or packed into panels).
 struct HostPlan {
   int64_t max_degree = 0, rows_empty = 0, rows_tail = 0, rows_mid = 0, rows_hub = 0;
@@ -157,10 +170,16 @@ struct HostPlan {
   std::vector<int32_t> slice_rows, ell, hub_rows, hub_task_begin;
   std::vector<int32_t> tcol;  // column indices of the task rows (mid and hub), in row order
   std::vector<Task> tasks;    // start: offset into tcol
+  // packed index format: the task rows' columns as gap bit fields (tcol is then emptied)
+  bool packed = false;
+  std::vector<uint32_t> tbits;
+  std::vector<PTask> ptasks;
 };
 // Device pointers of a plan (the resident handle's, or one streamed panel's).
 struct PlanView {
-  const int32_t* colidx;
+  const int32_t* colidx;   // plain: task rows' column indices
+  const uint32_t* tbits;   // packed: their gap bit stream (tasks are then PTask)
+  int packed;
   const void* tasks;
   int64_t ntasks, nhub_tasks;
   const int32_t* slice_rows;
@@ -174,12 +193,15 @@ struct PlanView {
   int64_t nhub;
 };
 int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
-                    int tail_max, int hub_min, int hub_chunk, HostPlan& hp);
+                    int tail_max, int hub_min, int hub_chunk, bool packed, HostPlan& hp);
+// Bytes the column indices of row i take in a plan (ELL slice, plain task indices or packed
+// gaps), for sizing panels.
+size_t plan_row_index_bytes(const int32_t* cols, int64_t d, int tail_max, int hub_chunk, bool packed);
 int spmm_view(const PlanView& v, const void* X, void* Y, void* partial, int b, fe_dtype dt,
               cudaStream_t s);
 int spmm_resident(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s);
 int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx, int tail_max,
-                    int hub_min, int hub_chunk);
+                    int hub_min, int hub_chunk, bool packed);
 int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx,
                    const fe_csr_opts& o);
 int semiext_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s);

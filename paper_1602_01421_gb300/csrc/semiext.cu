@@ -21,6 +21,7 @@ namespace fe {
 
 struct PanelInfo {
   int64_t r0, r1, nnz;
+  int64_t index_words;  // plain: task column indices; packed: gap bit-stream words
   size_t off_colidx, off_slice_rows, off_ell, off_tasks, off_hub_rows, off_hub_begin, bytes;
   size_t host_off;  // offset of the packed panel in the pinned arena
   int nbuckets;
@@ -39,15 +40,18 @@ struct SemiExt {
   cudaStream_t copy = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr}, done = nullptr;
   int timeout_ms = 60000;
+  bool packed = false;   // task rows' columns as bit-packed gaps (index_format)
   bool direct = false;   // kernels read the pinned panels through their device mapping
   bool pending = false;  // a previous call returned FE_ERR_TIMEOUT with work in flight
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Bytes a row adds to a packed panel (estimate used to cut panels).
-static size_t row_bytes(int64_t d, int tail_max, int hub_min, int hub_chunk) {
-  size_t b = 4 * (size_t)d;                  // ELL (tail rows) or task column indices
+// Bytes row i adds to a panel (estimate used to cut panels): its column indices in the plan's
+// format, plus its slice row id or its task records.
+static size_t row_bytes(const int32_t* cols, int64_t d, int tail_max, int hub_min, int hub_chunk,
+                        bool packed) {
+  size_t b = plan_row_index_bytes(cols, d, tail_max, hub_chunk, packed);
   if (d <= tail_max) b += 4;
   else if (d <= hub_min) b += sizeof(Task);
   else b += sizeof(Task) * (size_t)ceil_div(d, hub_chunk) + 8;
@@ -75,7 +79,11 @@ static size_t slice_padding(int tail_max) {
 
 int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const fe_csr_opts& o) {
   const int64_t n = h->n;
-  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, kMaxTailDegree) : kDefaultTailMax;
+  // index format: packed gaps unless the caller asks for plain indices (the streamed bytes are
+  // what bound this mode)
+  const bool packed = o.index_format != FE_INDEX_PLAIN;
+  int tail_max = o.tail_max > 0 ? std::min(o.tail_max, kMaxTailDegree)
+                                : (packed ? kDefaultTailMaxPacked : kDefaultTailMax);
   if (o.tail_max <= 0) {
     // default cutoff: keep the slice padding below 1/8 of a panel buffer
     const size_t half = o.device_mem_cap_bytes > 0 ? (size_t)o.device_mem_cap_bytes / 2 : 0;
@@ -86,15 +94,26 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
   if (hub_min < tail_max) hub_min = tail_max;
   const int64_t cap = o.device_mem_cap_bytes;
   // resident size: the plan (task column indices, ELL slices, tasks); if it fits, stay resident
+  // resident size with plain indices (an upper bound for a packed resident plan)
   size_t resident = 64 * 1024;
   int64_t max_hub_tasks = 0;
+  #pragma omp parallel for schedule(static) reduction(+ : resident, max_hub_tasks)
   for (int64_t i = 0; i < n; ++i) {
     const int64_t d = rowptr[i + 1] - rowptr[i];
-    resident += row_bytes(d, tail_max, hub_min, hub_chunk) + 4;
+    resident += row_bytes(colidx + rowptr[i], d, tail_max, hub_min, hub_chunk, false) + 4;
     if (d > hub_min) max_hub_tasks += ceil_div(d, hub_chunk);
   }
   resident += 16 * 8 * (size_t)max_hub_tasks;
-  if ((int64_t)resident <= cap) return spmm_build_plan(h, rowptr, colidx, tail_max, hub_min, hub_chunk);
+  if ((int64_t)resident <= cap)
+    return spmm_build_plan(h, rowptr, colidx, tail_max, hub_min, hub_chunk,
+                           o.index_format == FE_INDEX_PACKED);
+  std::vector<uint32_t> rbytes(n);
+  #pragma omp parallel for schedule(dynamic, 4096)
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t d = rowptr[i + 1] - rowptr[i];
+    rbytes[i] = (uint32_t)std::min<size_t>(
+        row_bytes(colidx + rowptr[i], d, tail_max, hub_min, hub_chunk, packed) + 4 + 64, UINT32_MAX);
+  }
 
   SemiExt* sx = new SemiExt();
   h->sx = sx;
@@ -102,6 +121,8 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
   h->semi_external = 1;
   sx->timeout_ms = o.copy_timeout_ms > 0 ? o.copy_timeout_ms : 60000;
   sx->direct = o.semi_direct != 0;
+  sx->packed = packed;
+  h->plan.packed = packed ? 1 : 0;
   // cut panels: packed size <= target and nnz <= panel_nnz
   // hub partials + slack
   const size_t reserve = 16 * 8 * (size_t)std::min<int64_t>(max_hub_tasks, 1 << 20) + (64 << 10);
@@ -116,8 +137,7 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
     int64_t r0 = 0;
     size_t acc = 0;
     for (int64_t i = 0; i < n; ++i) {
-      const int64_t d = rowptr[i + 1] - rowptr[i];
-      const size_t rb = row_bytes(d, tail_max, hub_min, hub_chunk) + 4 + 64;
+      const size_t rb = rbytes[i];
       if (i > r0 && (acc + rb > target || rowptr[i + 1] - rowptr[r0] > panel_nnz)) {
         ranges.push_back({r0, i});
         r0 = i;
@@ -133,17 +153,20 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
   int64_t maxhub = 0;
   for (size_t p = 0; p < ranges.size(); ++p) {
     HostPlan& hp = plans[p];
-    FE_TRY(build_host_plan(rowptr, colidx, ranges[p].first, ranges[p].second, tail_max, hub_min, hub_chunk, hp));
+    FE_TRY(build_host_plan(rowptr, colidx, ranges[p].first, ranges[p].second, tail_max, hub_min,
+                           hub_chunk, packed, hp));
     PanelInfo pi;
     memset(&pi, 0, sizeof(pi));
     pi.r0 = ranges[p].first;
     pi.r1 = ranges[p].second;
     pi.nnz = rowptr[pi.r1] - rowptr[pi.r0];
     size_t off = 0;
-    pi.off_colidx = off; off = align256(off + 4 * (size_t)hp.tcol_total);
+    pi.index_words = packed ? (int64_t)hp.tbits.size() : hp.tcol_total;
+    pi.off_colidx = off; off = align256(off + 4 * (size_t)pi.index_words);
+    h->plan.index_bytes += 4 * (pi.index_words + hp.ell_total);
     pi.off_slice_rows = off; off = align256(off + 4 * hp.slice_rows.size());
     pi.off_ell = off; off = align256(off + 4 * (size_t)hp.ell_total);
-    pi.off_tasks = off; off = align256(off + sizeof(Task) * (size_t)hp.ntasks);
+    pi.off_tasks = off; off = align256(off + (packed ? sizeof(PTask) : sizeof(Task)) * (size_t)hp.ntasks);
     pi.off_hub_rows = off; off = align256(off + 4 * (size_t)hp.nhub);
     pi.off_hub_begin = off; off = align256(off + 4 * (size_t)(hp.nhub + 1));
     pi.bytes = off;
@@ -182,10 +205,12 @@ int semiext_create(fe_csr h, const int64_t* rowptr, const int32_t* colidx, const
     const PanelInfo& pi = sx->panels[p];
     const HostPlan& hp = plans[p];
     char* base = sx->pinned + pi.host_off;
-    memcpy(base + pi.off_colidx, hp.tcol.data(), 4 * (size_t)hp.tcol_total);
+    if (packed) memcpy(base + pi.off_colidx, hp.tbits.data(), 4 * (size_t)pi.index_words);
+    else memcpy(base + pi.off_colidx, hp.tcol.data(), 4 * (size_t)pi.index_words);
     memcpy(base + pi.off_slice_rows, hp.slice_rows.data(), 4 * hp.slice_rows.size());
     memcpy(base + pi.off_ell, hp.ell.data(), 4 * (size_t)hp.ell_total);
-    memcpy(base + pi.off_tasks, hp.tasks.data(), sizeof(Task) * (size_t)hp.ntasks);
+    if (packed) memcpy(base + pi.off_tasks, hp.ptasks.data(), sizeof(PTask) * (size_t)hp.ntasks);
+    else memcpy(base + pi.off_tasks, hp.tasks.data(), sizeof(Task) * (size_t)hp.ntasks);
     memcpy(base + pi.off_hub_rows, hp.hub_rows.data(), 4 * (size_t)hp.nhub);
     memcpy(base + pi.off_hub_begin, hp.hub_task_begin.data(), 4 * (size_t)(hp.nhub + 1));
   }
@@ -234,6 +259,8 @@ int semiext_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStrea
     PlanView v;
     memset(&v, 0, sizeof(v));
     v.colidx = reinterpret_cast<const int32_t*>(base + pi.off_colidx);
+    v.tbits = reinterpret_cast<const uint32_t*>(base + pi.off_colidx);
+    v.packed = sx->packed ? 1 : 0;
     v.tasks = base + pi.off_tasks;
     v.ntasks = pi.ntasks;
     v.nhub_tasks = pi.nhub_tasks;

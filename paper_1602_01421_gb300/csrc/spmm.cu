@@ -27,6 +27,7 @@
 namespace fe {
 
 static_assert(sizeof(Task) == 16, "Task must be 16 bytes");
+static_assert(sizeof(PTask) == 32, "PTask must be 32 bytes");
 
 // Per (type, b, fragment width) geometry: a lane moves NE elements (<= FB bytes: 16, or 32
 // with 256-bit loads when X is 32-byte aligned) per load; an X row of b elements spans C lanes
@@ -46,7 +47,9 @@ struct Geo {
 
 struct SpmmParams {
   const int32_t* colidx;
+  const uint32_t* tbits;
   const Task* tasks;
+  const PTask* ptasks;
   int64_t ntasks, nhub_tasks, task_ctas;
   const int32_t* slice_rows;
   const int32_t* ell;
@@ -60,26 +63,64 @@ struct SpmmParams {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
 
-template <typename T, int B, bool V32>
+template <typename T, int B, bool V32, bool PACKED>
 __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const T* __restrict__ X,
                                          T* __restrict__ Y, T* __restrict__ partial, int lane) {
   using G = Geo<T, B, V32>;
-  const int4 raw = __ldg(reinterpret_cast<const int4*>(p.tasks + ti));
-  const int64_t start = (int64_t)(uint32_t)raw.x | ((int64_t)raw.y << 32);
-  const int row = raw.z;
-  const int len = raw.w;
+  int64_t start;
+  int row, len;
+  int cbase = 0, w = 1;
+  if constexpr (PACKED) {
+    const int4 r0 = __ldg(reinterpret_cast<const int4*>(p.ptasks + ti));
+    const int4 r1 = __ldg(reinterpret_cast<const int4*>(p.ptasks + ti) + 1);
+    start = (int64_t)(uint32_t)r0.x | ((int64_t)r0.y << 32);  // word offset
+    row = r0.z;
+    len = r0.w;
+    cbase = r1.x;
+    w = r1.y;
+  } else {
+    const int4 raw = __ldg(reinterpret_cast<const int4*>(p.tasks + ti));
+    start = (int64_t)(uint32_t)raw.x | ((int64_t)raw.y << 32);
+    row = raw.z;
+    len = raw.w;
+  }
   const int chunk = lane % G::C;
   const int slot = lane / G::C;
   T acc[G::NE];
 #pragma unroll
   for (int e = 0; e < G::NE; ++e) acc[e] = T(0);
   const int32_t* __restrict__ ci = p.colidx + start;
+  const uint32_t* __restrict__ tb = p.tbits + start;
+  const uint32_t wmask = (1u << w) - 1u;  // 1 <= w <= 31
+  int carry = cbase;  // packed: the column reached by the previous round
   for (int base = 0; base < len; base += 32 * G::UNROLL) {
     int cols[G::UNROLL];
 #pragma unroll
     for (int u = 0; u < G::UNROLL; ++u) {
       int k = base + u * 32 + lane;
-      cols[u] = k < len ? __ldcs(ci + k) : -1;
+      if constexpr (PACKED) {
+        // field k of w bits, then an inclusive prefix sum of the gaps across the warp
+        if (base + u * 32 < len) {
+          int g = 0;
+          if (k < len) {
+            const int64_t bit = (int64_t)k * w;
+            const int64_t wi = bit >> 5;
+            g = (int)(__funnelshift_r(__ldcs(tb + wi), __ldcs(tb + wi + 1), (int)(bit & 31)) & wmask);
+          }
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(kFull, g, off);
+            if (lane >= off) g += y;
+          }
+          const int col = carry + g;
+          carry = __shfl_sync(kFull, col, 31);
+          cols[u] = k < len ? col : -1;
+        } else {
+          cols[u] = -1;
+        }
+      } else {
+        cols[u] = k < len ? __ldcs(ci + k) : -1;
+      }
     }
 #pragma unroll
     for (int u = 0; u < G::UNROLL; ++u) {
@@ -174,13 +215,13 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
   }
 }
 
-template <typename T, int B, bool V32>
+template <typename T, int B, bool V32, bool PACKED>
 __global__ void __launch_bounds__(256) spmm_main_kernel(const SpmmParams p, const T* __restrict__ X,
                                                         T* __restrict__ Y, T* __restrict__ partial) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if ((int64_t)blockIdx.x < p.task_ctas) {
     const int64_t ti = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-    if (ti < p.ntasks) run_task<T, B, V32>(p, ti, X, Y, partial, lane);
+    if (ti < p.ntasks) run_task<T, B, V32, PACKED>(p, ti, X, Y, partial, lane);
   } else {
     const int64_t si = ((int64_t)blockIdx.x - p.task_ctas) * kWarpsPerCta + warp;
     if (si < p.nslices) run_slice<T, B, V32>(p, si, X, Y, lane);
@@ -206,7 +247,9 @@ static int launch_spmm(const PlanView& pv, const T* X, T* Y, T* partial, cudaStr
   SpmmParams p;
   memset(&p, 0, sizeof(p));
   p.colidx = pv.colidx;
+  p.tbits = pv.tbits;
   p.tasks = reinterpret_cast<const Task*>(pv.tasks);
+  p.ptasks = reinterpret_cast<const PTask*>(pv.tasks);
   p.ntasks = pv.ntasks;
   p.nhub_tasks = pv.nhub_tasks;
   p.slice_rows = pv.slice_rows;
@@ -226,10 +269,13 @@ static int launch_spmm(const PlanView& pv, const T* X, T* Y, T* partial, cudaStr
     bool v32 = false;
     if constexpr (B * sizeof(T) >= 32) v32 = ((uintptr_t)X % 32) == 0;
     if (v32) {
-      if constexpr (B * sizeof(T) >= 32)
-        spmm_main_kernel<T, B, true><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+      if constexpr (B * sizeof(T) >= 32) {
+        if (pv.packed) spmm_main_kernel<T, B, true, true><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+        else spmm_main_kernel<T, B, true, false><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+      }
     } else {
-      spmm_main_kernel<T, B, false><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+      if (pv.packed) spmm_main_kernel<T, B, false, true><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+      else spmm_main_kernel<T, B, false, false><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
     }
     count_launch();
     FE_CUDA(cudaGetLastError());
@@ -249,6 +295,8 @@ PlanView resident_view(fe_csr h) {
   PlanView v;
   memset(&v, 0, sizeof(v));
   v.colidx = h->d_colidx;
+  v.tbits = pl.d_tbits;
+  v.packed = pl.packed;
   v.tasks = pl.d_tasks;
   v.ntasks = pl.ntasks;
   v.nhub_tasks = pl.nhub_tasks;
@@ -318,8 +366,71 @@ static int dev_upload(fe_csr h, void** dst, const void* src, size_t bytes) {
 
 // Plan of rows [r0, r1): task starts are offsets into hp.tcol, the column indices of the
 // panel's task rows only (tail rows are read from the ELL slices); row ids are global.
+static int bit_length(uint32_t x) { return x == 0 ? 0 : 32 - __builtin_clz(x); }
+
+size_t plan_row_index_bytes(const int32_t* cols, int64_t d, int tail_max, int hub_chunk, bool packed) {
+  if (d <= tail_max || !packed) return 4 * (size_t)d;
+  // packed: every chunk of hub_chunk entries is a segment of one gap width, word-aligned
+  std::vector<int32_t> sorted;
+  const int32_t* c = cols;
+  if (!std::is_sorted(cols, cols + d)) {
+    sorted.assign(cols, cols + d);
+    std::sort(sorted.begin(), sorted.end());
+    c = sorted.data();
+  }
+  size_t bytes = 0;
+  for (int64_t s0 = 0; s0 < d; s0 += hub_chunk) {
+    const int64_t s1 = std::min<int64_t>(d, s0 + hub_chunk);
+    int w = 1;
+    for (int64_t k = s0 + 1; k < s1; ++k) w = std::max(w, bit_length((uint32_t)(c[k] - c[k - 1])));
+    bytes += 4 * (size_t)ceil_div((s1 - s0) * w, 32) + 16;  // + the larger task record
+  }
+  return bytes;
+}
+
+// Packed index format: each task's sorted columns become gap fields of the task's width w
+// (g_0 = 0, g_k = c_k - c_{k-1}) in a word-aligned segment of the bit stream, so that tasks can
+// be encoded in parallel; two zero words pad the end (the decoder reads a two-word window).
+static void pack_tasks(HostPlan& hp) {
+  const int64_t nt = hp.ntasks;
+  hp.ptasks.resize(nt);
+  std::vector<int64_t> words(nt + 1, 0);
+  #pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t t = 0; t < nt; ++t) {
+    const Task& tk = hp.tasks[t];
+    const int32_t* c = hp.tcol.data() + tk.start;
+    int w = 1;
+    for (int k = 1; k < tk.len; ++k) w = std::max(w, bit_length((uint32_t)(c[k] - c[k - 1])));
+    hp.ptasks[t] = PTask{0, tk.row, tk.len, c[0], w, 0, 0};
+    words[t + 1] = ceil_div((int64_t)tk.len * w, 32);
+  }
+  for (int64_t t = 0; t < nt; ++t) words[t + 1] += words[t];
+  hp.tbits.assign(words[nt] + 2, 0u);
+  #pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t t = 0; t < nt; ++t) {
+    PTask& pt = hp.ptasks[t];
+    pt.woff = words[t];
+    const int32_t* c = hp.tcol.data() + hp.tasks[t].start;
+    uint32_t* out = hp.tbits.data() + words[t];
+    const int w = pt.w;
+    for (int k = 1; k < pt.len; ++k) {
+      const uint32_t g = (uint32_t)(c[k] - c[k - 1]);
+      const int64_t bit = (int64_t)k * w;
+      const int64_t wi = bit >> 5;
+      const int sh = (int)(bit & 31);
+      out[wi] |= g << sh;
+      if (sh + w > 32) out[wi + 1] |= g >> (32 - sh);
+    }
+  }
+  hp.tcol.clear();
+  hp.tcol.shrink_to_fit();
+  hp.tasks.clear();
+  hp.tasks.shrink_to_fit();
+  hp.packed = true;
+}
+
 int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
-                    int tail_max, int hub_min, int hub_chunk, HostPlan& hp) {
+                    int tail_max, int hub_min, int hub_chunk, bool packed, HostPlan& hp) {
   hp = HostPlan();
   std::vector<int64_t> tail_cnt(tail_max + 1, 0);
   std::vector<int64_t> mid_cnt(hub_min + 1, 0);
@@ -384,6 +495,8 @@ int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, in
       continue;
     }
     memcpy(hp.tcol.data() + tpos, colidx + rowptr[i], sizeof(int32_t) * (size_t)d);
+    if (packed && !std::is_sorted(hp.tcol.data() + tpos, hp.tcol.data() + tpos + d))
+      std::sort(hp.tcol.data() + tpos, hp.tcol.data() + tpos + d);
     if (d <= hub_min) {
       hp.tasks[mid_pos[d]++] = Task{tpos, (int32_t)i, (int32_t)d};
     } else {
@@ -417,11 +530,12 @@ int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, in
     }
   }
   hp.ell_total = ell_total;
+  if (packed) pack_tasks(hp);
   return FE_OK;
 }
 
 int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx_raw, int tail_max,
-                    int hub_min, int hub_chunk) {
+                    int hub_min, int hub_chunk, bool packed) {
   const int64_t n = h->n;
   const int32_t* colidx = colidx_raw;
   fe_spmm_plan& pl = h->plan;
@@ -429,7 +543,8 @@ int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx_raw, 
   pl.hub_min = hub_min;
   pl.hub_chunk = hub_chunk;
   HostPlan hp;
-  FE_TRY(build_host_plan(rowptr, colidx, 0, n, tail_max, hub_min, hub_chunk, hp));
+  FE_TRY(build_host_plan(rowptr, colidx, 0, n, tail_max, hub_min, hub_chunk, packed, hp));
+  pl.packed = packed ? 1 : 0;
   h->max_degree = hp.max_degree;
   h->rows_empty = hp.rows_empty;
   h->rows_tail = hp.rows_tail;
@@ -445,10 +560,17 @@ int spmm_build_plan(fe_csr h, const int64_t* rowptr, const int32_t* colidx_raw, 
   pl.ntasks = hp.ntasks;
   pl.nhub_tasks = hp.nhub_tasks;
   pl.nhub = hp.nhub;
-  FE_TRY(dev_upload(h, (void**)&h->d_colidx, hp.tcol.data(), sizeof(int32_t) * hp.tcol_total));
+  if (packed) {
+    FE_TRY(dev_upload(h, (void**)&pl.d_tbits, hp.tbits.data(), sizeof(uint32_t) * hp.tbits.size()));
+    FE_TRY(dev_upload(h, &pl.d_tasks, hp.ptasks.data(), sizeof(PTask) * hp.ntasks));
+    pl.index_bytes = (int64_t)(sizeof(uint32_t) * hp.tbits.size() + sizeof(int32_t) * hp.ell_total);
+  } else {
+    FE_TRY(dev_upload(h, (void**)&h->d_colidx, hp.tcol.data(), sizeof(int32_t) * hp.tcol_total));
+    FE_TRY(dev_upload(h, &pl.d_tasks, hp.tasks.data(), sizeof(Task) * hp.ntasks));
+    pl.index_bytes = (int64_t)(sizeof(int32_t) * (hp.tcol_total + hp.ell_total));
+  }
   FE_TRY(dev_upload(h, (void**)&pl.d_slice_rows, hp.slice_rows.data(), sizeof(int32_t) * hp.slice_rows.size()));
   FE_TRY(dev_upload(h, (void**)&pl.d_ell, hp.ell.data(), sizeof(int32_t) * hp.ell_total));
-  FE_TRY(dev_upload(h, &pl.d_tasks, hp.tasks.data(), sizeof(Task) * hp.ntasks));
   FE_TRY(dev_upload(h, (void**)&pl.d_hub_rows, hp.hub_rows.data(), sizeof(int32_t) * hp.nhub));
   FE_TRY(dev_upload(h, (void**)&pl.d_hub_task_begin, hp.hub_task_begin.data(), sizeof(int32_t) * (hp.nhub + 1)));
   if (hp.nhub_tasks > 0) {

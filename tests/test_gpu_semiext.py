@@ -26,9 +26,10 @@ def test_semiext_equals_resident_and_oracle(g16, prec, b, direct):
     with fe.Csr.from_graph(g16, device_mem_cap_bytes=3 << 20, semi_direct=direct) as hs:
         info = hs.info()
         Ys = fe.spmm(hs, Xd).cpu().numpy()
-    # the small cap picks a smaller slice cutoff; the resident handle takes the same one
-    assert 4 <= info["tail_max"] < 128
-    with fe.Csr.from_graph(g16, tail_max=info["tail_max"]) as hr:
+    # semi-external handles default to packed indices and a small slice cutoff; the resident
+    # handle takes the same plan shape
+    assert info["index_format"] == 2 and 4 <= info["tail_max"] <= 16
+    with fe.Csr.from_graph(g16, tail_max=info["tail_max"], index_format="packed") as hr:
         Yr = fe.spmm(hr, Xd).cpu().numpy()
     assert info["semi_external"] == 1 and info["panels"] > 2
     assert info["device_bytes"] <= 3 << 20
@@ -53,9 +54,22 @@ def test_semiext_eigs_matches_resident(direct):
         assert hs.info()["semi_external"] == 1
         tm = hs.info()["tail_max"]
         ev_s, X, st_s = fe.eigs(hs, 8, 4, 8, 1e-8, "LM", seed=1)
-    with fe.Csr.from_graph(g, tail_max=tm) as hr:
+    with fe.Csr.from_graph(g, tail_max=tm, index_format="packed") as hr:
         ev_r, _, st_r = fe.eigs(hr, 8, 4, 8, 1e-8, "LM", seed=1)
     assert np.allclose(ev_s, ev_r, rtol=1e-12) and st_s["restarts"] == st_r["restarts"]
+
+
+@pytest.mark.parametrize("fmt", ["plain", "packed"])
+def test_semiext_index_formats_match_oracle(g16, fmt):
+    """Both column-index formats streamed in panels; packed panels move fewer bytes."""
+    X = graphgen.normal_block(g16.n, 4, seed=21)
+    with fe.Csr.from_graph(g16, device_mem_cap_bytes=3 << 20, index_format=fmt) as hs:
+        info = hs.info()
+        Y = fe.spmm(hs, to_dev(X)).cpu().numpy()
+    assert info["semi_external"] == 1 and info["index_format"] == (2 if fmt == "packed" else 1)
+    if fmt == "packed":
+        assert info["index_bytes"] < 0.8 * 4 * g16.nnz
+    assert_spmm_close(g16, X, Y, 1e-13)
 
 
 def test_cap_large_enough_stays_resident(g16):

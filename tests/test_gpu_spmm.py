@@ -52,15 +52,17 @@ def test_spmm_parity(graphs, name, b, prec):
                                    dict(tail_max=4, hub_min=64, hub_chunk=4096),
                                    dict(tail_max=128, hub_min=200, hub_chunk=100)])
 def test_spmm_parity_all_paths_small(prec, knobs):
-    """Tiny thresholds push most rows through the hub split and the partial reduce."""
+    """Tiny thresholds push most rows through the hub split and the partial reduce, with plain
+    and with packed column indices."""
     g = graphgen.rmat(13, seed=9)
-    for b in (1, 4, 16):
-        X = graphgen.normal_block(g.n, b, seed=b, dtype=NP[prec])
-        with fe.Csr.from_graph(g, **knobs) as h:
-            info = h.info()
-            Y = fe.spmm(h, to_dev(X)).cpu().numpy()
-        assert info["rows_hub"] > 0
-        assert_spmm_close(g, X, Y, TOL[prec])
+    for fmt in ("plain", "packed"):
+        for b in (1, 4, 16):
+            X = graphgen.normal_block(g.n, b, seed=b, dtype=NP[prec])
+            with fe.Csr.from_graph(g, index_format=fmt, **knobs) as h:
+                info = h.info()
+                Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+            assert info["rows_hub"] > 0
+            assert_spmm_close(g, X, Y, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
@@ -101,6 +103,51 @@ def test_spmm_parity_16_byte_aligned_blocks(graphs, prec, b):
         Y32 = fe.spmm(h, to_dev(X)).cpu().numpy()
     assert_spmm_close(g, X, Y16, TOL[prec])
     assert_spmm_close(g, X, Y32, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("name", ["rmat14", "rmat13-noperm", "star9000", "complete300", "er3000",
+                                  "union-isolated"])
+def test_spmm_parity_packed_index(graphs, prec, name):
+    """Task rows' columns as bit-packed gaps (index_format packed): same results as the oracle,
+    fewer index bytes than the plain plan."""
+    g = graphs[name]
+    with fe.Csr.from_graph(g, index_format="packed") as h, fe.Csr.from_graph(g, tail_max=16) as hp:
+        info, info_plain = h.info(), hp.info()
+        assert info["index_format"] == 2 and info_plain["index_format"] == 1
+        assert info["tail_max"] == 16
+        if info["rows_mid"] + info["rows_hub"] > 0:
+            assert info["index_bytes"] < info_plain["index_bytes"]
+        for b in (1, 2, 4, 8, 16):
+            X = graphgen.normal_block(g.n, b, seed=b + 30, dtype=NP[prec])
+            Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+            assert_spmm_close(g, X, Y, TOL[prec])
+            # same column order and task split as the plain plan: identical results
+            assert np.array_equal(Y, fe.spmm(hp, to_dev(X)).cpu().numpy())
+
+
+@pytest.mark.parametrize("fmt", ["plain", "packed"])
+def test_spmm_unsorted_rows_and_duplicates(fmt):
+    """CSR rows in arbitrary order with repeated entries (A_ij = multiplicity); the packed
+    plan sorts each row before taking gaps (gap 0 for a repeat)."""
+    g = graphgen.rmat(12, seed=4)
+    rng = np.random.default_rng(3)
+    rows, cols = [], []
+    for i in range(g.n):
+        c = list(g.colidx[g.rowptr[i]:g.rowptr[i + 1]])
+        c += [int(x) for x in rng.choice(c, size=min(len(c), 3), replace=False)] if c else []
+        rng.shuffle(c)
+        rows.append(len(c))
+        cols.extend(c)
+    rowptr = np.concatenate([[0], np.cumsum(rows)]).astype(np.int64)
+    colidx = np.array(cols, dtype=np.int32)
+    gu = graphgen.CSR(g.n, rowptr, colidx, "unsorted-dup")
+    for prec in ("f32", "f64"):
+        for b in (1, 4, 16):
+            X = graphgen.normal_block(g.n, b, seed=b, dtype=NP[prec])
+            with fe.Csr(rowptr, colidx, index_format=fmt, tail_max=8, hub_min=64, hub_chunk=48) as h:
+                Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+            assert_spmm_close(gu, X, Y, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
