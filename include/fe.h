@@ -111,7 +111,8 @@ typedef struct {
   int index_format;
   /* 1 = also build the transposed pattern A^T (host counting sort at create, then its own
    * SpMM plan), needed by fe_spmm_t and fe_svds: a directed graph's adjacency matrix is not
-   * symmetric (Section 4.3.2).  Resident handles only.  Default 0. */
+   * symmetric (Section 4.3.2).  With a device_mem_cap_bytes, A^T gets its own panels under the
+   * same cap (the pair may hold up to twice the cap on the device).  Default 0. */
   int transpose;
 } fe_csr_opts;
 
@@ -355,7 +356,7 @@ int fe_eigs_ex(fe_csr h, int nev, int block, int nblocks, double tol, fe_which w
  * operator A^T A (one fe_spmm and one fe_spmm_t per block), largest eigenvalues first; then
  * sigma_i = sqrt(theta_i), v_i = the Ritz vectors, u_i = A v_i / sigma_i (0 if sigma_i = 0).
  * The convergence test is fe_eigs_ex's, applied to A^T A (tol relative to theta = sigma^2).
- * The handle needs fe_csr_opts.transpose = 1 and must be resident.  block, nblocks, opts as
+ * The handle needs fe_csr_opts.transpose = 1 (resident or semi-external).  block, nblocks, opts as
  * for fe_eigs_ex (modes FP64 and MIXED; starts RANDOM and USER; FE_START_LEARNED is rejected).
  * svals: HOST, nsv doubles.  right, left: DEVICE, n x nsv COLUMN-major FP64, each may be
  * NULL; each v_i has its largest-magnitude entry positive.  stats->spmm_blocks counts

@@ -200,8 +200,6 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   FE_ARG(nnz == 0 || colidx != nullptr, "fe_csr_create: colidx is NULL");
   if (o.validate) FE_TRY(validate_csr(n, rowptr, colidx));
   if (o.check_symmetric) FE_TRY(check_symmetric(n, rowptr, colidx));
-  FE_ARG(!o.transpose || o.device_mem_cap_bytes <= 0,
-         "fe_csr_create: transpose needs a resident handle (device_mem_cap_bytes = 0)");
   fe_csr h = new fe_csr_s();
   h->n = n;
   h->nnz = nnz;

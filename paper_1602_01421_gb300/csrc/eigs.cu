@@ -43,6 +43,12 @@ int normalize_signs(double* X, int64_t n, int ncols, cudaStream_t s);
 int mlp_start_block(fe_csr h, const float* weights, int hidden, int b, uint64_t seed,
                     double* out, cudaStream_t s);
 
+// Y = A X on a resident or a semi-external handle
+static int spmm_any(fe_csr h, const void* X, void* Y, int b, fe_dtype dt, cudaStream_t s) {
+  if (h->semi_external) return semiext_spmm(h, X, Y, b, dt, s);
+  return spmm_resident(h, X, Y, b, dt, s);
+}
+
 constexpr double kSmallTheta = 1e-3;
 constexpr uint64_t kStreamStart = 4;
 constexpr int kStagnated = 1;  // Phase::run: the FP32 phase stopped improving
@@ -151,14 +157,13 @@ struct Phase {
     return FE_OK;
   }
 
-  // Yb = Op X: A X, or A^T (A X) for the SVD operator
+  // Yb = Op X: A X, or A^T (A X) for the SVD operator (either handle may stream its panels)
   int spmm_dispatch(const void* X, void* Yb) {
     if (op_ata) {
-      FE_TRY(spmm_resident(h, X, opbuf.p, b, dt, s));
-      return spmm_resident(h->t, opbuf.p, Yb, b, dt, s);
+      FE_TRY(spmm_any(h, X, opbuf.p, b, dt, s));
+      return spmm_any(h->t, opbuf.p, Yb, b, dt, s);
     }
-    if (h->semi_external) return semiext_spmm(h, X, Yb, b, dt, s);
-    return spmm_resident(h, X, Yb, b, dt, s);
+    return spmm_any(h, X, Yb, b, dt, s);
   }
 
   // Ritz values/vectors of the current H, convergence estimate; returns nconv
@@ -504,7 +509,6 @@ int fe_svds(fe_csr h, int nsv, int block, int nblocks, double tol, const fe_eigs
             double* svals, double* right, double* left, fe_eigs_stats* stats) {
   FE_ARG(h != nullptr, "fe_svds: NULL handle");
   FE_ARG(h->t != nullptr, "fe_svds: the handle has no transpose (create it with transpose = 1)");
-  FE_ARG(!h->semi_external, "fe_svds: the handle must be resident");
   FE_ARG(svals != nullptr, "fe_svds: svals is NULL");
   FE_ARG(!opts || opts->start != FE_START_LEARNED, "fe_svds: FE_START_LEARNED is not supported");
   cudaStream_t s = cur_stream();
@@ -526,7 +530,7 @@ int fe_svds(fe_csr h, int nsv, int block, int nblocks, double tol, const fe_eigs
   if (left) {
     // u_c = A v_c / sigma_c, one column at a time (b = 1 SpMMs on the column-major V)
     for (int c = 0; c < nsv; ++c)
-      FE_TRY(spmm_resident(h, V + (size_t)c * n, left + (size_t)c * n, 1, FE_F64, s));
+      FE_TRY(spmm_any(h, V + (size_t)c * n, left + (size_t)c * n, 1, FE_F64, s));
     DevBuf dinv;
     FE_TRY(dinv.alloc(sizeof(double) * nsv));
     FE_CUDA(cudaMemcpyAsync(dinv.p, inv.data(), sizeof(double) * nsv, cudaMemcpyHostToDevice, s));

@@ -50,8 +50,6 @@ def test_spmm_t_needs_the_transpose():
             fe.spmm_t(h, to_dev(np.ones((g.n, 4))))
         with pytest.raises(fe.FeError):
             fe.svds(h, 4, 2, 8, 1e-8)
-    with pytest.raises(fe.FeError):
-        fe.Csr.from_graph(g, transpose=True, device_mem_cap_bytes=1 << 20)
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
@@ -77,6 +75,30 @@ def test_svds_matches_oracle_and_dense(mode):
     # the right singular subspace agrees with the oracle's
     c = np.linalg.svd(ref.right.T @ V, compute_uv=False)
     assert c.min() > 1 - 1e-6
+
+
+@pytest.mark.parametrize("fmt", ["plain", "packed"])
+def test_svds_semi_external(fmt):
+    """The paper's setting for its directed page graph: the SVD with the matrix (and here its
+    transpose) streamed in panels from pinned host memory."""
+    g = graphgen.rmat(14, seed=7, directed=True)
+    t = _tcsr(g)
+    ref = svd.svds(g.rowptr, g.colidx, 6, 2, 12, 1e-8, seed=1)
+    X = graphgen.normal_block(g.n, 4, seed=2)
+    with fe.Csr.from_graph(g, device_mem_cap_bytes=1 << 18, index_format=fmt) as hs:
+        info = hs.info()
+        assert info["semi_external"] == 1 and info["has_transpose"] == 1 and info["panels"] > 2
+        Yt = fe.spmm_t(hs, to_dev(X)).cpu().numpy()
+        sv, V, U, st = fe.svds(hs, 6, 2, 12, 1e-8, seed=1)
+    ref_t = core.spmm(t.rowptr, t.colidx, X)
+    assert np.all(np.abs(Yt - ref_t) <= 1e-13 * core.spmm(t.rowptr, t.colidx, np.abs(X)))
+    assert st["converged"]
+    assert np.allclose(sv, ref.svals, rtol=1e-8)
+    A = g.dense()
+    V, U = V.cpu().numpy(), U.cpu().numpy()
+    assert np.abs(A @ V - U * sv).max() <= 1e-12 * sv[0]
+    r = np.linalg.norm(A.T @ (A @ V) - V * sv ** 2, axis=0)
+    assert np.all(r <= 1e-8 * sv[0] ** 2 * 1.001)
 
 
 def test_svds_same_start_same_iteration_as_oracle():
