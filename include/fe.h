@@ -7,13 +7,14 @@
  * Table 1 (MvTransMv, MvTimesMatAddMv, ...).  This library runs all of it on one GPU:
  *
  *   fe_csr_create / fe_csr_create_ex / fe_csr_destroy   the sparse matrix (Section 3.3.1)
- *   fe_spmm                                              Y = A X   (Section 3.3.3)
+ *   fe_spmm / fe_spmm_t                                  Y = A X, Y = A^T X (Section 3.3.3)
  *   fe_block_gram                                        MvTransMv  (Table 1, "op3")
  *   fe_block_update                                      MvTimesMatAddMv (Table 1, "op1")
  *   fe_block_update_gram                                 op1 then op3 on the result, one sweep
  *   fe_block_orth                                        re-orthogonalisation (Section 3.1)
  *   fe_random_normal                                     MvRandom (Table 1)
  *   fe_eigs / fe_eigs_ex                                 Block Krylov-Schur (Sections 1, 3.1)
+ *   fe_svds                                              singular triplets via A^T A (4.3.2)
  *
  * Conventions shared by every entry point:
  *  - Return 0 (FE_OK) on success and a negative FE_ERR_* code on failure; fe_last_error()

@@ -14,6 +14,10 @@
 // The subspace lives in HBM as NB+1 row-major n x b blocks (plus NB-1 spares); the host sees
 // only the m Ritz values and residual estimates once per restart.
 //
+// SVD (fe_svds, Section 4.3.2): the same iteration on the operator A^T A (an SpMM with A, then
+// one with the handle's transpose), largest eigenvalues first; sigma = sqrt(theta), left
+// vectors A v / sigma.
+//
 // Mixed mode: the same iteration with an FP32 subspace, FP32 SpMM and FP32 block updates
 // (FP64 small matrices, FP64 CholQR factors and Gram reductions) to a loose tolerance, then
 // the FP64 iteration restarted from the FP32 Ritz vectors as its start block (block size

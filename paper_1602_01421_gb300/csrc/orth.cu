@@ -8,6 +8,10 @@
 //           R1 = chol(S - G2^T G2)      (CholeskyQR pass 1, pivots checked)
 //           W <- (W - V G2) R1^{-1}     (one fused update)
 //   pass 3  R2 = chol(W^T W),  W <- W R2^{-1},  R = R2 R1   (CholeskyQR pass 2)
+// With pass1_f32 (the solver's default for FP64 subspaces) the pass-1 Gram runs in FP32
+// arithmetic -- G1 only steers the subtraction, and H records G1 + G2, what was subtracted --
+// and pass 2's correction V C (C = -G2 R1^{-1}, entries below 1e-5) is formed in FP32
+// arithmetic and added to the FP64 W R1^{-1}; all other products are FP64.
 // The small b x b / k x b algebra runs in single-CTA kernels; updates after a failed pivot
 // check are skipped on the device and the host finishes with column-wise two-pass
 // Gram-Schmidt, replacing a column whose remainder is below 1e-12 ||A|| by a random

@@ -4,17 +4,22 @@
 // GB300 layout of A, built once per handle from the CSR (Section 3.3.1 / 3.3.3 motives: the
 // paper fights branchy single-entry rows with SCSR+COO tiles and power-law load imbalance
 // with work stealing; here the same two problems are solved by degree binning):
-//   * tail rows (degree <= tail_max, 85% of R-MAT rows): grouped by degree into 32-row
-//     slices whose column indices are stored transposed ("SELL-32"): lane l of a warp owns
-//     row l of the slice and step t loads ell[t*32 + l], one coalesced 128-byte load per
-//     step and no divergence, since all 32 rows of a slice have the same degree;
+//   * tail rows (degree <= tail_max, default 128; 97% of the scale-22 R-MAT rows): grouped by
+//     exact degree into 32-row slices whose column indices are stored transposed
+//     ("SELL-32"): lane l of a warp owns row l of the slice and step t loads ell[t*32 + l],
+//     one coalesced 128-byte load per step and no divergence or masked lane, since all 32
+//     rows of a slice have the same degree;
 //   * mid rows (tail_max < degree <= hub_min): one warp per row (a "task"), 32 consecutive
-//     column indices per coalesced load, each lane gathering 16 bytes of an X row;
+//     column indices per coalesced load, each lane gathering up to 32 bytes of an X row
+//     (one 256-bit load when X is 32-byte aligned), partial sums combined by a
+//     reduce-scatter butterfly;
 //   * hub rows (degree > hub_min): split into tasks of hub_chunk non-zeros; each task writes
 //     a partial row, and a second kernel adds a hub's partials in task order (deterministic,
 //     no atomics).
 // Tasks are ordered longest first so the block scheduler handles them like a longest-
-// processing-time list; tail slices follow in the same launch.
+// processing-time list; tail slices follow in the same launch.  The task rows' column
+// indices are stored either as int32 or, in the packed format, as per-task gap fields that a
+// warp decodes with a prefix sum (fewer bytes to stream from host memory).
 #include <stdio.h>
 #include <string.h>
 
