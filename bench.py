@@ -217,7 +217,8 @@ def run_ours(args):
     t_gen = time.perf_counter() - t_gen
     n, nnz = g.n, g.nnz
     t0 = time.perf_counter()
-    h = fe.Csr.from_graph(g)
+    # --index-format applies to the profiler mode spmm1; the step uses the default plan
+    h = fe.Csr.from_graph(g, index_format=args.index_format if args.only == "spmm1" else "auto")
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     info = h.info()
@@ -655,7 +656,7 @@ def main():
     ap.add_argument("--no-svd", action="store_true", help="skip the directed-graph SVD leg")
     ap.add_argument("--no-semi", action="store_true")
     ap.add_argument("--index-format", default="auto", choices=["auto", "plain", "packed"],
-                    help="semiext27: column-index format of the streamed CSR")
+                    help="semiext27 and --only spmm1: column-index format of the CSR")
     ap.add_argument("--semi-modes", default="mixed,fp64",
                     help="semiext27: solve modes to time on the semi-external handle ('' = none)")
 

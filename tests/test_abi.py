@@ -68,6 +68,19 @@ def test_null_and_bad_arguments():
     assert lib.fe_csr_create(0, None, None, ctypes.byref(out)) == _lib.FE_ERR_INVALID
 
 
+def test_bad_index_format_rejected_on_host():
+    lib = fe.load()
+    rowptr = np.array([0, 1, 2], dtype=np.int64)
+    colidx = np.array([1, 0], dtype=np.int32)
+    o = _lib.CsrOpts()
+    lib.fe_csr_opts_default(ctypes.byref(o))
+    o.index_format = 7
+    out = ctypes.c_void_p()
+    rc = lib.fe_csr_create_ex(2, rowptr.ctypes.data_as(ctypes.c_void_p),
+                              colidx.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), ctypes.byref(out))
+    assert rc == _lib.FE_ERR_INVALID and b"index_format" in lib.fe_last_error()
+
+
 def test_struct_layouts_match_header():
     # field offsets the C compiler gives the structs (x86-64 and aarch64 share the LP64 ABI)
     assert ctypes.sizeof(_lib.CsrOpts) == 56
