@@ -7,13 +7,16 @@ plain FP64 Block Krylov-Schur solve for the 8 largest-magnitude eigenpairs, bloc
 (subspace 32), tol 1e-8, counter-RNG start: SpMM, block Gram/update re-orthogonalisation,
 CholQR2, Rayleigh-Ritz, restarts and the explicit residual check, all on the GPU.
 Beside it: the SpMM sweep b in {1,2,4,8,16} x {FP32, FP64} in GB/s of compulsory bytes, the
-mixed-precision solve, the end-to-end time through host buffers, and the CPU oracle.
+mixed-precision and learned-start solves, 32 eigenpairs with a 128-vector subspace, the SVD
+of a directed R-MAT graph, the semi-external SpMM, the end-to-end time through host buffers,
+and the CPU oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scale S]
+    python bench.py --config mixed24|learned24|semiext27     (the larger configurations)
 
-Under torchrun (N > 1) every rank solves its own copy of the workload (replicas: the solve
-does not shard across the single-GPU machines this targets); value = all ranks' solves / the
-slowest rank's time.
+Under torchrun (N > 1) every rank solves its own copy of the workload (replicas: one solve
+runs on one GPU and is not split across GPUs); value = all ranks' solves / the slowest rank's
+time.
 """
 from __future__ import annotations
 
