@@ -314,6 +314,12 @@ typedef struct {
                              arithmetic (the FP64 second pass restores full orthogonality, and
                              the coefficients actually subtracted enter H, so the Krylov
                              relation keeps FP64 accuracy), 1 = in FP64 (0) */
+  int subspace_host;      /* 1 = keep the subspace blocks in pinned host memory that the GPU
+                             reads and writes over the CPU-GPU link (the paper's external-memory
+                             vector subspace, Section 3.4.3), with the newest block cached in
+                             device memory for the next SpMM (its most-recent-matrix caching,
+                             Section 3.4.4); for subspaces larger than HBM.  Same arithmetic,
+                             same results as 0 (default). */
 } fe_eigs_opts;
 
 void fe_eigs_opts_default(fe_eigs_opts* opts);

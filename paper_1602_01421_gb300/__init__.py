@@ -208,8 +208,10 @@ def random_normal(n: int, b: int, dtype=None, seed: int = 1, stream: int = 4, of
 def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: str = "LM", *,
          mode: str = "fp64", start=None, seed: int = 1, max_restarts: int = 500,
          mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 5e-6,
-         orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True):
-    """Block Krylov-Schur (fe_eigs_ex).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
+         orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True,
+         subspace: str = "device"):
+    """Block Krylov-Schur (fe_eigs_ex).  subspace="host" keeps the subspace blocks in pinned
+    host memory (newest block cached on the device).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
     None, stats dict).  orth_pass1: "fp32" or "fp64" arithmetic for the first Gram-Schmidt
     pass's Gram on an FP64 subspace."""
     torch = _torch()
@@ -221,6 +223,7 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
     o.mode = _lib.MODE[mode]
     o.mixed_tol = float(mixed_tol)
     o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
+    o.subspace_host = {"device": 0, "host": 1}[subspace]
     o.mlp_hidden = int(mlp_hidden)
     if start is not None:
         start = start.to(torch.float64).contiguous()
@@ -246,7 +249,8 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
 
 def svds(h: Csr, nsv: int, block: int, nblocks: int, tol: float = 1e-8, *, mode: str = "fp64",
          start=None, seed: int = 1, max_restarts: int = 500, mixed_tol: float = 5e-6,
-         orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True):
+         orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True,
+         subspace: str = "device"):
     """Largest singular triplets of the handle's matrix (fe_svds; needs transpose=True).
     Returns (svals numpy, right (n, nsv) CUDA float64 or None, left (n, nsv) or None, stats)."""
     torch = _torch()
@@ -258,6 +262,7 @@ def svds(h: Csr, nsv: int, block: int, nblocks: int, tol: float = 1e-8, *, mode:
     o.mode = _lib.MODE[mode]
     o.mixed_tol = float(mixed_tol)
     o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
+    o.subspace_host = {"device": 0, "host": 1}[subspace]
     if start is not None:
         start = start.to(torch.float64).contiguous()
         o.start = _lib.START["user"]

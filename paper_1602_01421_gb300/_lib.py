@@ -48,7 +48,7 @@ class EigsOpts(ctypes.Structure):
                 ("start", ctypes.c_int), ("start_block", ctypes.c_void_p),
                 ("mlp_weights", ctypes.c_void_p), ("mlp_hidden", ctypes.c_int),
                 ("mixed_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
-                ("orth_pass1", ctypes.c_int)]
+                ("orth_pass1", ctypes.c_int), ("subspace_host", ctypes.c_int)]
 
 
 class EigsStats(ctypes.Structure):

@@ -75,6 +75,28 @@ __global__ void diag_neg_kernel(const double* __restrict__ theta, int off, int b
   if (e < b * b) C[e] = (e / b == e % b) ? -theta[off + e / b] : 0.0;
 }
 
+// Pinned host memory mapped into the device address space (the host-memory subspace tier).
+struct HostBuf {
+  void* h = nullptr;   // host address
+  void* d = nullptr;   // device address of the same memory
+  HostBuf() = default;
+  HostBuf(const HostBuf&) = delete;
+  HostBuf& operator=(const HostBuf&) = delete;
+  ~HostBuf() {
+    if (h) cudaFreeHost(h);
+  }
+  int alloc(size_t bytes) {
+    cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h = nullptr;
+      return set_error(FE_ERR_OOM, "cudaHostAlloc(%zu) for the host-memory subspace failed", bytes);
+    }
+    FE_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+    return FE_OK;
+  }
+};
+
 struct Phase {
   fe_csr h;
   int64_t n;
@@ -86,12 +108,15 @@ struct Phase {
   int max_restarts, max_sweeps;
   int pass1_f32 = 0;  // FP64 subspace: first Gram-Schmidt pass's Gram in FP32 arithmetic
   int op_ata = 0;  // 1: iterate with A^T A (SVD of a directed graph's matrix, Section 4.3.2)
+  int subspace_host = 0;  // 1: subspace blocks in mapped pinned host memory, newest block cached
   int stagnation_window = 0;  // > 0: stop when the worst wanted rho/scale has not halved
                               // over this many restarts (FP32 phase: at its precision floor
                               // the ratio only fluctuates)
   cudaStream_t s;
   // state
-  DevBuf vmem, hmem, small, xmem, ritzwork, opbuf;
+  DevBuf vmem, hmem, small, xmem, ritzwork, opbuf, cachemem;
+  HostBuf vhost;
+  void* cache[2] = {nullptr, nullptr};  // subspace_host: device copies (newest block, next)
   std::vector<void*> slot, spare, xblk, axblk;
   double *H = nullptr, *theta = nullptr, *Y = nullptr, *rho = nullptr, *anorm = nullptr,
          *Cdiag = nullptr, *gtmp = nullptr;
@@ -107,10 +132,20 @@ struct Phase {
     const size_t blk = (size_t)n * b * es;
     const int nx = (nev + b - 1) / b;
     const int nblocks = (NB + 1) + (NB - 1);
-    FE_TRY(vmem.alloc(blk * nblocks));
+    char* vbase;
+    if (subspace_host) {
+      FE_TRY(vhost.alloc(blk * nblocks));
+      vbase = static_cast<char*>(vhost.d);
+      FE_TRY(cachemem.alloc(blk * 2));
+      cache[0] = cachemem.p;
+      cache[1] = (char*)cachemem.p + blk;
+    } else {
+      FE_TRY(vmem.alloc(blk * nblocks));
+      vbase = static_cast<char*>(vmem.p);
+    }
     FE_TRY(xmem.alloc(blk * 2 * nx));
-    for (int i = 0; i <= NB; ++i) slot.push_back((char*)vmem.p + blk * i);
-    for (int i = 0; i < NB - 1; ++i) spare.push_back((char*)vmem.p + blk * (NB + 1 + i));
+    for (int i = 0; i <= NB; ++i) slot.push_back(vbase + blk * i);
+    for (int i = 0; i < NB - 1; ++i) spare.push_back(vbase + blk * (NB + 1 + i));
     for (int i = 0; i < nx; ++i) xblk.push_back((char*)xmem.p + blk * i);
     for (int i = 0; i < nx; ++i) axblk.push_back((char*)xmem.p + blk * (nx + i));
     FE_TRY(hmem.alloc(sizeof(double) * (size_t)(m + b) * m));
@@ -147,16 +182,27 @@ struct Phase {
     // the start block's column norms seed the ||A|| scale (update_anorm = 1)
     FE_TRY(orth_ex(none, n, slot[0], b, dt, anorm, 1, seed, &rng_counter, nullptr, b, gtmp, b,
                    &replacements, s, pass1_f32));
+    if (subspace_host)
+      FE_CUDA(cudaMemcpyAsync(cache[0], slot[0], (size_t)n * b * dt_size(dt), cudaMemcpyDefault, s));
     return FE_OK;
   }
 
+  // Host-memory subspace: the SpMM reads the device copy of the newest block (cache[0]) and
+  // writes the next block into cache[1], which is orthogonalised in device memory against the
+  // host-resident blocks and then copied out to its slot; the two caches then swap roles.
   int expand(int k) {
     for (int j = k / b; j < NB; ++j) {
-      FE_TRY(spmm_dispatch(slot[j], slot[j + 1]));
+      void* x = subspace_host ? cache[0] : slot[j];
+      void* w = subspace_host ? cache[1] : slot[j + 1];
+      FE_TRY(spmm_dispatch(x, w));
       ++spmm_blocks;
       BlockSet V = slots(0, j + 1);
-      FE_TRY(orth_ex(V, n, slot[j + 1], b, dt, anorm, 1, seed, &rng_counter, H + (size_t)j * b, m,
+      FE_TRY(orth_ex(V, n, w, b, dt, anorm, 1, seed, &rng_counter, H + (size_t)j * b, m,
                      H + (size_t)(j + 1) * b * m + (size_t)j * b, m, &replacements, s, pass1_f32));
+      if (subspace_host) {
+        FE_CUDA(cudaMemcpyAsync(slot[j + 1], w, (size_t)n * b * dt_size(dt), cudaMemcpyDefault, s));
+        std::swap(cache[0], cache[1]);
+      }
     }
     return FE_OK;
   }
@@ -398,6 +444,7 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
   p1.max_sweeps = o.max_sweeps;
   p1.pass1_f32 = o.orth_pass1 == 0;
   p1.op_ata = op_ata;
+  p1.subspace_host = o.subspace_host != 0;
   p1.s = s;
   int rc;
   double secs32 = 0.0;
@@ -461,6 +508,7 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
     p2.max_sweeps = o.max_sweeps;
     p2.pass1_f32 = o.orth_pass1 == 0;
     p2.op_ata = op_ata;
+    p2.subspace_host = o.subspace_host != 0;
     p2.s = s;
     p2.tol = tol;
     p2.dt = FE_F64;

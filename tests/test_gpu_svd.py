@@ -146,3 +146,13 @@ def test_svds_vectors_optional_and_learned_start_rejected():
         rc = lib.fe_svds(h.handle, 4, 2, 8, 1e-8, ctypes.byref(o),
                          out.ctypes.data_as(ctypes.c_void_p), None, None, None)
         assert rc == _lib.FE_ERR_INVALID
+
+
+def test_svds_host_memory_subspace_same_results():
+    g = graphgen.rmat(12, seed=3, directed=True)
+    with fe.Csr.from_graph(g) as h:
+        sv_d, V_d, U_d, st_d = fe.svds(h, 8, 2, 16, 1e-8, seed=1)
+        sv_h, V_h, U_h, st_h = fe.svds(h, 8, 2, 16, 1e-8, seed=1, subspace="host")
+    assert st_h["converged"] and np.array_equal(sv_h, sv_d)
+    assert np.array_equal(V_h.cpu().numpy(), V_d.cpu().numpy())
+    assert np.array_equal(U_h.cpu().numpy(), U_d.cpu().numpy())
