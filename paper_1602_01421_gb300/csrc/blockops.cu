@@ -64,22 +64,6 @@ __device__ __forceinline__ void load_vrow(const T* __restrict__ base, int ld, in
   }
 }
 
-// FP64 -> FP32 by truncating the significand (IEEE 754 binary64 -> binary32 field by field:
-// sign, exponent rebiased from 1023 to 127, top 23 of the 52 fraction bits), on the integer
-// units so that the FP64 pipe is not touched.  Relative error below 2^-23; magnitudes below
-// 2^-126 become signed zero, above the binary32 range infinity.
-__device__ __forceinline__ float f64_to_f32_trunc(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  unsigned bits = sign | ((unsigned)e << 23) | frac;
-  if (e <= 0) bits = sign;
-  if (e >= 255) bits = sign | 0x7f800000u;
-  return __uint_as_float(bits);
-}
-
 // ---------------------------------------------------------------- gram
 // Rows [r, r + rows) of tile (j, q0) of V_j^T W from the staged W rows sW (lane = row, four
 // row loads in flight per lane when the block is narrow).  Products and sums in TC (T, or

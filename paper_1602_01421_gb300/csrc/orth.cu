@@ -19,9 +19,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fe_internal.cuh"
+#include "vec.cuh"
 
 namespace fe {
 
@@ -148,6 +150,73 @@ __global__ void orth_post3_kernel(const double* __restrict__ S2, int b,
     Rout[p * ldr + q] = r;
     M[e] = Ri[e];
   }
+  if (tid == 0) {  // status[2]: R2^{-1} is the identity up to kSmallCorrection
+    double dmax = 0.0;
+    for (int e = 0; e < b * b; ++e) dmax = fmax(dmax, fabs(Ri[e] - (e / b == e % b ? 1.0 : 0.0)));
+    status[2] = dmax <= kSmallCorrection ? 1 : 0;
+  }
+}
+
+// W <- W M for the second CholeskyQR pass (M = R2^{-1}), skipped after a failed check.  After
+// an FP64 first pass M is the identity to about 1e-15; when allow32 and status[2] say every
+// |M - I| entry is at most kSmallCorrection, the product is taken as W + W (M - I) with the
+// correction in FP32 arithmetic (W converted by integer truncation), far below FP64 rounding of W.
+template <typename T, int B>
+__global__ void __launch_bounds__(256) right_mult_kernel(T* __restrict__ W, int64_t n,
+                                                         const double* __restrict__ M,
+                                                         const int* __restrict__ status, int allow32) {
+  if (status[0]) return;
+  __shared__ T sM[B * B];
+  __shared__ float sD[B * B];
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    sM[e] = (T)M[e];
+    sD[e] = (float)(M[e] - (e / B == e % B ? 1.0 : 0.0));
+  }
+  __syncthreads();
+  const bool small = sizeof(T) == 8 && allow32 && status[2] != 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    T w[B], out[B];
+    ld_row_rw<T, B>(W + r * B, w);
+    if (small) {
+      float wf[B];
+#pragma unroll
+      for (int p = 0; p < B; ++p) wf[p] = f64_to_f32_trunc((double)w[p]);
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        float c = 0.f;
+#pragma unroll
+        for (int p = 0; p < B; ++p) c = fmaf(wf[p], sD[p * B + q], c);
+        out[q] = w[q] + (T)c;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        T x = T(0);
+#pragma unroll
+        for (int p = 0; p < B; ++p) x = fma(w[p], sM[p * B + q], x);
+        out[q] = x;
+      }
+    }
+    st_row<T, B>(W + r * B, out);
+  }
+}
+
+template <typename T>
+static int launch_right_mult(T* W, int64_t n, int b, const double* M, const int* status,
+                             int allow32, cudaStream_t s) {
+  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * num_sms()));
+  switch (b) {
+    case 1: right_mult_kernel<T, 1><<<ctas, 256, 0, s>>>(W, n, M, status, allow32); break;
+    case 2: right_mult_kernel<T, 2><<<ctas, 256, 0, s>>>(W, n, M, status, allow32); break;
+    case 4: right_mult_kernel<T, 4><<<ctas, 256, 0, s>>>(W, n, M, status, allow32); break;
+    case 8: right_mult_kernel<T, 8><<<ctas, 256, 0, s>>>(W, n, M, status, allow32); break;
+    case 16: right_mult_kernel<T, 16><<<ctas, 256, 0, s>>>(W, n, M, status, allow32); break;
+    default: return set_error(FE_ERR_INVALID, "orth: b = %d", b);
+  }
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
 }
 
 __global__ void add_col_kernel(double* __restrict__ dst, int ld, int col,
@@ -277,7 +346,7 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   if (!sG1 || !sG2 || !sM || !sC || !sRacc || !sS2 || !sStat || !gdummy) return FE_ERR_OOM;
   int* status = reinterpret_cast<int*>(sStat);
   if (!d_G) d_G = gdummy;  // k == 0: nothing is written to G
-  FE_CUDA(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
+  FE_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), s));
   std::vector<const void*> vx(V.blk, V.blk + V.nv);
   vx.push_back(W);
   BlockSet Vx = blockset_of(vx, b, b);
@@ -319,8 +388,9 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   orth_post3_kernel<<<1, 64, 0, s>>>(sS2, b, sRacc, sM, d_R, ldr, status);
   count_launch();
   FE_CUDA(cudaGetLastError());
-  BlockSet none = blockset_of({}, b, b);
-  FE_TRY(update_skip(none, n, nullptr, 0.0, 1.0, sM, W, b, b, dt, status, s));
+  const int allow32 = (pass1_f32 && dt == FE_F64) ? 1 : 0;
+  if (dt == FE_F64) FE_TRY(launch_right_mult(static_cast<double*>(W), n, b, sM, status, allow32, s));
+  else FE_TRY(launch_right_mult(static_cast<float*>(W), n, b, sM, status, 0, s));
   int st = 0;
   double an = 0.0;
   FE_CUDA(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
