@@ -86,7 +86,8 @@ typedef struct {
    * (O(nnz log deg) on the host).  Default 0. */
   int check_symmetric;
   /* Rows with degree <= tail_max (at most 128) go to the degree-sorted slice format, one row
-   * per lane (0 = default 128);
+   * per lane (0 = default: 128; 16 for packed plans; semi-external handles with a small cap
+   * may go lower to bound the slices' padding);
    * rows with degree > hub_min are split into chunks of hub_chunk non-zeros
    * (0 = defaults 4096 / 4096).  Tuning knobs only; results do not depend on them beyond
    * floating-point summation order. */
@@ -144,9 +145,11 @@ typedef struct {
  * entry is 1, as for the adjacency matrix of a graph).  rowptr (n+1 int64) and colidx
  * (nnz = rowptr[n] int32) are HOST pointers and are copied; the caller may free them when
  * the call returns.  n >= 1, 0 <= nnz.  Duplicate entries count twice (A_ij = multiplicity).
- * The eigensolver assumes A symmetric (the adjacency matrix of an undirected graph).
+ * fe_eigs assumes A symmetric (the adjacency matrix of an undirected graph); fe_svds takes
+ * any A (a directed graph) through A^T A.  Column indices need not be sorted within a row.
  * Errors: FE_ERR_INVALID (null pointers, n < 1, malformed rowptr, column out of range,
- * asymmetric pattern when check_symmetric), FE_ERR_OOM, FE_ERR_CUDA.  Synchronous.
+ * asymmetric pattern when check_symmetric, bad index_format), FE_ERR_OOM, FE_ERR_CUDA.
+ * Synchronous.
  */
 int fe_csr_create(int64_t n, const int64_t* rowptr, const int32_t* colidx, fe_csr* out);
 int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
@@ -159,8 +162,10 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info);
  * SpMM, Section 3.3.3: Y = A X, i.e. Y[i, :] = sum over the non-zeros (i, j) of X[j, :].
  * X and Y are DEVICE pointers to row-major n x b blocks of type dt, 1 <= b <= 16,
  * b in {1, 2, 4, 8, 16}; Y is overwritten (rows of empty matrix rows become 0); X and Y must
- * not overlap.  Accumulation is in dt (FP32 sums are ordered as short per-lane sums combined
- * by a tree, so the error stays near log2(degree) ulps of sum |X|).  Both pointers must be
+ * not overlap.  Accumulation is in dt.  Rows of degree <= tail_max are summed in order by
+ * one lane (worst-case FP32 error (degree - 1) * 2^-24 * sum |X|, about sqrt(degree) * 2^-24
+ * for inputs of random sign; tail_max = 16 keeps the worst case below 1e-6 * sum |X|); longer
+ * rows as short per-lane sums combined by a tree (error near log2(degree) ulps).  Both pointers must be
  * 16-byte aligned.  Errors: FE_ERR_INVALID (null/unaligned pointer, unsupported b),
  * FE_ERR_CUDA, FE_ERR_TIMEOUT (semi-external copy wait).  Asynchronous when resident.
  */
