@@ -80,7 +80,8 @@ typedef struct {
    * semi-external SpMM (Section 3.3) with host memory in place of SSDs. */
   int64_t device_mem_cap_bytes;
   /* 1 = check that rowptr is monotone with rowptr[0] == 0 and every column index lies in
-   * [0, n) (O(n + nnz) on the host).  Default 1. */
+   * [0, n) (O(n + nnz) on the host).  Default 1.  0 skips the check, and the caller then
+   * guarantees it: the SpMM kernels gather X rows at the stored indices without bounds checks. */
   int validate;
   /* 1 = additionally check that the pattern is symmetric and free of self-loops
    * (O(nnz log deg) on the host).  Default 0. */
