@@ -7,12 +7,12 @@ This package generates inputs only and holds none of the method's arithmetic:
   * graphs with closed-form spectra (cycle, complete, star, hypercube, disjoint unions);
   * directed graphs (directed R-MAT and families with closed-form singular values) for the
     SVD path;
-  * seeded N(0, 1) dense blocks.
+  * seeded N(0, 1) and U[0, 1) dense blocks.
 """
 from .graphs import (CSR, rmat, cycle, complete, star, hypercube, path, erdos_renyi,
-                     disjoint_union, from_edges, normal_block, build, directed_cycle, out_star,
+                     disjoint_union, from_edges, normal_block, uniform_block, build, directed_cycle, out_star,
                      transitive_tournament, complete_bipartite_directed)
 
 __all__ = ["CSR", "rmat", "cycle", "complete", "star", "hypercube", "path", "erdos_renyi",
-           "disjoint_union", "from_edges", "normal_block", "build", "directed_cycle", "out_star",
+           "disjoint_union", "from_edges", "normal_block", "uniform_block", "build", "directed_cycle", "out_star",
            "transitive_tournament", "complete_bipartite_directed"]

@@ -178,6 +178,11 @@ def normal_block(n: int, b: int, seed: int, dtype=np.float64) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal((n, b)).astype(dtype)
 
 
+def uniform_block(n: int, b: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Seeded U[0,1) row-major n x b block (numpy PCG64)."""
+    return np.random.default_rng(seed).random((n, b)).astype(dtype)
+
+
 # ---- directed graphs (inputs of the SVD path)
 
 def directed_cycle(n: int) -> CSR:

@@ -163,11 +163,16 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info);
  * SpMM, Section 3.3.3: Y = A X, i.e. Y[i, :] = sum over the non-zeros (i, j) of X[j, :].
  * X and Y are DEVICE pointers to row-major n x b blocks of type dt, 1 <= b <= 16,
  * b in {1, 2, 4, 8, 16}; Y is overwritten (rows of empty matrix rows become 0); X and Y must
- * not overlap.  Accumulation is in dt.  Rows of degree <= tail_max are summed in order by
- * one lane (worst-case FP32 error (degree - 1) * 2^-24 * sum |X|, about sqrt(degree) * 2^-24
- * for inputs of random sign; tail_max = 16 keeps the worst case below 1e-6 * sum |X|); longer
- * rows as short per-lane sums combined by a tree (error near log2(degree) ulps).  Both pointers must be
- * 16-byte aligned.  Errors: FE_ERR_INVALID (null/unaligned pointer, unsupported b),
+ * not overlap.  Accumulation is in dt.  Accuracy, per entry, against the exact sum of the
+ * given X values, for any degree and any signs ((A|X|)_ij = sum over the row of |X[j, :]|):
+ *   FP32: every lane's running sum is compensated (Kahan), lanes' sums are combined by a tree
+ *         of at most 5 levels, and the chunks of a split hub row are added in compensated
+ *         FP64 and rounded once, so |error| <= 9 * 2^-24 * (A|X|)_ij (about 5.4e-7, plus
+ *         terms of order degree * 2^-48);
+ *   FP64: plain sums, |error| <= (m + 6) * 2^-53 * (A|X|)_ij, m the longest run one lane adds:
+ *         m <= tail_max for rows in the slices, m <= 512 for longer rows when X is 32-byte
+ *         aligned (1024 when it is only 16-byte aligned and b = 16), so below 6e-14 (1.2e-13).
+ * Both pointers must be 16-byte aligned.  Errors: FE_ERR_INVALID (null/unaligned pointer, unsupported b),
  * FE_ERR_CUDA, FE_ERR_TIMEOUT (semi-external copy wait).  Asynchronous when resident.
  */
 int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);

@@ -57,16 +57,53 @@ void DevBuf::release() {
 }
 
 int num_sms() {
-  static int sms[64] = {0};
+  static std::atomic<int> sms[kMaxDevices];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!sms[dev]) {
-    int v = 0;
+  if (dev < 0 || dev >= kMaxDevices) dev = 0;
+  int v = sms[dev].load(std::memory_order_relaxed);
+  if (!v) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    sms[dev] = v > 0 ? v : 1;
+    v = v > 0 ? v : 1;
+    sms[dev].store(v, std::memory_order_relaxed);
   }
-  return sms[dev];
+  return v;
+}
+
+int cur_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(FE_ERR_INVALID, "device ordinal %d beyond the library's %d", dev, kMaxDevices);
+  return dev;
+}
+
+int kernel_configure(KernelSetup& ks, const void* func, int max_smem) {
+  const int dev = cur_device();
+  if (dev < 0) return dev;
+  std::lock_guard<std::mutex> lock(ks.mu);
+  if (!ks.configured[dev]) {
+    FE_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    ks.configured[dev] = true;
+  }
+  return FE_OK;
+}
+
+int kernel_occupancy(KernelSetup& ks, const void* func, int threads, size_t smem, int slot,
+                     int* per_sm) {
+  const int dev = cur_device();
+  if (dev < 0) return dev;
+  FE_ARG(slot >= 0 && slot < kSetupSlots, "internal: launch-shape slot %d", slot);
+  std::lock_guard<std::mutex> lock(ks.mu);
+  if (ks.per_sm[dev][slot] == 0 || smem > ks.per_sm_smem[dev][slot]) {
+    int nb = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem));
+    ks.per_sm[dev][slot] = std::max(nb, 1);
+    ks.per_sm_smem[dev][slot] = smem;
+  }
+  *per_sm = ks.per_sm[dev][slot];
+  return FE_OK;
 }
 
 BlockSet make_blockset(const void* base, int nv, int bv, int ld, int64_t bstride, fe_dtype dt) {

@@ -30,17 +30,21 @@ constexpr int kScratchSlots = 32;
 struct ScratchPool {
   DevBuf bufs[kScratchSlots];
 };
-static thread_local ScratchPool* t_pool = nullptr;
-static thread_local int t_pool_dev = -1;
-
-static ScratchPool& pool() {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (!t_pool || t_pool_dev != dev) {
-    t_pool = new ScratchPool();  // per thread and device; lives until exit
-    t_pool_dev = dev;
+// One pool per (host thread, device), created on first use and kept until the thread exits,
+// so a thread that switches devices keeps every device's buffers instead of reallocating them.
+struct ThreadPools {
+  ScratchPool* p[kMaxDevices] = {};
+  ~ThreadPools() {
+    for (ScratchPool* q : p) delete q;
   }
-  return *t_pool;
+};
+static thread_local ThreadPools t_pools;
+
+static ScratchPool* pool() {
+  const int dev = cur_device();
+  if (dev < 0) return nullptr;
+  if (!t_pools.p[dev]) t_pools.p[dev] = new ScratchPool();
+  return t_pools.p[dev];
 }
 
 double* small_scratch(int slot, size_t count) {
@@ -48,7 +52,9 @@ double* small_scratch(int slot, size_t count) {
     set_error(FE_ERR_INVALID, "internal: scratch slot %d out of range", slot);
     return nullptr;
   }
-  DevBuf& b = pool().bufs[slot];
+  ScratchPool* pl = pool();
+  if (!pl) return nullptr;
+  DevBuf& b = pl->bufs[slot];
   if (b.alloc(count * sizeof(double)) != FE_OK) return nullptr;
   return b.as<double>();
 }
@@ -217,19 +223,11 @@ static int launch_gram_tpw(const BlockSet& V, int64_t n, const T* W, int bw, int
   R = std::max(32, R - R % 32);
   const size_t smem = (((size_t)R * bw * sizeof(TC) + 15) & ~(size_t)15) + (size_t)nout * sizeof(double);
   FE_ARG(smem <= 200 * 1024, "gram: output too large (%d entries)", nout);
-  static int per_sm = 0;  // per instantiation (and per smem size class; re-queried when it grows)
-  static size_t per_sm_smem = 0;
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(gram_kernel<T, BV, NQ, TPW, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
-  if (per_sm == 0 || smem > per_sm_smem) {
-    int nb = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gram_kernel<T, BV, NQ, TPW, TC>, 256, smem));
-    per_sm = std::max(nb, 1);
-    per_sm_smem = smem;
-  }
+  static KernelSetup ks;
+  const void* fn = reinterpret_cast<const void*>(gram_kernel<T, BV, NQ, TPW, TC>);
+  FE_TRY(kernel_configure(ks, fn, 200 * 1024));
+  int per_sm = 0;
+  FE_TRY(kernel_occupancy(ks, fn, 256, smem, 0, &per_sm));
   int64_t nctas = std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm * num_sms());
   nctas = std::max<int64_t>(nctas, 1);
   double* part = scratch;
@@ -391,11 +389,8 @@ static int launch_update(const BlockSet& V, int64_t n, const double* C, double a
                          const double* M, T* W, int ldw, const int* skip, cudaStream_t s) {
   const size_t smem = ((size_t)V.nv * BV * BW + (size_t)BW * BW) * sizeof(T);
   FE_ARG(smem <= 200 * 1024, "update: coefficient matrix too large");
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(update_kernel<T, BV, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
+  static KernelSetup ks;
+  FE_TRY(kernel_configure(ks, reinterpret_cast<const void*>(update_kernel<T, BV, BW>), 200 * 1024));
   int ctas = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
   ctas = std::max(ctas, 1);
   update_kernel<T, BV, BW><<<ctas, 256, smem, s>>>(V, C, alpha, beta, M, W, ldw, n, skip);
@@ -510,11 +505,8 @@ static int launch_combine(const BlockSet& V, int64_t n, const double* Y, int ldy
   constexpr int OB = BV <= 4 ? 8 : (BV == 8 ? 4 : 2);
   const size_t smem = (size_t)V.nv * BV * Out.nv * BV * sizeof(T);
   FE_ARG(smem <= 200 * 1024, "combine: coefficient matrix too large");
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(combine_kernel<T, BV, OB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
+  static KernelSetup ks;
+  FE_TRY(kernel_configure(ks, reinterpret_cast<const void*>(combine_kernel<T, BV, OB>), 200 * 1024));
   int ctas = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
   ctas = std::max(ctas, 1);
   combine_kernel<T, BV, OB><<<ctas, 256, smem, s>>>(V, Y, ldy, Out, n);
@@ -910,22 +902,14 @@ static int launch_update_gram_tpw(const BlockSet& V, int64_t n, const double* C,
   const size_t smem = ((((size_t)k * BW + BW * BW + 2 * (size_t)R * BW) * sizeof(T) + 15) & ~(size_t)15) +
                       (size_t)nout * sizeof(double) + (vc32 ? (size_t)k * BW * sizeof(float) : 0);
   FE_ARG(smem <= 200 * 1024, "update_gram: coefficient matrix too large");
-  static bool configured = false;
-  static int per_sm[17] = {0};  // by warps per block
-  static size_t per_sm_smem[17] = {0};
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(update_gram_kernel<T, BV, BW, TPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
-  const int wq = threads / 32;
+  static KernelSetup ks;
+  const void* fn = reinterpret_cast<const void*>(update_gram_kernel<T, BV, BW, TPW>);
+  FE_TRY(kernel_configure(ks, fn, 200 * 1024));
+  const int wq = threads / 32;  // launch shape: warps per block
   FE_ARG(threads % 32 == 0 && wq >= 8 && wq <= 16, "update_gram: %d threads", threads);
-  if (per_sm[wq] == 0 || smem > per_sm_smem[wq]) {
-    int nb = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_gram_kernel<T, BV, BW, TPW>, threads, smem));
-    per_sm[wq] = std::max(nb, 1);
-    per_sm_smem[wq] = smem;
-  }
-  int nctas = (int)std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm[wq] * num_sms());
+  int per_sm = 0;
+  FE_TRY(kernel_occupancy(ks, fn, threads, smem, wq, &per_sm));
+  int nctas = (int)std::min<int64_t>(ceil_div(n, R), (int64_t)per_sm * num_sms());
   nctas = std::max(nctas, 1);
   double* part = small_scratch(0, (size_t)nctas * nout);
   if (!part) return FE_ERR_OOM;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <mutex>
 #include <vector>
 
 #include "fe.h"
@@ -44,7 +45,24 @@ struct DevBuf {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline bool is_pow2_le16(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16; }
-int num_sms();
+int num_sms();  // SMs of the current device
+
+// Per-device launch set-up of one kernel, shared by every host thread.  The dynamic shared-
+// memory limit is raised once on each device that launches the kernel; blocks per SM are cached
+// per device and per launch shape (slot < kSetupSlots) and re-queried when a launch needs more
+// shared memory than the cached figure was taken for.  One static KernelSetup per kernel.
+constexpr int kMaxDevices = 64;
+constexpr int kSetupSlots = 17;
+struct KernelSetup {
+  std::mutex mu;
+  bool configured[kMaxDevices] = {};
+  int per_sm[kMaxDevices][kSetupSlots] = {};
+  size_t per_sm_smem[kMaxDevices][kSetupSlots] = {};
+};
+int cur_device();  // the current device's ordinal (FE_ERR_INVALID beyond kMaxDevices: < 0)
+int kernel_configure(KernelSetup& ks, const void* func, int max_smem);
+int kernel_occupancy(KernelSetup& ks, const void* func, int threads, size_t smem, int slot,
+                     int* per_sm);
 
 // ---------------------------------------------------------------- block descriptors
 // A set of nv tall blocks; block j is n x bv with row stride ld (elements), starting at

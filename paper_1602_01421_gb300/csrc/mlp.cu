@@ -557,11 +557,8 @@ static int loss_grad_hb(const float* F, int64_t n, const float* params, const fl
   count_launch();
   const size_t smem = sizeof(float) * S::TOTAL;
   FE_ARG(smem <= 220 * 1024, "mlp: hidden/b too large for the gradient kernel");
-  static bool configured = false;
-  if (!configured) {
-    FE_CUDA(cudaFuncSetAttribute(mlp_grad_kernel<H, B, TT, SPAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = true;
-  }
+  static KernelSetup ks;
+  FE_TRY(kernel_configure(ks, reinterpret_cast<const void*>(mlp_grad_kernel<H, B, TT, SPAN>), (int)smem));
   mlp_grad_kernel<H, B, TT, SPAN><<<gctas, kTR, smem, s>>>(F, n, params, U, coef, gpart);
   count_launch();
   grad_reduce_kernel<<<(unsigned)ceil_div(P::COUNT, 256), 256, 0, s>>>(gpart, gctas, P::COUNT, grad);

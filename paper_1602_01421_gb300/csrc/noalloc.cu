@@ -16,7 +16,6 @@ constexpr size_t kNoAllocScratchDoubles = 262144;
 constexpr int kNoAllocMaxOutputs = 2048;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
-constexpr int kMaxDevices = 64;
 static double* g_noalloc_addr[kMaxDevices];  // device address of the array, per device
 static std::mutex g_noalloc_mu;
 

@@ -344,12 +344,10 @@ int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double
   FE_ARG(smem <= 225 * 1024, "ritz: subspace m = %d too large", m);
   const bool big = m > kRitzSmallMax;
   FE_ARG(!big || work != nullptr, "ritz: m = %d needs a global workspace", m);
-  static bool configured[2] = {false, false};
-  if (!configured[big]) {
-    FE_CUDA(cudaFuncSetAttribute(big ? ritz_kernel<true> : ritz_kernel<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
-    configured[big] = true;
-  }
+  static KernelSetup ks[2];
+  FE_TRY(kernel_configure(ks[big], big ? reinterpret_cast<const void*>(ritz_kernel<true>)
+                                       : reinterpret_cast<const void*>(ritz_kernel<false>),
+                          225 * 1024));
   // one CTA: a rotation step is (m/2)^2 / 2 2 x 2 blocks plus m^2 / 2 Q updates between two
   // barriers; FP64 work on one SM runs at 2 DFMA per clock, hence the FP32 sweeps first
   if (big)

@@ -20,6 +20,9 @@
 // processing-time list; tail slices follow in the same launch.  The task rows' column
 // indices are stored either as int32 or, in the packed format, as per-task gap fields that a
 // warp decodes with a prefix sum (fewer bytes to stream from host memory).
+// FP32 sums are compensated per lane (Kahan) before the lane tree, and hub chunks are added in
+// compensated FP64, so the FP32 error bound (9 * 2^-24 * A|X| per entry) does not grow with the
+// degree or depend on the signs of X.
 #include <stdio.h>
 #include <string.h>
 
@@ -68,6 +71,23 @@ struct SpmmParams {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
 
+// Per-lane running sums.  FP32: Kahan's compensated summation (Kahan 1965; Higham, "Accuracy
+// and Stability of Numerical Algorithms", 2nd ed., Thm. 4.8): c carries the rounding error of
+// the last addition, so a lane's sum of m terms is within (2u + O(m u^2)) sum |x| of the exact
+// sum (u = 2^-24), whatever the number of terms and their signs, instead of (m - 1) u sum |x|.
+// Four FP32 adds per term; nvcc does not reassociate floating-point adds, so the correction
+// survives compilation.  FP64: plain adds (m u with u = 2^-53 is already far below the FP64
+// bound).  kahan_add(s, c, x) adds x; kahan_value(s, c) is the compensated sum.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+__device__ __forceinline__ void kahan_add(double& s, double&, double x) { s += x; }
+__device__ __forceinline__ float kahan_value(float s, float c) { return s - c; }
+__device__ __forceinline__ double kahan_value(double s, double) { return s; }
+
 template <typename T, int B, bool V32, bool PACKED>
 __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const T* __restrict__ X,
                                          T* __restrict__ Y, T* __restrict__ partial, int lane) {
@@ -91,9 +111,9 @@ __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const 
   }
   const int chunk = lane % G::C;
   const int slot = lane / G::C;
-  T acc[G::NE];
+  T acc[G::NE], cmp[G::NE];
 #pragma unroll
-  for (int e = 0; e < G::NE; ++e) acc[e] = T(0);
+  for (int e = 0; e < G::NE; ++e) acc[e] = cmp[e] = T(0);
   const int32_t* __restrict__ ci = p.colidx + start;
   const uint32_t* __restrict__ tb = p.tbits + start;
   const uint32_t wmask = (1u << w) - 1u;  // 1 <= w <= 31
@@ -138,12 +158,14 @@ __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const 
             T f[G::NE];
             ld_frag<T, G::NE>(X + (int64_t)col * B + chunk * G::NE, f);
 #pragma unroll
-            for (int e = 0; e < G::NE; ++e) acc[e] += f[e];
+            for (int e = 0; e < G::NE; ++e) kahan_add(acc[e], cmp[e], f[e]);
           }
         }
       }
     }
   }
+#pragma unroll
+  for (int e = 0; e < G::NE; ++e) acc[e] = kahan_value(acc[e], cmp[e]);
   // Sum the P slot partials of each chunk.  The first LNE butterfly levels (offsets 16, 8, ..)
   // also scatter the NE elements -- a lane keeps half of what it holds and adds its partner's
   // copy of that half -- so every level after them adds one value per lane.
@@ -184,9 +206,9 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
   const int deg = p.bucket_deg[bkt];
   const int64_t off = p.bucket_ell_base[bkt] + (si - p.bucket_slice_begin[bkt]) * 32 * (int64_t)deg;
   const int row = __ldcs(p.slice_rows + si * 32 + lane);
-  T acc[B];
+  T acc[B], cmp[B];
 #pragma unroll
-  for (int e = 0; e < B; ++e) acc[e] = T(0);
+  for (int e = 0; e < B; ++e) acc[e] = cmp[e] = T(0);
   const int32_t* __restrict__ e = p.ell + off + lane;
   int t = 0;
   for (; t + 4 <= deg; t += 4) {
@@ -200,7 +222,7 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
         T f[G::NE];
         ld_frag<T, G::NE>(X + (int64_t)c[u] * B + ch * G::NE, f);
 #pragma unroll
-        for (int q = 0; q < G::NE; ++q) acc[ch * G::NE + q] += f[q];
+        for (int q = 0; q < G::NE; ++q) kahan_add(acc[ch * G::NE + q], cmp[ch * G::NE + q], f[q]);
       }
   }
   for (; t < deg; ++t) {
@@ -210,9 +232,11 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
       T f[G::NE];
       ld_frag<T, G::NE>(X + (int64_t)c * B + ch * G::NE, f);
 #pragma unroll
-      for (int q = 0; q < G::NE; ++q) acc[ch * G::NE + q] += f[q];
+      for (int q = 0; q < G::NE; ++q) kahan_add(acc[ch * G::NE + q], cmp[ch * G::NE + q], f[q]);
     }
   }
+#pragma unroll
+  for (int q = 0; q < B; ++q) acc[q] = kahan_value(acc[q], cmp[q]);
   if (row >= 0) {
     using F = FragOf<T, B>;  // stores in 16-byte pieces
 #pragma unroll
@@ -233,7 +257,10 @@ __global__ void __launch_bounds__(256) spmm_main_kernel(const SpmmParams p, cons
   }
 }
 
-// Y[hub_rows[h]] = sum of the hub's task partials in task order.
+// Y[hub_rows[h]] = sum of the hub's task partials in task order, in FP64 with Neumaier's
+// compensation (Neumaier 1974: the TwoSum error of every add is collected separately), then
+// one rounding to T: the partials add with an error of at most 2^-53 |sum| + O(k 2^-106) sum
+// |partial| whatever their number k, so a hub adds one rounding of T to its chunks' errors.
 template <typename T, int B>
 __global__ void hub_reduce_kernel(const int32_t* __restrict__ hub_rows,
                                   const int32_t* __restrict__ hub_task_begin, int64_t nhub,
@@ -242,9 +269,14 @@ __global__ void hub_reduce_kernel(const int32_t* __restrict__ hub_rows,
   if (i >= nhub * B) return;
   const int64_t h = i / B;
   const int c = (int)(i % B);
-  T s = T(0);
-  for (int t = hub_task_begin[h]; t < hub_task_begin[h + 1]; ++t) s += partial[(int64_t)t * B + c];
-  Y[(int64_t)hub_rows[h] * B + c] = s;
+  double s = 0.0, e = 0.0;
+  for (int t = hub_task_begin[h]; t < hub_task_begin[h + 1]; ++t) {
+    const double x = (double)partial[(int64_t)t * B + c];
+    const double u = s + x;
+    e += fabs(s) >= fabs(x) ? (s - u) + x : (x - u) + s;
+    s = u;
+  }
+  Y[(int64_t)hub_rows[h] * B + c] = (T)(s + e);
 }
 
 template <typename T, int B>

@@ -2,7 +2,9 @@
 
 Tolerances (the SpMM accuracy requirement of 1e-6 relative, read per entry against A|X|, the condition
 number of a sum): FP64 |Y - Y*| <= 1e-13 (A|X|), FP32 <= 1e-6 (A|X|) with Y* the FP64 sum of
-the same FP32 inputs.  A 1 = degree must be exact in either precision.
+the same FP32 inputs.  A 1 = degree must be exact in either precision.  Inputs of one sign
+(where rounding errors of a plain in-order sum do not cancel) are checked against the FP32
+kernel's stated worst case, 9 * 2^-24 (A|X|).
 """
 import numpy as np
 import pytest
@@ -14,6 +16,36 @@ from tests.gpu_util import assert_spmm_close, to_dev, torch
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-6, "f64": 1e-13}
+# the FP32 kernel's worst case per entry (compensated lane sums, <= 5 tree levels, one rounding
+# of a split hub row's FP64 sum), in units of A|X|
+F32_BOUND = 9 * 2.0 ** -24
+# all-equal entries: a plain in-order FP32 sum of 127 (69) copies of this value is off by 1.47e-6
+# (1.05e-6) of the exact sum (found by scanning 20000 values in [1, 2) with numpy float32 sums)
+ADVERSARIAL_C = np.float32(1.9397392272949219)
+
+
+def one_signed_block(kind, n, b, seed):
+    """U[0,1), U[1,2) or the constant ADVERSARIAL_C, FP32, n x b."""
+    if kind == "const":
+        return np.full((n, b), ADVERSARIAL_C, dtype=np.float32)
+    lo = 0.0 if kind == "u01" else 1.0
+    return (lo + graphgen.uniform_block(n, b, seed=seed)).astype(np.float32)
+
+
+def plain_sum_error(g, X, rows):
+    """Largest |in-order FP32 sum - exact| / A|X| over `rows` (what a kernel summing each row
+    in order, uncompensated, would get) -- shows that an input can catch such a kernel."""
+    worst = 0.0
+    for i in rows:
+        cols = g.colidx[g.rowptr[i]:g.rowptr[i + 1]]
+        if len(cols) == 0:
+            continue
+        s = np.zeros(X.shape[1], dtype=np.float32)
+        for c in cols:
+            s = (s + X[c]).astype(np.float32)
+        exact = X[cols].astype(np.float64).sum(0)
+        worst = max(worst, float((np.abs(s - exact) / np.abs(X[cols]).astype(np.float64).sum(0)).max()))
+    return worst
 NP = {"f32": np.float32, "f64": np.float64}
 
 GRAPHS = {
@@ -22,6 +54,7 @@ GRAPHS = {
     "rmat13-noperm": lambda: graphgen.rmat(13, seed=2, permute=False),
     "star9000": lambda: graphgen.star(9000),              # one hub split into 3 chunks
     "complete70": lambda: graphgen.complete(70),          # all rows in one slice bucket (deg 69)
+    "complete128": lambda: graphgen.complete(128),        # slice rows of degree 127
     "complete300": lambda: graphgen.complete(300),        # all rows warp tasks (deg 299)
     "cycle1001": lambda: graphgen.cycle(1001),            # all rows tail (deg 2), ragged slice
     "er3000": lambda: graphgen.erdos_renyi(3000, 12.0, seed=5),
@@ -150,6 +183,28 @@ def test_spmm_unsorted_rows_and_duplicates(fmt):
             assert_spmm_close(gu, X, Y, TOL[prec])
 
 
+@pytest.mark.parametrize("kind", ["u01", "u12", "const"])
+@pytest.mark.parametrize("fmt", ["plain", "packed"])
+@pytest.mark.parametrize("b", [1, 4, 16])
+def test_spmm_f32_one_signed_inputs(graphs, kind, fmt, b):
+    """FP32 with inputs of one sign (the rounding errors of a plain in-order sum then add up
+    instead of cancelling): every entry within the stated worst case 9 * 2^-24 (A|X|), on
+    graphs whose rows reach every path (slices up to degree 128, warp tasks, split hubs)."""
+    for name in ("rmat14", "complete70", "complete128", "complete300", "star9000", "er3000"):
+        g = graphs[name]
+        X = one_signed_block(kind, g.n, b, seed=11 + b)
+        with fe.Csr.from_graph(g, index_format=fmt) as h:
+            Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+        ratio = assert_spmm_close(g, X, Y, F32_BOUND)
+        assert ratio <= F32_BOUND
+    if kind == "const" and fmt == "plain" and b == 1:
+        # the constant input catches an uncompensated kernel: plain in-order sums of the
+        # degree-69 and degree-127 rows of K70 and K128 miss the 1e-6 contract
+        for name in ("complete70", "complete128"):
+            g = graphs[name]
+            assert plain_sum_error(g, one_signed_block("const", g.n, 1, 0), range(4)) > TOL["f32"]
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_ones_give_degrees_exactly(graphs, prec):
     t = torch()
@@ -221,3 +276,21 @@ def test_spmm_full_size_sampled_rows(prec, b):
         ones = t.ones((g.n, b), dtype=t.float32 if prec == "f32" else t.float64, device="cuda")
         Yd = fe.spmm(h, ones)[:, 0].cpu().numpy()
     assert np.array_equal(Yd, deg.astype(Yd.dtype))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("fmt", ["plain", "packed"])
+@pytest.mark.parametrize("kind", ["u12", "const"])
+def test_spmm_f32_one_signed_full_size(fmt, kind):
+    """R-MAT scale 22, FP32 b in {1, 4, 16}, inputs of one sign: every row of degree 64..128
+    (the longest thread-per-row sums of the default plan; warp tasks in the packed plan), every
+    hub row and the 2000 highest-degree rows, within 9 * 2^-24 (A|X|)."""
+    g = graphgen.rmat(22, seed=1)
+    deg = g.degrees()
+    rows = np.unique(np.concatenate([np.nonzero((deg >= 64) & (deg <= 128))[0],
+                                     np.argsort(-deg)[:2000], np.nonzero(deg > 4096)[0]]))
+    with fe.Csr.from_graph(g, index_format=fmt) as h:
+        for b in (1, 4, 16):
+            X = one_signed_block(kind, g.n, b, seed=5 + b)
+            Y = fe.spmm(h, to_dev(X)).cpu().numpy()
+            assert assert_spmm_close(g, X, Y, F32_BOUND, rows=rows) <= F32_BOUND

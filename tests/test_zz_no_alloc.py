@@ -1,7 +1,8 @@
 """fe_block_gram_noalloc: the Gram product for callers that cannot allocate device memory
 (their device memory is reserved by their own allocator, or they must avoid calls that can
 synchronise the device).  Called through the C ABI and compared with fe_block_gram, the
-allocating entry point, on two calls in a row.  Collected last on purpose."""
+allocating entry point, on two calls in a row, and with the oracle's MvTransMv (Table 1).
+Collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -9,6 +10,7 @@ import pytest
 
 import graphgen
 import paper_1602_01421_gb300 as fe
+from oracle import blockops
 from tests.gpu_util import to_dev, torch
 
 pytestmark = pytest.mark.gpu
@@ -62,3 +64,40 @@ def test_noalloc_gram_rejects_oversized_output():
     G = t.zeros((256, 16), dtype=t.float64, device="cuda")
     assert _noalloc(lib, V, W, 1.0, G) == -1
     assert b"2048" in lib.fe_last_error()
+
+
+def _oracle_check(V, W, alpha, G, tol):
+    """G against the oracle's MvTransMv on the same inputs, per entry within
+    tol * alpha * (|V|^T |W|)."""
+    Vh = V.cpu().numpy().astype(np.float64)
+    Wh = W.cpu().numpy().astype(np.float64)
+    nv, n, bv = Vh.shape
+    AA = Vh.transpose(1, 0, 2).reshape(n, nv * bv)   # column j*bv + p = block j's column p
+    ref = blockops.mv_trans_mv(alpha, AA, Wh)
+    bound = tol * abs(alpha) * (np.abs(AA).T @ np.abs(Wh))
+    err = np.abs(G.cpu().numpy() - ref)
+    assert (err <= bound).all(), f"max err {err.max():.3e}"
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("shape", [(8, 16, 16), (4, 16, 2), (32, 2, 16), (5, 1, 8)])
+def test_noalloc_gram_matches_oracle_at_and_below_the_size_limit(prec, shape):
+    """nv * bv * bw up to the 2048-entry limit: at the limit the static scratch holds 128 CTAs'
+    partials, so the grid is cut to fit it; bv != bw gives non-square output tiles.  Two calls
+    in a row on different inputs, each checked against the oracle and against fe_block_gram."""
+    t = torch()
+    lib = _lib()
+    fe._stream()
+    nv, bv, bw = shape
+    for call, n in enumerate([200003, 65537]):
+        V = to_dev(graphgen.normal_block(nv * n, bv, seed=40 + call, dtype=NP[prec]).reshape(nv, n, bv))
+        W = to_dev(graphgen.normal_block(n, bw, seed=50 + call, dtype=NP[prec]))
+        G = t.full((nv * bv, bw), float("nan"), dtype=t.float64, device="cuda")
+        assert _noalloc(lib, V, W, -1.5, G) == 0, lib.fe_last_error()
+        ref = fe.block_gram(V, W, alpha=-1.5)
+        t.cuda.synchronize()
+        assert t.isfinite(G).all(), f"call {call}"
+        _oracle_check(V, W, -1.5, G, TOL[prec])
+        absprod = 1.5 * (V.abs().to(t.float64).permute(0, 2, 1).reshape(nv * bv, n)
+                         @ W.abs().to(t.float64))
+        assert bool(((G - ref).abs() <= 2 * TOL[prec] * absprod).all()), f"call {call}"
