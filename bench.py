@@ -121,40 +121,76 @@ def dist_setup():
     return ws, rank, local
 
 
+def oracle_full_solves():
+    """Full oracle solves of the benchmark graphs (block SpMM counts, restarts, time), written by
+    tests/golden/make_oracle_solves.py, which calls only the oracle."""
+    p = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
 def run_reference(args):
-    """The oracle (plain CPU FP64 Block Krylov-Schur) timed on the host cores."""
+    """The oracle (plain CPU FP64 Block Krylov-Schur) timed on the host cores.
+
+    Each timed step is one bounded sample of the workload: the oracle's solve stopped after
+    --ref-cycles Krylov-Schur cycles (the first cycle builds all 8 blocks, every later one 3),
+    so steps x ms_per_step is time actually spent.  `value` extrapolates the sample's time per
+    block SpMM step to the block count of the oracle's OWN full solve of the same graph
+    (tests/golden/oracle_solves.json).  The first cycles orthogonalise against fewer blocks
+    than the average cycle, so the extrapolation errs on the fast side for the oracle."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
-    import numpy as np
     import graphgen
     from oracle import bks
     g = graphgen.rmat(args.scale, seed=1)
     cores = os.cpu_count()
-    for _ in range(args.warmup if args.scale <= 16 else 0):
-        bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1, max_restarts=0)
-    times, steps_done = [], []
+    full = oracle_full_solves().get(f"rmat{args.scale}")
+    for _ in range(args.warmup):
+        bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
+                               max_restarts=0)
+    times, blocks = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         r = bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
                                    max_restarts=args.ref_cycles - 1)
         times.append(time.perf_counter() - t0)
-        steps_done.append(r.spmm_blocks)
-    # a full solve needs the GPU solve's block-SpMM count; scale the sample by block steps
-    full_blocks = args.ref_solve_blocks
-    per_block = sum(times) / sum(steps_done)
+        blocks.append(r.spmm_blocks)
+    per_block = sum(times) / sum(blocks)
+    if full is not None:
+        full_blocks, basis = full["spmm_blocks"], (f"the oracle's own full solve of this graph "
+                                                   f"({full['spmm_blocks']} block SpMMs, "
+                                                   f"{full['restarts']} restarts)")
+    else:
+        full_blocks, basis = blocks[0], "no full oracle solve recorded for this scale: the sample itself"
     t_solve = per_block * full_blocks
     sample = (f"{args.ref_cycles} Krylov-Schur cycle(s) of the oracle on R-MAT scale {args.scale} "
-              f"({steps_done[0]} block SpMM steps), scaled to {full_blocks} block steps per solve")
-    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t_solve, "unit": "solves/s",
+              f"({blocks[0]} block SpMMs, {statistics.median(times):.2f} s median) per step; "
+              f"time per block SpMM x {full_blocks} block SpMMs of {basis}")
+    # config 1 (scale 14): the oracle's full solve fits in seconds -- timed once, in full
+    t14 = None
+    if args.scale != 14 and not args.no_config1:
+        g14 = graphgen.rmat(14, seed=1)
+        t0 = time.perf_counter()
+        r14 = bks.block_krylov_schur(g14.rowptr, g14.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
+                                     max_restarts=5000)
+        t14 = {"workload": "rmat14-ef16 FP64 Block Krylov-Schur nev8 b4 m32 tol1e-8 (full solve)",
+               "s": round(time.perf_counter() - t0, 3), "restarts": int(r14.restarts),
+               "spmm_blocks": int(r14.spmm_blocks), "converged": bool(r14.converged)}
+    value = 1.0 / t_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * t_solve, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1000.0 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale}-ef16 FP64 Block Krylov-Schur nev8 b4 m32 tol1e-8",
                        "n": g.n, "nnz": g.nnz},
-            "cpu_baseline": {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores,
+            "sample": {"ms_per_step": 1000.0 * statistics.mean(times), "block_spmms_per_step": blocks[0],
+                       "s_per_block_spmm": per_block},
+            "extrapolation": {"full_solve_block_spmms": full_blocks, "basis": basis,
+                              "s_per_solve": t_solve},
+            "full_solve_config1": t14,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
-            "e2e": {"value": 1.0 / t_solve, "unit": "solves/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -184,16 +220,21 @@ def ugram_inputs(fe, torch, n):
     return Vg, Cg, Wg
 
 
-def cpu_baseline(g, gpu_blocks, cycles=1):
+def cpu_baseline(g, scale, cycles=2):
+    """The oracle on a bounded sample (its first `cycles` Krylov-Schur cycles), time per block
+    SpMM scaled to the block count of the oracle's own full solve of the graph."""
     from oracle import bks
     t0 = time.perf_counter()
     r = bks.block_krylov_schur(g.rowptr, g.colidx, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
                                max_restarts=cycles - 1)
     t = time.perf_counter() - t0
-    t_solve = t / r.spmm_blocks * gpu_blocks
+    full = oracle_full_solves().get(f"rmat{scale}")
+    blocks = full["spmm_blocks"] if full else r.spmm_blocks
+    t_solve = t / r.spmm_blocks * blocks
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{cycles} Krylov-Schur cycle ({r.spmm_blocks} block SpMM steps, {t:.1f} s) of "
-                      f"the oracle on the same graph, scaled to the GPU solve's {gpu_blocks} block steps"}
+            "sample": f"{cycles} Krylov-Schur cycles ({r.spmm_blocks} block SpMMs, {t:.1f} s) of the "
+                      f"oracle on the same graph; time per block SpMM x {blocks} block SpMMs "
+                      + ("of the oracle's own full solve" if full else "(no full solve recorded)")}
 
 
 def run_ours(args):
@@ -341,6 +382,50 @@ def run_ours(args):
                 "ms_per_launch": round(tg, 4), "stream": "torch current stream",
                 "hbm_frac": round(ubytes / (tg / 1000.0) / 1e9 / hbm_peak, 4)}
     del Vg, Wg, Cg
+
+    # ---- the same FP64 solve with every orthogonalisation product in FP64 arithmetic
+    # (orth_pass1 = fp64: no FP32-arithmetic first Gram-Schmidt pass or small corrections)
+    fp64_all = None
+    if not args.no_fp64_all:
+        try:
+            out = {}
+            def run_all64():
+                out["r"] = fe.eigs(h, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1, orth_pass1="fp64",
+                                   max_restarts=MAX_RESTARTS)
+            run_all64()
+            ta = time_cuda(run_all64, 1, torch)[0]
+            eva, Xa, sta = out["r"]
+            fp64_all = {"s": ta / 1000.0, "restarts": sta["restarts"], "spmm_blocks": sta["spmm_blocks"],
+                        "converged": sta["converged"], "max_resid": sta["max_resid"],
+                        "max_rel_eval_diff_vs_step": float(np.max(np.abs(eva - ev) / np.abs(ev))),
+                        "step_speedup": ta / ms_per_step}
+        except Exception as e:
+            fp64_all = {"error": str(e)}
+
+    # ---- config 1: R-MAT scale 14, the full plain FP64 solve (the oracle arm times its own
+    # full solve of the same graph)
+    config1 = None
+    if not args.no_config1 and args.scale != 14:
+        try:
+            g14 = graphgen.rmat(14, seed=1)
+            with fe.Csr.from_graph(g14) as h14:
+                out = {}
+                def run14():
+                    out["r"] = fe.eigs(h14, NEV, BLOCK, NBLOCKS, TOL, "LM", seed=1,
+                                       max_restarts=MAX_RESTARTS)
+                for _ in range(3):
+                    run14()
+                t14 = statistics.median(time_cuda(run14, 5, torch))
+                ev14, _, st14 = out["r"]
+            full14 = oracle_full_solves().get("rmat14")
+            config1 = {"workload": "rmat14-ef16 FP64 Block Krylov-Schur nev8 b4 m32 tol1e-8 (full solve)",
+                       "s": t14 / 1000.0, "restarts": st14["restarts"], "spmm_blocks": st14["spmm_blocks"],
+                       "converged": st14["converged"],
+                       "max_rel_eval_diff_vs_oracle": (float(np.max(np.abs(ev14 - np.array(full14["evals"]))
+                                                                    / np.abs(np.array(full14["evals"]))))
+                                                       if full14 else None)}
+        except Exception as e:
+            config1 = {"error": str(e)}
 
     # ---- mixed-precision solve on the same graph (time to 8 eigenpairs)
     t_mixed = None
@@ -517,14 +602,14 @@ def run_ours(args):
             "time_to_8_eigenpairs_s": ms_per_step / 1000.0,
             "eigs": {"restarts": stats[-1]["restarts"], "spmm_blocks": blocks,
                      "evals_head": [float(x) for x in ev[:3]], "max_resid": stats[-1]["max_resid"]},
-            "mixed": t_mixed, "learned": learned_res, "many_eigs": many, "svd": svd_res, "semi_external": semi,
+            "fp64_all_orth": fp64_all, "config1": config1, "mixed": t_mixed, "learned": learned_res, "many_eigs": many, "svd": svd_res, "semi_external": semi,
             "spmm_sweep": sweep, "spmm_roofline": spmm_roofline, "roofline": roofline,
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": int(launches),
             "setup": {"graph_gen_s": round(t_gen, 2), "csr_create_s": round(t_create, 3),
                       "device_bytes": info["device_bytes"]}}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(g, blocks)
+        line["cpu_baseline"] = cpu_baseline(g, args.scale)
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
@@ -654,6 +739,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-fp64-all", action="store_true",
+                    help="skip the FP64 solve with all-FP64 orthogonalisation arithmetic")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-many", action="store_true", help="skip the nev 32 (m = 128) leg")
     ap.add_argument("--no-svd", action="store_true", help="skip the directed-graph SVD leg")
@@ -668,8 +755,10 @@ def main():
     # kernel changes
     ap.add_argument("--traffic", type=float, default=1.073919e9 + 126.096384e6,
                     help="ncu DRAM bytes per launch of the roofline kernel")
-    ap.add_argument("--ref-cycles", type=int, default=1)
-    ap.add_argument("--ref-solve-blocks", type=int, default=150)
+    ap.add_argument("--ref-cycles", type=int, default=2,
+                    help="reference arm: Krylov-Schur cycles of the oracle per timed sample")
+    ap.add_argument("--no-config1", action="store_true",
+                    help="skip the full scale-14 solves (both arms)")
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
                     help="where the clock samples are written")
     ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1", "ugram1"],

@@ -53,6 +53,11 @@ typedef enum { FE_F32 = 0, FE_F64 = 1 } fe_dtype;
 typedef enum { FE_LM = 0, FE_LA = 1, FE_SA = 2 } fe_which; /* largest |x|, largest, smallest */
 typedef enum { FE_MODE_FP64 = 0, FE_MODE_MIXED = 1 } fe_mode;
 typedef enum { FE_START_RANDOM = 0, FE_START_USER = 1, FE_START_LEARNED = 2 } fe_start;
+/* Arithmetic of the FP64 dense block products that support it (fe_block_combine and the
+ * solver's restart and Ritz-vector products): FE_ENGINE_AUTO = tensor cores where the shape is
+ * supported, FMA otherwise; FE_ENGINE_FMA = FP64 fused multiply-adds; FE_ENGINE_TC = tensor
+ * cores (exact BF16 digit products, see fe_block_combine), FE_ERR_INVALID where unsupported. */
+typedef enum { FE_ENGINE_AUTO = 0, FE_ENGINE_FMA = 1, FE_ENGINE_TC = 2 } fe_engine;
 
 /* Message for the last failing call on this thread ("" if none).  Never NULL. */
 const char* fe_last_error(void);
@@ -165,13 +170,15 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info);
  * b in {1, 2, 4, 8, 16}; Y is overwritten (rows of empty matrix rows become 0); X and Y must
  * not overlap.  Accumulation is in dt.  Accuracy, per entry, against the exact sum of the
  * given X values, for any degree and any signs ((A|X|)_ij = sum over the row of |X[j, :]|):
- *   FP32: every lane's running sum is compensated (Kahan), lanes' sums are combined by a tree
- *         of at most 5 levels, and the chunks of a split hub row are added in compensated
- *         FP64 and rounded once, so |error| <= 9 * 2^-24 * (A|X|)_ij (about 5.4e-7, plus
- *         terms of order degree * 2^-48);
- *   FP64: plain sums, |error| <= (m + 6) * 2^-53 * (A|X|)_ij, m the longest run one lane adds:
- *         m <= tail_max for rows in the slices, m <= 512 for longer rows when X is 32-byte
- *         aligned (1024 when it is only 16-byte aligned and b = 16), so below 6e-14 (1.2e-13).
+ *   FP32: a lane adds the X rows it gathers in groups of four (pairwise), the group sums into a
+ *         compensated (Kahan) running sum, lanes' sums are combined by a tree of at most 5
+ *         levels, and the chunks of a split hub row are added in compensated FP64 and rounded
+ *         once, so |error| <= 10 * 2^-24 * (A|X|)_ij (about 6.0e-7, plus terms of order
+ *         degree * 2^-48);
+ *   FP64: the same order with plain sums, |error| <= (m/4 + 8) * 2^-53 * (A|X|)_ij, m the
+ *         longest run one lane adds: m <= tail_max for rows in the slices, m <= 512 for longer
+ *         rows when X is 32-byte aligned (1024 when it is only 16-byte aligned and b = 16), so
+ *         below 1.6e-14 (3e-14).
  * Both pointers must be 16-byte aligned.  Errors: FE_ERR_INVALID (null/unaligned pointer, unsupported b),
  * FE_ERR_CUDA, FE_ERR_TIMEOUT (semi-external copy wait).  Asynchronous when resident.
  */
@@ -235,6 +242,26 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
  */
 int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* C, double alpha,
                          double beta, void* W, fe_dtype dt, double* G);
+
+/*
+ * Block product with several output blocks, the restart and Ritz-vector product of the
+ * Krylov-Schur solver, V_new = V Y (Table 1 "op1", MvTimesMatAddMv with beta = 0; Section 3.1
+ * step (2)): output block o (n x bv) = sum_j V_j Y[j*bv:(j+1)*bv, o*bv:(o+1)*bv].
+ * V: DEVICE, nv blocks of n x bv (block after block); Y: DEVICE FP64 row-major
+ * (nv*bv) x (nout*bv); Out: DEVICE, nout blocks of n x bv, overwritten, must not alias V.
+ * 1 <= nv <= 32, 1 <= nout <= 32, bv in {1, 2, 4, 8, 16}.
+ * engine (fe_engine): for FP64 with K = nv*bv <= 64 and N = nout*bv <= 32, FE_ENGINE_AUTO and
+ * FE_ENGINE_TC use the tensor cores: every V row is cut, relative to its largest exponent, into
+ * seven 8-bit digits, every Y column likewise; the digit products (exact in BF16 x BF16 -> FP32
+ * for K <= 32 per accumulator) of weight classes i + j <= 6 are summed on the tensor cores and
+ * assembled in 128-bit integer arithmetic, so that |error| <= 2^-49 K max_c|V[r][c]|
+ * max_c|Y[c][q]| + 2^-52 |result| (results below 2^-1022 flush to zero; entries must be finite,
+ * subnormal entries are read as zero).  Otherwise, and for FE_ENGINE_FMA, FMA kernels in dt
+ * (FP32 blocks: FP32 arithmetic).  Errors: FE_ERR_INVALID (including FE_ENGINE_TC with an
+ * unsupported shape), FE_ERR_OOM, FE_ERR_CUDA.  Asynchronous.
+ */
+int fe_block_combine(const void* V, int64_t n, int nv, int bv, const double* Y, int nout, void* Out,
+                     fe_dtype dt, int engine);
 
 /*
  * Re-orthogonalisation step of the block Krylov expansion (Section 3.1 step (1)): block
@@ -331,6 +358,10 @@ typedef struct {
                              device memory for the next SpMM (its most-recent-matrix caching,
                              Section 3.4.4); for subspaces larger than HBM.  Same arithmetic,
                              same results as 0 (default). */
+  int engine;             /* FP64 restart and Ritz-vector products: FE_ENGINE_FMA = FP64 FMA,
+                             FE_ENGINE_AUTO or FE_ENGINE_TC = tensor cores wherever
+                             fe_block_combine supports the shape (subspace m <= 64, kept
+                             vectors <= 32), FP64 FMA elsewhere (FE_ENGINE_AUTO) */
 } fe_eigs_opts;
 
 void fe_eigs_opts_default(fe_eigs_opts* opts);

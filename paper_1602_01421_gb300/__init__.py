@@ -147,6 +147,21 @@ def block_gram(V, W, alpha: float = 1.0, G=None):
     return G
 
 
+def block_combine(V, Y, nout: int, Out=None, engine: str = "auto"):
+    """Out blocks o = sum_j V_j Y[j-block rows, o-block columns] (fe_block_combine).
+    V: (nv, n, bv) blocks; Y: float64 (nv*bv, nout*bv); returns Out (nout, n, bv).
+    engine: "auto", "fma" or "tc" (tensor-core split products, FP64 only)."""
+    torch = _torch()
+    nv, n, bv = V.shape
+    if Out is None:
+        Out = torch.empty((nout, n, bv), dtype=V.dtype, device=V.device)
+    Y = Y.to(torch.float64).contiguous()
+    _stream()
+    check(load().fe_block_combine(_dev(V, "V"), n, nv, bv, _dev(Y, "Y"), nout, _dev(Out, "Out"),
+                                  _dt(V), _lib.ENGINE[engine]))
+    return Out
+
+
 def block_update(V, C, W, alpha: float = 1.0, beta: float = 1.0):
     """W = beta W + alpha V C (fe_block_update).  V: (nv, n, bv) or None; C: float64."""
     n, bw = W.shape
@@ -209,11 +224,12 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
          mode: str = "fp64", start=None, seed: int = 1, max_restarts: int = 500,
          mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 5e-6,
          orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True,
-         subspace: str = "device"):
+         subspace: str = "device", engine: str = "auto"):
     """Block Krylov-Schur (fe_eigs_ex).  subspace="host" keeps the subspace blocks in pinned
     host memory (newest block cached on the device).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
     None, stats dict).  orth_pass1: "fp32" or "fp64" arithmetic for the first Gram-Schmidt
-    pass's Gram on an FP64 subspace."""
+    pass's Gram on an FP64 subspace.  engine: "auto"/"tc" (tensor-core restart products where
+    supported) or "fma"."""
     torch = _torch()
     lib = load()
     o = _lib.EigsOpts()
@@ -224,6 +240,7 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
     o.mixed_tol = float(mixed_tol)
     o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
     o.subspace_host = {"device": 0, "host": 1}[subspace]
+    o.engine = _lib.ENGINE[engine]
     o.mlp_hidden = int(mlp_hidden)
     if start is not None:
         start = start.to(torch.float64).contiguous()
@@ -250,7 +267,7 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
 def svds(h: Csr, nsv: int, block: int, nblocks: int, tol: float = 1e-8, *, mode: str = "fp64",
          start=None, seed: int = 1, max_restarts: int = 500, mixed_tol: float = 5e-6,
          orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True,
-         subspace: str = "device"):
+         subspace: str = "device", engine: str = "auto"):
     """Largest singular triplets of the handle's matrix (fe_svds; needs transpose=True).
     Returns (svals numpy, right (n, nsv) CUDA float64 or None, left (n, nsv) or None, stats)."""
     torch = _torch()
@@ -263,6 +280,7 @@ def svds(h: Csr, nsv: int, block: int, nblocks: int, tol: float = 1e-8, *, mode:
     o.mixed_tol = float(mixed_tol)
     o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
     o.subspace_host = {"device": 0, "host": 1}[subspace]
+    o.engine = _lib.ENGINE[engine]
     if start is not None:
         start = start.to(torch.float64).contiguous()
         o.start = _lib.START["user"]

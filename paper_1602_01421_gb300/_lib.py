@@ -22,6 +22,7 @@ WHICH = {"LM": 0, "LA": 1, "SA": 2}
 MODE = {"fp64": 0, "mixed": 1}
 START = {"random": 0, "user": 1, "learned": 2}
 INDEX_FORMAT = {"auto": 0, "plain": 1, "packed": 2}
+ENGINE = {"auto": 0, "fma": 1, "tc": 2}
 
 
 class CsrOpts(ctypes.Structure):
@@ -48,7 +49,8 @@ class EigsOpts(ctypes.Structure):
                 ("start", ctypes.c_int), ("start_block", ctypes.c_void_p),
                 ("mlp_weights", ctypes.c_void_p), ("mlp_hidden", ctypes.c_int),
                 ("mixed_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
-                ("orth_pass1", ctypes.c_int), ("subspace_host", ctypes.c_int)]
+                ("orth_pass1", ctypes.c_int), ("subspace_host", ctypes.c_int),
+                ("engine", ctypes.c_int)]
 
 
 class EigsStats(ctypes.Structure):
@@ -92,6 +94,7 @@ def load(build_if_missing: bool = True):
                               ctypes.POINTER(EigsStats)]),
             "fe_block_gram": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_block_update": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, i32]),
+            "fe_block_combine": (i32, [vp, i64, i32, i32, vp, i32, vp, i32, i32]),
             "fe_block_update_gram": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, vp]),
             "fe_block_orth": (i32, [vp, i64, i32, i32, vp, i32, dbl, ctypes.c_uint64, vp, vp,
                                     ctypes.POINTER(i32)]),

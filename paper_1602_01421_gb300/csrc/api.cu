@@ -347,6 +347,26 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
   return update(vs, n, C, alpha, beta, nullptr, W, bw, bw, dt, cur_stream());
 }
 
+int fe_block_combine(const void* V, int64_t n, int nv, int bv, const double* Y, int nout, void* Out,
+                     fe_dtype dt, int engine) {
+  FE_ARG(V && Y && Out, "fe_block_combine: NULL pointer");
+  FE_ARG(n >= 1, "fe_block_combine: n < 1");
+  FE_ARG(nv >= 1 && nv <= 32, "fe_block_combine: nv = %d not in [1, 32]", nv);
+  FE_ARG(nout >= 1 && nout <= 32, "fe_block_combine: nout = %d not in [1, 32]", nout);
+  FE_ARG(is_pow2_le16(bv), "fe_block_combine: bv = %d not in {1,2,4,8,16}", bv);
+  FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_combine: bad dtype");
+  {
+    const size_t es = dt == FE_F32 ? 4 : 8;
+    const char* va = (const char*)V;
+    const char* oa = (const char*)Out;
+    FE_ARG(oa + (size_t)nout * n * bv * es <= va || va + (size_t)nv * n * bv * es <= oa,
+           "fe_block_combine: Out aliases V");
+  }
+  BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
+  BlockSet os = make_blockset(Out, nout, bv, bv, n * bv, dt);
+  return combine(vs, n, Y, nout * bv, os, dt, cur_stream(), engine);
+}
+
 int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* C, double alpha,
                          double beta, void* W, fe_dtype dt, double* G) {
   FE_ARG(W && G, "fe_block_update_gram: NULL W or G");

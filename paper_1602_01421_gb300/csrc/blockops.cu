@@ -516,9 +516,17 @@ static int launch_combine(const BlockSet& V, int64_t n, const double* Y, int ldy
 }
 
 int combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
-            fe_dtype dt, cudaStream_t s) {
+            fe_dtype dt, cudaStream_t s, int engine) {
   FE_ARG(V.bv == Out.bv, "combine: block widths differ");
   FE_ARG(V.nv >= 1 && Out.nv >= 1, "combine: empty block set");
+  FE_ARG(engine == FE_ENGINE_AUTO || engine == FE_ENGINE_FMA || engine == FE_ENGINE_TC,
+         "combine: engine = %d", engine);
+  if (engine != FE_ENGINE_FMA && dt == FE_F64) {
+    if (tc_combine_supported(V, Out, dt)) return tc_combine(V, n, Y, ldy, Out, s);
+    FE_ARG(engine == FE_ENGINE_AUTO,
+           "combine: the tensor-core engine takes FP64 blocks with nv*bv <= 64 and nout*bv <= 32");
+  }
+  FE_ARG(engine != FE_ENGINE_TC, "combine: the tensor-core engine takes FP64 blocks only");
   if (dt == FE_F32) {
     switch (V.bv) {
       case 1: return launch_combine<float, 1>(V, n, Y, ldy, Out, s);

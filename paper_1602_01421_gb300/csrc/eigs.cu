@@ -109,6 +109,7 @@ struct Phase {
   int pass1_f32 = 0;  // FP64 subspace: first Gram-Schmidt pass's Gram in FP32 arithmetic
   int op_ata = 0;  // 1: iterate with A^T A (SVD of a directed graph's matrix, Section 4.3.2)
   int subspace_host = 0;  // 1: subspace blocks in mapped pinned host memory, newest block cached
+  int engine = FE_ENGINE_AUTO;  // FP64 restart / Ritz-vector products (tensor cores where supported)
   int stagnation_window = 0;  // > 0: stop when the worst wanted rho/scale has not halved
                               // over this many restarts (FP32 phase: at its precision floor
                               // the ratio only fluctuates)
@@ -166,6 +167,10 @@ struct Phase {
     resid_h.assign(nev, 0.0);
     return FE_OK;
   }
+
+  // engine of the restart / Ritz-vector products: FMA when asked for, otherwise tensor cores
+  // wherever the shape and precision allow (FE_ENGINE_TC does not fail the solve elsewhere)
+  int product_engine() const { return engine == FE_ENGINE_FMA ? FE_ENGINE_FMA : FE_ENGINE_AUTO; }
 
   BlockSet slots(int j0, int j1) const {  // slots [j0, j1)
     std::vector<const void*> v(slot.begin() + j0, slot.begin() + j1);
@@ -254,7 +259,7 @@ struct Phase {
     const int nx = (int)xblk.size();
     BlockSet V = slots(0, NB);
     BlockSet X = blockset_of(std::vector<const void*>(xblk.begin(), xblk.end()), b, b);
-    FE_TRY(combine(V, n, Y, m, X, dt, s));
+    FE_TRY(combine(V, n, Y, m, X, dt, s, product_engine()));
     std::vector<double> nrm(b);
     max_resid = 0.0;
     *good = true;
@@ -289,7 +294,7 @@ struct Phase {
     BlockSet V = slots(0, NB);
     std::vector<const void*> outs(spare.begin(), spare.begin() + k / b);
     BlockSet Out = blockset_of(outs, b, b);
-    FE_TRY(combine(V, n, Y, m, Out, dt, s));
+    FE_TRY(combine(V, n, Y, m, Out, dt, s, product_engine()));
     for (int o = 0; o < k / b; ++o) std::swap(slot[o], spare[o]);
     std::swap(slot[k / b], slot[NB]);
     ++restarts;
@@ -417,6 +422,8 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
   if (o.max_restarts < 0) o.max_restarts = 0;
   if (o.max_sweeps <= 0) o.max_sweeps = 60;
   FE_ARG(o.orth_pass1 == 0 || o.orth_pass1 == 1, "fe_eigs: orth_pass1 = %d not 0 or 1", o.orth_pass1);
+  FE_ARG(o.engine == FE_ENGINE_AUTO || o.engine == FE_ENGINE_FMA || o.engine == FE_ENGINE_TC,
+         "fe_eigs: engine = %d", o.engine);
   cudaStream_t s = cur_stream();
   const int m = block * nblocks;
 
@@ -445,6 +452,7 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
   p1.pass1_f32 = o.orth_pass1 == 0;
   p1.op_ata = op_ata;
   p1.subspace_host = o.subspace_host != 0;
+  p1.engine = o.engine;
   p1.s = s;
   int rc;
   double secs32 = 0.0;
@@ -509,6 +517,7 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
     p2.pass1_f32 = o.orth_pass1 == 0;
     p2.op_ata = op_ata;
     p2.subspace_host = o.subspace_host != 0;
+    p2.engine = o.engine;
     p2.s = s;
     p2.tol = tol;
     p2.dt = FE_F64;

@@ -97,8 +97,13 @@ int update(const BlockSet& V, int64_t n, const double* C, double alpha, double b
            const double* M, void* W, int bw, int ldw, fe_dtype dt, cudaStream_t s);
 // Out_o[r] = sum_j V_j[r] Y[j*bv.., o*bv..] for o < nout (Y: (nv*bv) x ldy FP64 device,
 // output column block o uses Y columns [o*bv, (o+1)*bv)).  Out blocks must not alias V.
+// engine (fe_engine): FP64 blocks go to the tensor-core split-product kernel (tcgemm.cu) when
+// it supports the shape (AUTO) or always (TC, error otherwise); FMA keeps the FMA kernel.
 int combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
-            fe_dtype dt, cudaStream_t s);
+            fe_dtype dt, cudaStream_t s, int engine = FE_ENGINE_AUTO);
+bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt);
+int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
+               cudaStream_t s);
 // Small-matrix device scratch: a pool of FP64 buffers reused across calls on this thread.
 double* small_scratch(int slot, size_t count);
 int random_normal(void* X, int64_t n, int b, int ld, fe_dtype dt, uint64_t seed,

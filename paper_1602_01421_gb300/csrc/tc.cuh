@@ -1,0 +1,128 @@
+// Fifth-generation tensor core (tcgen05) and mbarrier primitives for sm_100-family GPUs, as
+// inline PTX (PTX ISA 8.6+, "Tensor Core 5th Generation Family Instructions"):
+//   * tensor memory (TMEM): per-SM accumulator memory of 128 lanes x 512 columns of 32 bits,
+//     allocated per CTA in power-of-two column counts (>= 32) by one warp;
+//   * tcgen05.mma: D (TMEM, FP32) (+)= A (shared memory) x B (shared memory), issued by one
+//     thread, completion signalled on an mbarrier by tcgen05.commit;
+//   * tcgen05.ld: each warp of a warpgroup reads its 32 TMEM lanes into registers.
+// Operand tiles use the no-swizzle K-major canonical layout: 8 x 16-byte "core matrices"
+// (8 rows of 8 bf16), element (row, k) at (row / 8) * SBO + (k / 8) * LBO + (row % 8) * 16 +
+// (k % 8) * 2 bytes; the shared-memory matrix descriptor carries start address, LBO and SBO.
+#pragma once
+#include <stdint.h>
+
+namespace fe {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Make the initialised barrier visible to the asynchronous proxy (the tensor core's commit).
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One bounded wait for the phase with the given parity to complete: true when it completed,
+// false after max_spins polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_spins) {
+  const uint32_t a = smem_addr(bar);
+  for (uint32_t i = 0; i < max_spins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- fences
+// Shared-memory writes by threads (generic proxy) -> visible to tcgen05.mma (async proxy).
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- TMEM allocation (one warp)
+// Writes the TMEM base address (lane 0, first column) to *dst (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// ---------------------------------------------------------------- descriptors
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension byte offset
+// (between core matrices adjacent in K), stride byte offset (between 8-row groups), all >> 4;
+// bits 46-47 = 1 (the sm_100 descriptor version), base offset 0, layout type 0 (no swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// Instruction descriptor of tcgen05.mma.kind::f16: BF16 A and B, FP32 D, both K-major, no
+// negation or sparsity; N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | (1u << 7)                    // A format: BF16
+         | (1u << 10)                   // B format: BF16
+         | ((uint32_t)(N >> 3) << 17)   // N
+         | ((uint32_t)(M >> 4) << 24);  // M
+}
+
+// ---------------------------------------------------------------- MMA, commit, loads
+// D[tmem] = A x B^T (accumulate = 0) or D += A x B^T (accumulate = 1); A is M x 16, B is N x 16
+// (both K-major bf16), D is M x N FP32 (lane = row, column = n for M = 128).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive once on the mbarrier when every tcgen05.mma issued so far by this thread completes.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+// Warp-collective: lane l of the calling warp receives 4 consecutive 32-bit columns of TMEM lane
+// (taddr's lane field + l), starting at taddr's column.  Complete after ld_wait().
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Pins registers filled by tmem_ld4 after the tmem_ld_wait that precedes this call: volatile
+// asm statements keep their order, so no use of r can be scheduled before the wait.
+__device__ __forceinline__ void reg_after_wait(uint32_t (&r)[4]) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
+}
+
+}  // namespace tc
+}  // namespace fe

@@ -1,0 +1,376 @@
+// FP64 tall-skinny products on the BF16 tensor cores by exact digit splitting ("split
+// products"; the Ozaki scheme, Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012), for
+// the restart / Ritz-vector product of the Block Krylov-Schur solver (Table 1 "op1" shape,
+// V_out = V Y with V n x K, Y K x N, K <= 64 and N <= 32):
+//
+//   * every V row is scaled by its largest binary exponent and its 53-bit aligned significands
+//     are cut into seven 8-bit digits (sign-magnitude, so every digit is an integer in
+//     [-255, 255] and exact in BF16): V[r][c] = 2^(Er - 1075) sum_i d_i[r][c] 2^(45 - 8 i);
+//   * every Y column likewise by its largest exponent: Y[c][q] = 2^(Fq - 1075) sum_j e_j 2^(45-8j);
+//   * the digit products are exact in the tensor core's FP32 accumulator as long as each
+//     accumulator sums at most 2^24 / 255^2 = 258 of them: one accumulator per digit-weight
+//     class g = i + j (g <= 6) and per 32-wide slice of K holds at most 7 * 32 products;
+//   * V Y = 2^(Er + Fq - 2108) * T with T = sum_g D_g 2^(8 (6 - g)), assembled exactly in
+//     128-bit integer arithmetic from the accumulators and rounded once (truncation) to FP64.
+//
+// Error: the digit products dropped (i + j >= 7) and the truncation of each entry below its
+// row's (column's) leading bit bound |error| <= 2^-49 * K * max_c |V[r][c]| * max_c |Y[c][q]|
+// plus 2^-52 |result|; the FP64 pipe is not used at all (FP64 on this part runs at 1/64 of FP32).
+//
+// Kernel structure (one 128-row tile per loop trip, two persistent CTAs of 128 threads per SM):
+// thread t loads row t of the V tile, splits it and writes the digits into shared memory in the
+// no-swizzle K-major core-matrix layout; thread 0 issues the 28 x (K/16) tcgen05.mma into the
+// CTA's tensor memory and commits to an mbarrier; every thread then reads its row's
+// accumulators (TMEM lane t) with tcgen05.ld, assembles its N FP64 results and stores them.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "fe_internal.cuh"
+#include "tc.cuh"
+#include "vec.cuh"
+
+namespace fe {
+
+namespace {
+
+constexpr int kDigits = 7;           // 8-bit digits per 53-bit significand (7 * 8 >= 53)
+constexpr int kClasses = 7;          // digit-weight classes g = i + j kept (g <= 6)
+constexpr int kTileRows = 128;       // MMA M
+constexpr int kKChunk = 32;          // K columns per accumulator set (exactness bound)
+constexpr int kMaxK = 64;
+constexpr int kMaxN = 32;
+constexpr int kThreads = 128;
+constexpr uint32_t kWaitSpins = 1u << 24;
+constexpr int kCoreBytes = 128;      // 8 rows x 16 bytes
+// A (V digits): per (K chunk, digit) a 128 x 32 bf16 tile = 8 KB; SBO = 4 core matrices
+constexpr int kATileBytes = kTileRows * kKChunk * 2;
+constexpr uint32_t kLBO = kCoreBytes;               // next core matrix along K
+constexpr uint32_t kSBO = (kKChunk / 8) * kCoreBytes;  // next 8-row group
+
+// Byte offset of element (row, k) of a [rows x 32] bf16 K-major tile (k < 32).
+__host__ __device__ inline uint32_t tile_off(int row, int k) {
+  return (uint32_t)((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Biased exponent field of a double (0 for zero and subnormals, which are read as zero).
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// Significand of x aligned to the binary exponent field emax (>= x's): a non-negative integer
+// below 2^53 with x = +-M * 2^(emax - 1075) up to the bits shifted out.
+__device__ __forceinline__ uint64_t aligned_sig(double x, int emax) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const int sh = emax - e;
+  if (e == 0 || sh > 52) return 0;
+  return ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
+}
+
+// Digit i of an aligned significand: bits [45 - 8 i, 52 - 8 i] for i < 6, the low 5 bits
+// shifted up by 3 for i = 6 (weight 2^(45 - 8 i) in both cases).
+__device__ __forceinline__ uint32_t digit(uint64_t m, int i) {
+  return i < 6 ? (uint32_t)(m >> (45 - 8 * i)) & 0xFFu : ((uint32_t)m & 0x1Fu) << 3;
+}
+
+// Two digits (each an integer in [0, 255]) with signs s0, s1 (0 or 1) as a packed bf16 pair:
+// 2^23 + d is exact in FP32, minus 2^23 gives d as an FP32 whose top 16 bits are its bf16.
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t d0, uint32_t d1, uint32_t s0, uint32_t s1) {
+  const float f0 = __uint_as_float(0x4B000000u | d0) - 8388608.0f;
+  const float f1 = __uint_as_float(0x4B000000u | d1) - 8388608.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | (s0 << 15) | (s1 << 31);
+}
+
+// Exact integer value of an FP32 accumulator holding an integer of magnitude below 2^24.
+__device__ __forceinline__ int64_t acc_int(uint32_t bits) {
+  return (int64_t)__float2int_rn(__uint_as_float(bits));
+}
+
+// 2^s * T rounded toward zero to FP64, T = hi * 2^32 + lo (|T| < 2^75); flushes to zero below
+// the normal range and saturates to infinity above it.
+__device__ __forceinline__ double assemble(int64_t hi, int64_t lo, int s) {
+  __int128 t = ((__int128)hi << 32) + (__int128)lo;
+  if (t == 0) return 0.0;
+  const uint64_t sign = t < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned __int128 a = t < 0 ? (unsigned __int128)(-t) : (unsigned __int128)t;
+  const uint64_t ah = (uint64_t)(a >> 64), al = (uint64_t)a;
+  const int msb = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);
+  // significand: bits [msb - 52, msb] of a (truncated)
+  uint64_t m;
+  if (msb >= 52) m = (uint64_t)(a >> (msb - 52));
+  else m = al << (52 - msb);
+  const int ef = msb + s + 1023;
+  if (ef <= 0) return __longlong_as_double((long long)sign);
+  if (ef >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((uint64_t)ef << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+struct TcArgs {
+  const double* vblk[kMaxK];   // K / BV blocks of n x BV (ld BV)
+  double* oblk[kMaxN];         // N / BV output blocks of n x BV (ld BV); fewer when BV < 4
+  int64_t n;
+  int K, N, NP;                // NP: N padded to the MMA's N (16 or 32)
+  int nkc;                     // K chunks of 32
+  const uint16_t* bdig;        // global: [nkc][7][NP x 32] canonical tiles
+  const int* fexp;             // global: N column exponent fields of Y
+  int* status;                 // device word: 1 = an MMA wait ran out
+};
+
+}  // namespace
+
+// Y (K x N FP64, row-major, ld ldy) -> per-column exponent fields and the seven digit tiles of
+// every 32-row K chunk in the MMA's B layout (row q of B = column q of Y; rows N..NP-1 and
+// K beyond K zero).  One CTA.
+__global__ void tc_prep_y_kernel(const double* __restrict__ Y, int ldy, int K, int N, int NP, int nkc,
+                                 uint16_t* __restrict__ bdig, int* __restrict__ fexp) {
+  __shared__ int sf[kMaxN];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    int f = 0;
+    for (int c = 0; c < K; ++c) f = max(f, exp_field(Y[c * ldy + q]));
+    sf[q] = f;
+    fexp[q] = f;
+  }
+  __syncthreads();
+  const int per_tile = NP * kKChunk;  // elements of one [NP x 32] tile
+  const int total = nkc * per_tile;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int kc = e / per_tile, r = e % per_tile;
+    const int q = r / kKChunk, k = r % kKChunk;
+    const int c = kc * kKChunk + k;
+    uint64_t m = 0;
+    uint32_t sgn = 0;
+    if (q < N && c < K) {
+      const double y = Y[c * ldy + q];
+      m = aligned_sig(y, sf[q]);
+      sgn = (uint32_t)((uint64_t)__double_as_longlong(y) >> 63);
+    }
+    for (int j = 0; j < kDigits; ++j) {
+      const uint32_t d = digit(m, j);
+      const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+      const uint16_t bits = (uint16_t)((__float_as_uint(f) >> 16) | (sgn << 15));
+      char* tile = reinterpret_cast<char*>(bdig) + (size_t)(kc * kDigits + j) * per_tile * 2;
+      *reinterpret_cast<uint16_t*>(tile + tile_off(q, k)) = bits;
+    }
+  }
+}
+
+template <int BV>
+__global__ void __launch_bounds__(kThreads) tc_combine_kernel(const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int nkc = a.nkc, NP = a.NP;
+  unsigned char* sA = smem;                                        // [nkc][7] x 8 KB
+  unsigned char* sB = sA + (size_t)nkc * kDigits * kATileBytes;    // [nkc][7] x NP*64
+  const size_t btile = (size_t)NP * kKChunk * 2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + (size_t)nkc * kDigits * btile);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  int* sF = reinterpret_cast<int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t ncols = (uint32_t)nkc * kClasses * NP <= 256 ? 256u : 512u;
+
+  // B digits and column exponents (once per CTA)
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.bdig);
+    int4* dst = reinterpret_cast<int4*>(sB);
+    const int n16 = (int)((size_t)nkc * kDigits * btile / 16);
+    for (int e = tid; e < n16; e += kThreads) dst[e] = src[e];
+    for (int q = tid; q < a.N; q += kThreads) sF[q] = a.fexp[q];
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, ncols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t idesc = tc::idesc_bf16_f32(kTileRows, NP);
+  const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int64_t ntiles = (a.n + kTileRows - 1) / kTileRows;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r = tile * kTileRows + tid;
+    const bool live = r < a.n;
+    // ---- load and split row r of V (K values)
+    double v[kMaxK];
+    int emax = 0;
+#pragma unroll
+    for (int c0 = 0; c0 < kMaxK; c0 += BV) {
+      if (c0 < a.K) {
+        if (live) {
+          ld_row<double, BV>(a.vblk[c0 / BV] + r * BV, &v[c0]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < BV; ++p) v[c0 + p] = 0.0;
+        }
+#pragma unroll
+        for (int p = 0; p < BV; ++p) emax = max(emax, exp_field(v[c0 + p]));
+      }
+    }
+#pragma unroll
+    for (int kc = 0; kc < kMaxK / kKChunk; ++kc) {
+      if (kc < nkc) {
+#pragma unroll
+        for (int k8 = 0; k8 < kKChunk; k8 += 8) {
+          uint32_t w[kDigits][4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = kc * kKChunk + k8 + 2 * e;
+            const double x0 = c < a.K ? v[c] : 0.0, x1 = c + 1 < a.K ? v[c + 1] : 0.0;
+            const uint64_t m0 = aligned_sig(x0, emax), m1 = aligned_sig(x1, emax);
+            const uint32_t s0 = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63);
+            const uint32_t s1 = (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63);
+#pragma unroll
+            for (int i = 0; i < kDigits; ++i) w[i][e] = bf16_pair(digit(m0, i), digit(m1, i), s0, s1);
+          }
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i)
+            *reinterpret_cast<uint4*>(sA + (size_t)(kc * kDigits + i) * kATileBytes + tile_off(tid, k8)) =
+                make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        }
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- one thread issues the digit products: class g = i + j accumulates A_i B_j
+    if (tid == 0) {
+      tc::fence_after_sync();
+      for (int kc = 0; kc < nkc; ++kc)
+        for (int g = 0; g < kClasses; ++g)
+          for (int i = 0; i <= g; ++i) {
+            const int j = g - i;
+            const uint32_t abase = sa0 + (uint32_t)((kc * kDigits + i) * kATileBytes);
+            const uint32_t bbase = sb0 + (uint32_t)((kc * kDigits + j) * btile);
+#pragma unroll
+            for (int ks = 0; ks < kKChunk / 16; ++ks) {
+              const uint64_t ad = tc::smem_desc(abase + ks * 2 * kLBO, kLBO, kSBO);
+              const uint64_t bd = tc::smem_desc(bbase + ks * 2 * kLBO, kLBO, kSBO);
+              tc::mma_bf16(tbase + (uint32_t)((kc * kClasses + g) * NP), ad, bd, idesc,
+                           (i > 0 || ks > 0) ? 1u : 0u);
+            }
+          }
+      tc::mma_commit(bar);
+    }
+    // ---- wait for the products (bounded), then read row tid's accumulators
+    bool ok = tc::mbar_wait(bar, phase, kWaitSpins);
+    if (!ok) {
+      failed = true;
+      tc::mbar_wait(bar, phase, kWaitSpins);  // let the MMAs in flight finish before TMEM is reused
+    }
+    phase ^= 1;
+    tc::fence_after_sync();
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    const int ebase = emax - 2108;
+    for (int q0 = 0; q0 < a.N; q0 += 4) {
+      uint32_t acc[kMaxK / kKChunk][kClasses][4];
+#pragma unroll
+      for (int kc = 0; kc < kMaxK / kKChunk; ++kc)
+        if (kc < nkc)
+#pragma unroll
+          for (int g = 0; g < kClasses; ++g)
+            tc::tmem_ld4(lane_addr + (uint32_t)((kc * kClasses + g) * NP + q0), acc[kc][g]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int kc = 0; kc < kMaxK / kKChunk; ++kc)
+        if (kc < nkc)
+#pragma unroll
+          for (int g = 0; g < kClasses; ++g) tc::reg_after_wait(acc[kc][g]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u;
+        int64_t hi = 0, lo = 0;
+#pragma unroll
+        for (int kc = 0; kc < kMaxK / kKChunk; ++kc)
+          if (kc < nkc) {
+            hi += (acc_int(acc[kc][0][u]) << 16) + (acc_int(acc[kc][1][u]) << 8) + acc_int(acc[kc][2][u]);
+            lo += (acc_int(acc[kc][3][u]) << 24) + (acc_int(acc[kc][4][u]) << 16) +
+                  (acc_int(acc[kc][5][u]) << 8) + acc_int(acc[kc][6][u]);
+          }
+        if (live && q < a.N) {
+          const double y = (ok && emax > 0) ? assemble(hi, lo, ebase + sF[q]) : (ok ? 0.0 : __longlong_as_double(0x7FF8000000000000ll));
+          a.oblk[q / BV][r * BV + q % BV] = y;
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // TMEM read and A tiles free for the next tile
+  }
+  if (failed && tid == 0) atomicExch(a.status, 1);
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+// Shared-memory bytes of tc_combine_kernel for nkc K chunks and padded N.
+static size_t tc_smem_bytes(int nkc, int NP) {
+  return (size_t)nkc * kDigits * kATileBytes + (size_t)nkc * kDigits * NP * kKChunk * 2 + 16 + 4 * kMaxN + 64;
+}
+
+bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt) {
+  const int K = V.nv * V.bv, N = Out.nv * Out.bv;
+  return dt == FE_F64 && V.bv == Out.bv && V.ld == V.bv && Out.ld == Out.bv && K >= 1 && K <= kMaxK &&
+         N >= 1 && N <= kMaxN && V.bv >= 1 && V.bv <= 16;
+}
+
+template <int BV>
+static int launch_tc_combine(const TcArgs& a, size_t smem, bool two_per_sm, cudaStream_t s) {
+  static KernelSetup ks;
+  const void* fn = reinterpret_cast<const void*>(tc_combine_kernel<BV>);
+  FE_TRY(kernel_configure(ks, fn, 227 * 1024));
+  const int64_t ntiles = ceil_div(a.n, kTileRows);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)(two_per_sm ? 2 : 1) * num_sms()));
+  tc_combine_kernel<BV><<<(unsigned)grid, kThreads, smem, s>>>(a);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// Out = V Y on the tensor cores (FP64 blocks; see tc_combine_supported for the shapes).
+int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
+               cudaStream_t s) {
+  FE_ARG(tc_combine_supported(V, Out, FE_F64), "tc_combine: unsupported shape");
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  const int BV = V.bv;
+  a.n = n;
+  a.K = V.nv * BV;
+  a.N = Out.nv * BV;
+  a.NP = a.N <= 16 ? 16 : 32;
+  a.nkc = (int)ceil_div(a.K, kKChunk);
+  for (int j = 0; j < V.nv; ++j) a.vblk[j] = static_cast<const double*>(V.blk[j]);
+  for (int o = 0; o < Out.nv; ++o) a.oblk[o] = const_cast<double*>(static_cast<const double*>(Out.blk[o]));
+  // scratch: B digit tiles, column exponents, status word
+  const size_t bbytes = (size_t)a.nkc * kDigits * a.NP * kKChunk * 2;
+  double* scr = small_scratch(17, bbytes / 8 + kMaxN + 2);
+  if (!scr) return FE_ERR_OOM;
+  a.bdig = reinterpret_cast<const uint16_t*>(scr);
+  a.fexp = reinterpret_cast<const int*>(scr + bbytes / 8);
+  a.status = reinterpret_cast<int*>(scr + bbytes / 8 + kMaxN);
+  FE_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
+  tc_prep_y_kernel<<<1, 256, 0, s>>>(Y, ldy, a.K, a.N, a.NP, a.nkc, const_cast<uint16_t*>(a.bdig),
+                                     const_cast<int*>(a.fexp));
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  // two CTAs per SM when their TMEM (256 columns each) fits; the shared-memory request keeps a
+  // third CTA off the SM, so no CTA waits in tcgen05.alloc
+  const bool two = a.nkc * kClasses * a.NP <= 256;
+  const size_t smem = std::max(tc_smem_bytes(a.nkc, a.NP), two ? (size_t)80 * 1024 : (size_t)120 * 1024);
+  switch (BV) {
+    case 1: return launch_tc_combine<1>(a, smem, two, s);
+    case 2: return launch_tc_combine<2>(a, smem, two, s);
+    case 4: return launch_tc_combine<4>(a, smem, two, s);
+    case 8: return launch_tc_combine<8>(a, smem, two, s);
+    case 16: return launch_tc_combine<16>(a, smem, two, s);
+  }
+  return set_error(FE_ERR_INVALID, "tc_combine: block width %d", BV);
+}
+
+}  // namespace fe

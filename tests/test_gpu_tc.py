@@ -1,0 +1,144 @@
+"""GPU parity of the tensor-core split-product block product (fe_block_combine, engine "tc";
+Table 1 "op1" with several output blocks, the restart product V Y of Section 3.1) against the
+oracle's MvTimesMatAddMv, and of the solver with tensor-core restart products against the
+oracle's Block Krylov-Schur.
+
+Bounds: the stated worst case |err| <= 2^-49 K max_c|V[r][c]| max_c|Y[c][q]| + 2^-52 |ref|
+(+ 2^-1022: results below the normal range flush to zero),
+and the FP64 block-operation tolerance 1e-13 (|V| |Y|) on N(0,1) data; integer data whose
+products fit in 53 bits are reproduced exactly.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import paper_1602_01421_gb300 as fe
+from oracle import bks, blockops
+from tests.gpu_util import to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _flat(Vb):
+    """(nv, n, bv) blocks -> the n x (nv*bv) matrix whose column j*bv + p is block j's column p."""
+    nv, n, bv = Vb.shape
+    return Vb.transpose(1, 0, 2).reshape(n, nv * bv)
+
+
+def _run(Vh, Yh, nout, engine="tc"):
+    V = to_dev(Vh)
+    Y = to_dev(Yh)
+    out = fe.block_combine(V, Y, nout, engine=engine)
+    torch().cuda.synchronize()
+    return _flat(out.cpu().numpy())
+
+
+def _check(Vh, Yh, got):
+    AA = _flat(Vh)
+    ref = blockops.mv_times_mat_add_mv(1.0, AA, Yh, 0.0, np.zeros((AA.shape[0], Yh.shape[1])))
+    K = AA.shape[1]
+    err = np.abs(got - ref)
+    # (results below the normal range, 2^-1022, flush to zero)
+    stated = (2.0 ** -49 * K * np.abs(AA).max(axis=1)[:, None] * np.abs(Yh).max(axis=0)[None, :]
+              + 2.0 ** -52 * np.abs(ref) + 2.0 ** -1022)
+    assert (err <= stated).all(), f"stated bound: worst {np.max(err - stated):.3e}"
+    return err, np.abs(AA) @ np.abs(Yh)
+
+
+SHAPES = [  # (n, nv, bv, nout)
+    (1, 8, 4, 5), (127, 8, 4, 5), (128, 8, 4, 5), (129, 8, 4, 2), (1000, 8, 4, 5),
+    (65537, 8, 4, 5), (4099, 16, 4, 8), (3001, 1, 1, 1), (2048, 3, 2, 7), (777, 32, 1, 32),
+    (5000, 8, 8, 4), (300, 4, 16, 2), (257, 2, 16, 1), (40000, 9, 4, 3), (1025, 5, 1, 13)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tc_combine_matches_oracle(shape):
+    """N(0,1) blocks: per entry within 1e-13 (|V||Y|) and within the stated bound; K up to 64
+    (two 32-wide accumulator sets), N up to 32, ragged last 128-row tiles."""
+    n, nv, bv, nout = shape
+    rng = np.random.default_rng(n + 7 * nv + bv)
+    Vh = rng.standard_normal((nv, n, bv))
+    Yh = rng.standard_normal((nv * bv, nout * bv))
+    got = _run(Vh, Yh, nout)
+    err, absprod = _check(Vh, Yh, got)
+    assert (err <= 1e-13 * absprod).all()
+
+
+def test_tc_combine_integers_exact():
+    """Integer entries (|x| <= 1000): every product sum fits in 53 bits, and the split products
+    are exact, so the result equals the integer product bit for bit."""
+    rng = np.random.default_rng(5)
+    n, nv, bv, nout = 10007, 8, 4, 5
+    Vi = rng.integers(-1000, 1001, (nv, n, bv))
+    Yi = rng.integers(-1000, 1001, (nv * bv, nout * bv))
+    got = _run(Vi.astype(np.float64), Yi.astype(np.float64), nout)
+    exact = _flat(Vi) @ Yi
+    assert np.array_equal(got, exact.astype(np.float64))
+
+
+def test_tc_combine_scales_and_special_rows():
+    """Rows of very different scales (1e-300 .. 1e300), rows with one large and many tiny
+    entries, zero rows, signed zeros and powers of two, against the stated bound."""
+    rng = np.random.default_rng(9)
+    n, nv, bv, nout = 4096, 8, 4, 5
+    Vh = rng.standard_normal((nv, n, bv))
+    scale = 10.0 ** rng.uniform(-300, 300, n)
+    Vh *= scale[None, :, None]
+    Vh[:, 10, :] = 0.0                       # zero row
+    Vh[:, 11, :] = -0.0
+    Vh[:, 12, :] = 2.0 ** rng.integers(-60, 60, (nv, bv))
+    Vh[:, 13, :] = 1e-30
+    Vh[0, 13, 0] = 1e30                      # one large entry, the rest 60 orders below
+    Yh = rng.standard_normal((nv * bv, nout * bv))
+    Yh[:, 3] *= 1e-200                       # a tiny column
+    Yh[5, :] = 0.0
+    got = _run(Vh, Yh, nout)
+    _check(Vh, Yh, got)
+    assert np.all(got[10] == 0.0) and np.all(got[11] == 0.0)
+
+
+def test_tc_and_fma_engines_agree():
+    rng = np.random.default_rng(11)
+    n, nv, bv, nout = 100003, 8, 4, 5
+    Vh = rng.standard_normal((nv, n, bv))
+    Yh = rng.standard_normal((nv * bv, nout * bv))
+    a = _run(Vh, Yh, nout, "tc")
+    b = _run(Vh, Yh, nout, "fma")
+    c = _run(Vh, Yh, nout, "auto")
+    assert np.array_equal(a, c)
+    absprod = np.abs(_flat(Vh)) @ np.abs(Yh)
+    assert (np.abs(a - b) <= 2e-13 * absprod).all()
+
+
+def test_tc_engine_rejects_unsupported():
+    t = torch()
+    V = t.zeros((17, 64, 4), dtype=t.float64, device="cuda")     # K = 68 > 64
+    Y = t.zeros((68, 4), dtype=t.float64, device="cuda")
+    with pytest.raises(fe.FeError):
+        fe.block_combine(V, Y, 1, engine="tc")
+    fe.block_combine(V, Y, 1, engine="auto")                      # FMA fallback
+    V32 = t.zeros((2, 64, 4), dtype=t.float32, device="cuda")
+    with pytest.raises(fe.FeError):
+        fe.block_combine(V32, t.zeros((8, 4), dtype=t.float64, device="cuda"), 1, engine="tc")
+
+
+@pytest.mark.parametrize("name,nev,b,nb", [("rmat14", 8, 4, 8), ("rmat12", 6, 8, 8),
+                                           ("er3000", 4, 2, 10)])
+def test_eigs_tensor_core_restarts_match_oracle(name, nev, b, nb):
+    """The FP64 solve with tensor-core restart / Ritz products (engine tc) against the oracle's
+    Block Krylov-Schur and against the FMA engine: eigenvalues within 1e-8 relative, explicit
+    residuals within tol * |theta_1|."""
+    g = {"rmat14": lambda: graphgen.rmat(14, seed=1), "rmat12": lambda: graphgen.rmat(12, seed=4),
+         "er3000": lambda: graphgen.erdos_renyi(3000, 10.0, seed=2)}[name]()
+    want = bks.block_krylov_schur(g.rowptr, g.colidx, nev, b, nb, 1e-8, "LM", seed=1,
+                                  max_restarts=2000).evals
+    with fe.Csr.from_graph(g) as h:
+        ev_tc, X, st = fe.eigs(h, nev, b, nb, 1e-8, "LM", seed=1, engine="tc", max_restarts=2000)
+        ev_f, _, st_f = fe.eigs(h, nev, b, nb, 1e-8, "LM", seed=1, engine="fma", max_restarts=2000)
+    assert st["converged"] and st_f["converged"]
+    np.testing.assert_allclose(ev_tc, want, rtol=1e-8)
+    np.testing.assert_allclose(ev_tc, ev_f, rtol=1e-8)
+    Xh = X.cpu().numpy()
+    from oracle import core
+    R = core.spmm(g.rowptr, g.colidx, Xh) - Xh * ev_tc
+    assert (np.linalg.norm(R, axis=0) <= 1e-8 * np.abs(ev_tc).max()).all()
