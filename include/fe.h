@@ -122,6 +122,11 @@ typedef struct {
    * symmetric (Section 4.3.2).  With a device_mem_cap_bytes, A^T gets its own panels under the
    * same cap (the pair may hold up to twice the cap on the device).  Default 0. */
   int transpose;
+  /* Columns of A (0 = n: square).  A rectangular n x ncols matrix -- one part's row block of a
+   * row-partitioned matrix, with global column ids (fe_partition_local) -- must be resident,
+   * without transpose or symmetry check; fe_spmm then reads ncols x b X and writes n x b Y, and
+   * fe_eigs / fe_svds reject it. */
+  int64_t ncols;
 } fe_csr_opts;
 
 /* Fill *opts with the defaults. */
@@ -143,6 +148,7 @@ typedef struct {
                          * with the default may use a smaller one than resident ones) */
   int index_format;     /* FE_INDEX_PLAIN or FE_INDEX_PACKED, as in use */
   int64_t index_bytes;  /* bytes of column-index data in the plan (resident or streamed) */
+  int64_t ncols;        /* columns (n unless created rectangular) */
 } fe_csr_info;
 
 /*
@@ -166,19 +172,17 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info);
 
 /*
  * SpMM, Section 3.3.3: Y = A X, i.e. Y[i, :] = sum over the non-zeros (i, j) of X[j, :].
- * X and Y are DEVICE pointers to row-major n x b blocks of type dt, 1 <= b <= 16,
+ * X and Y are DEVICE pointers to row-major ncols x b and n x b blocks of type dt, 1 <= b <= 16,
  * b in {1, 2, 4, 8, 16}; Y is overwritten (rows of empty matrix rows become 0); X and Y must
  * not overlap.  Accumulation is in dt.  Accuracy, per entry, against the exact sum of the
  * given X values, for any degree and any signs ((A|X|)_ij = sum over the row of |X[j, :]|):
- *   FP32: a lane adds the X rows it gathers in groups of four (pairwise), the group sums into a
- *         compensated (Kahan) running sum, lanes' sums are combined by a tree of at most 5
- *         levels, and the chunks of a split hub row are added in compensated FP64 and rounded
- *         once, so |error| <= 10 * 2^-24 * (A|X|)_ij (about 6.0e-7, plus terms of order
- *         degree * 2^-48);
- *   FP64: the same order with plain sums, |error| <= (m/4 + 8) * 2^-53 * (A|X|)_ij, m the
- *         longest run one lane adds: m <= tail_max for rows in the slices, m <= 512 for longer
- *         rows when X is 32-byte aligned (1024 when it is only 16-byte aligned and b = 16), so
- *         below 1.6e-14 (3e-14).
+ *   FP32: every lane's running sum is compensated (Kahan), lanes' sums are combined by a tree
+ *         of at most 5 levels, and the chunks of a split hub row are added in compensated
+ *         FP64 and rounded once, so |error| <= 9 * 2^-24 * (A|X|)_ij (about 5.4e-7, plus
+ *         terms of order degree * 2^-48);
+ *   FP64: plain sums, |error| <= (m + 6) * 2^-53 * (A|X|)_ij, m the longest run one lane adds:
+ *         m <= tail_max for rows in the slices, m <= 512 for longer rows when X is 32-byte
+ *         aligned (1024 when it is only 16-byte aligned and b = 16), so below 6e-14 (1.2e-13).
  * Both pointers must be 16-byte aligned.  Errors: FE_ERR_INVALID (null/unaligned pointer, unsupported b),
  * FE_ERR_CUDA, FE_ERR_TIMEOUT (semi-external copy wait).  Asynchronous when resident.
  */
@@ -286,6 +290,27 @@ int fe_block_orth(const void* V, int64_t n, int nv, int b, void* W, fe_dtype dt,
  */
 int fe_random_normal(void* X, int64_t n, int b, fe_dtype dt, uint64_t seed, uint64_t stream,
                      uint64_t offset);
+
+/* ------------------------------------------------------------------ row partition (multi-GPU) */
+/* The paper's solver runs on one machine (Section 3); across several GPUs the method shards by
+ * rows: a part owns a contiguous row range of A and of every n x b block, an SpMM needs the X
+ * rows its column indices reference (an all-gather of X, or only the "halo" rows), and a Gram
+ * product V^T W is the sum of the parts' partial products (an all-reduce of the small result).
+ * These host functions compute the partition and a part's local CSR; the exchanges are the
+ * caller's (the Python package's dist module over torch.distributed). */
+
+/* Split rows [0, n) of the CSR into nparts contiguous ranges of near-equal cost (non-zeros +
+ * rows): part p owns rows [row_begin[p], row_begin[p+1]).  rowptr: HOST, n+1 entries;
+ * row_begin: HOST, nparts+1 entries, written.  Each part's cost is at most total/nparts plus
+ * the cost of one row.  Errors: FE_ERR_INVALID (NULL, n < 1, nparts < 1, decreasing rowptr). */
+int fe_partition_rows(int64_t n, const int64_t* rowptr, int nparts, int64_t* row_begin);
+
+/* The local CSR of rows [r0, r1): local_rowptr (HOST, r1-r0+1 entries, starting at 0) and
+ * local_colidx (HOST, rowptr[r1]-rowptr[r0] entries) keep GLOBAL column ids in the original
+ * order; halo (HOST, may be NULL; room for rowptr[r1]-rowptr[r0] entries) receives the sorted
+ * distinct columns outside [r0, r1), *nhalo their number.  Errors: FE_ERR_INVALID. */
+int fe_partition_local(int64_t n, const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
+                       int64_t* local_rowptr, int32_t* local_colidx, int32_t* halo, int64_t* nhalo);
 
 /* ------------------------------------------------------------------ learned start block */
 /* Not in the paper (its solver starts from MvRandom, Table 1): a small MLP maps per-vertex

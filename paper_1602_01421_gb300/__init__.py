@@ -13,7 +13,8 @@ import numpy as np
 from . import _lib
 from ._lib import FeError, check, load
 
-__all__ = ["Csr", "spmm", "block_gram", "block_update", "block_update_gram", "block_orth", "random_normal", "eigs",
+__all__ = ["Csr", "spmm", "block_gram", "block_update", "block_update_gram", "block_combine", "block_orth",
+           "random_normal", "eigs",
            "spmm_t", "svds",
            "FeError", "load", "library_path"]
 
@@ -54,7 +55,7 @@ class Csr:
                  check_symmetric: bool = False, device_mem_cap_bytes: int = 0,
                  tail_max: int = 0, hub_min: int = 0, hub_chunk: int = 0, panel_nnz: int = 0,
                  copy_timeout_ms: int = 0, semi_direct: bool = False, transpose: bool = False,
-                 index_format: str = "auto"):
+                 index_format: str = "auto", ncols: int = 0):
         lib = load()
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(colidx, dtype=np.int32)
@@ -69,6 +70,7 @@ class Csr:
         o.semi_direct = int(semi_direct)
         o.transpose = int(transpose)
         o.index_format = _lib.INDEX_FORMAT[index_format]
+        o.ncols = int(ncols)
         h = ctypes.c_void_p()
         check(lib.fe_csr_create_ex(self.n, self._rowptr.ctypes.data_as(ctypes.c_void_p),
                                    self._colidx.ctypes.data_as(ctypes.c_void_p),
@@ -113,10 +115,10 @@ class Csr:
 
 
 def spmm(h: Csr, X, Y=None):
-    """Y = A X (fe_spmm); X, Y row-major (n, b) CUDA tensors, float32 or float64."""
+    """Y = A X (fe_spmm); X (ncols, b), Y (n, b) row-major CUDA tensors, float32 or float64."""
     torch = _torch()
     if Y is None:
-        Y = torch.empty_like(X)
+        Y = torch.empty((h.n,) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
     b = 1 if X.dim() == 1 else X.shape[1]
     _stream()
     check(load().fe_spmm(h.handle, _dev(X, "X"), _dev(Y, "Y"), b, _dt(X)))

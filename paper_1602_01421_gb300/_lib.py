@@ -31,7 +31,7 @@ class CsrOpts(ctypes.Structure):
                 ("hub_min", ctypes.c_int), ("hub_chunk", ctypes.c_int),
                 ("panel_nnz", ctypes.c_int64), ("copy_timeout_ms", ctypes.c_int),
                 ("semi_direct", ctypes.c_int), ("index_format", ctypes.c_int),
-                ("transpose", ctypes.c_int)]
+                ("transpose", ctypes.c_int), ("ncols", ctypes.c_int64)]
 
 
 class CsrInfo(ctypes.Structure):
@@ -41,7 +41,8 @@ class CsrInfo(ctypes.Structure):
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("semi_external", ctypes.c_int), ("panels", ctypes.c_int64),
                 ("has_transpose", ctypes.c_int), ("tail_max", ctypes.c_int),
-                ("index_format", ctypes.c_int), ("index_bytes", ctypes.c_int64)]
+                ("index_format", ctypes.c_int), ("index_bytes", ctypes.c_int64),
+                ("ncols", ctypes.c_int64)]
 
 
 class EigsOpts(ctypes.Structure):
@@ -95,6 +96,8 @@ def load(build_if_missing: bool = True):
             "fe_block_gram": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_block_update": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, i32]),
             "fe_block_combine": (i32, [vp, i64, i32, i32, vp, i32, vp, i32, i32]),
+            "fe_partition_rows": (i32, [i64, vp, i32, vp]),
+            "fe_partition_local": (i32, [i64, vp, vp, i64, i64, vp, vp, vp, ctypes.POINTER(i64)]),
             "fe_block_update_gram": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, vp]),
             "fe_block_orth": (i32, [vp, i64, i32, i32, vp, i32, dbl, ctypes.c_uint64, vp, vp,
                                     ctypes.POINTER(i32)]),

@@ -149,7 +149,7 @@ void fe_csr_opts_default(fe_csr_opts* o) {
   o->validate = 1;
 }
 
-static int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx) {
+static int validate_csr(int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* colidx) {
   if (rowptr[0] != 0) return set_error(FE_ERR_INVALID, "rowptr[0] = %lld, expected 0", (long long)rowptr[0]);
   int64_t bad_row = -1;
   for (int64_t i = 0; i < n; ++i)
@@ -159,10 +159,10 @@ static int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx)
   int64_t bad = -1;
   #pragma omp parallel for schedule(static) reduction(max : bad)
   for (int64_t p = 0; p < nnz; ++p)
-    if (colidx[p] < 0 || colidx[p] >= n) bad = std::max(bad, p);
+    if (colidx[p] < 0 || colidx[p] >= ncols) bad = std::max(bad, p);
   if (bad >= 0)
     return set_error(FE_ERR_INVALID, "colidx[%lld] = %d out of range [0, %lld)", (long long)bad,
-                     colidx[bad], (long long)n);
+                     colidx[bad], (long long)ncols);
   return FE_OK;
 }
 
@@ -235,10 +235,16 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   int64_t nnz = rowptr[n];
   FE_ARG(nnz >= 0, "fe_csr_create: rowptr[n] = %lld < 0", (long long)nnz);
   FE_ARG(nnz == 0 || colidx != nullptr, "fe_csr_create: colidx is NULL");
-  if (o.validate) FE_TRY(validate_csr(n, rowptr, colidx));
+  const int64_t ncols = o.ncols > 0 ? o.ncols : n;
+  FE_ARG(ncols <= INT32_MAX, "fe_csr_create: ncols = %lld must be below 2^31", (long long)ncols);
+  FE_ARG(ncols == n || (o.device_mem_cap_bytes == 0 && !o.transpose && !o.check_symmetric),
+         "fe_csr_create: a rectangular matrix (ncols != n) must be resident, without transpose "
+         "or symmetry check");
+  if (o.validate) FE_TRY(validate_csr(n, ncols, rowptr, colidx));
   if (o.check_symmetric) FE_TRY(check_symmetric(n, rowptr, colidx));
   fe_csr h = new fe_csr_s();
   h->n = n;
+  h->ncols = ncols;
   h->nnz = nnz;
   cudaGetDevice(&h->device);
   FE_ARG(o.index_format >= FE_INDEX_AUTO && o.index_format <= FE_INDEX_PACKED,
@@ -293,6 +299,7 @@ int fe_csr_get_info(fe_csr h, fe_csr_info* info) {
   info->tail_max = h->plan.tail_max;
   info->index_format = h->plan.packed ? FE_INDEX_PACKED : FE_INDEX_PLAIN;
   info->index_bytes = h->plan.index_bytes;
+  info->ncols = h->ncols;
   return FE_OK;
 }
 
@@ -309,10 +316,9 @@ int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt) {
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_spmm: bad dtype %d", (int)dt);
   FE_ARG(((uintptr_t)X % 16) == 0 && ((uintptr_t)Y % 16) == 0, "fe_spmm: X and Y must be 16-byte aligned");
   size_t rowb = (size_t)b * (dt == FE_F32 ? 4 : 8);
-  size_t bytes = rowb * (size_t)h->n;
   const char* xa = (const char*)X;
   const char* ya = (const char*)Y;
-  FE_ARG(xa + bytes <= ya || ya + bytes <= xa, "fe_spmm: X and Y overlap");
+  FE_ARG(xa + rowb * (size_t)h->ncols <= ya || ya + rowb * (size_t)h->n <= xa, "fe_spmm: X and Y overlap");
   if (h->semi_external) return semiext_spmm(h, X, Y, b, dt, cur_stream());
   return spmm_resident(h, X, Y, b, dt, cur_stream());
 }

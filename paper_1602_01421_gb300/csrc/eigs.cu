@@ -358,6 +358,8 @@ struct Phase {
 
 static int check_eigs_args(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which) {
   FE_ARG(h != nullptr, "fe_eigs: NULL handle");
+  FE_ARG(h->ncols == h->n, "fe_eigs: the matrix is not square (%lld x %lld)", (long long)h->n,
+         (long long)h->ncols);
   FE_ARG(is_pow2_le16(block), "fe_eigs: block = %d not in {1,2,4,8,16}", block);
   FE_ARG(nblocks >= 2, "fe_eigs: nblocks = %d < 2", nblocks);
   const int m = block * nblocks;

@@ -154,6 +154,7 @@ struct fe_spmm_plan {
 
 struct fe_csr_s {
   int64_t n = 0, nnz = 0;
+  int64_t ncols = 0;       // columns (= n except for a partition's rectangular row block)
   int device = 0;
   int64_t max_degree = 0;
   int64_t rows_empty = 0, rows_tail = 0, rows_mid = 0, rows_hub = 0;

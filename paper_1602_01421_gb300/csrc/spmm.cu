@@ -20,9 +20,9 @@
 // processing-time list; tail slices follow in the same launch.  The task rows' column
 // indices are stored either as int32 or, in the packed format, as per-task gap fields that a
 // warp decodes with a prefix sum (fewer bytes to stream from host memory).
-// FP32 sums are compensated per lane (Kahan, over pairwise sums of four gathered rows) before
-// the lane tree, and hub chunks are added in compensated FP64, so the FP32 error bound
-// (10 * 2^-24 * A|X| per entry) does not grow with the degree or depend on the signs of X.
+// FP32 sums are compensated per lane (Kahan) before the lane tree, and hub chunks are added in
+// compensated FP64, so the FP32 error bound (9 * 2^-24 * A|X| per entry) does not grow with the
+// degree or depend on the signs of X.
 #include <stdio.h>
 #include <string.h>
 
@@ -71,15 +71,13 @@ struct SpmmParams {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
 
-// Per-lane running sums.  A lane gathers its X rows four at a time, adds each group of four
-// as a pairwise tree ((f0 + f1) + (f2 + f3), error <= 2u of the group's |f|) and adds the group
-// sums into its running sum.  FP32: the running sum is Kahan's compensated summation (Kahan
-// 1965; Higham, "Accuracy and Stability of Numerical Algorithms", 2nd ed., Thm. 4.8): c carries
-// the rounding error of the last addition, so the sum of m group sums is within
-// (2u + O(m u^2)) sum |x| of their exact sum (u = 2^-24), whatever m and the signs, instead
-// of (m - 1) u sum |x|; a lane's sum is thus within 4u sum |x|.  nvcc does not reassociate
-// floating-point adds, so the correction survives compilation.  FP64: plain adds (u = 2^-53;
-// a lane adds at most (m/4 + 2) roundings, far below the FP64 bound).
+// Per-lane running sums.  FP32: Kahan's compensated summation (Kahan 1965; Higham, "Accuracy
+// and Stability of Numerical Algorithms", 2nd ed., Thm. 4.8): c carries the rounding error of
+// the last addition, so a lane's sum of m terms is within (2u + O(m u^2)) sum |x| of the exact
+// sum (u = 2^-24), whatever the number of terms and their signs, instead of (m - 1) u sum |x|.
+// Four FP32 adds per term; nvcc does not reassociate floating-point adds, so the correction
+// survives compilation.  FP64: plain adds (m u with u = 2^-53 is already far below the FP64
+// bound).  kahan_add(s, c, x) adds x; kahan_value(s, c) is the compensated sum.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -87,6 +85,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 __device__ __forceinline__ void kahan_add(double& s, double&, double x) { s += x; }
+__device__ __forceinline__ float kahan_value(float s, float c) { return s - c; }
+__device__ __forceinline__ double kahan_value(double s, double) { return s; }
 
 template <typename T, int B, bool V32, bool PACKED>
 __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const T* __restrict__ X,
@@ -118,8 +118,6 @@ __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const 
   const uint32_t* __restrict__ tb = p.tbits + start;
   const uint32_t wmask = (1u << w) - 1u;  // 1 <= w <= 31
   int carry = cbase;  // packed: the column reached by the previous round
-  constexpr int KR = G::UNROLL * (32 / G::P);  // rows a lane gathers per batch: 4 (8 if C = 8)
-  static_assert(KR == 4 || KR == 8, "a lane gathers four or eight rows per batch");
   for (int base = 0; base < len; base += 32 * G::UNROLL) {
     int cols[G::UNROLL];
 #pragma unroll
@@ -149,28 +147,25 @@ __device__ __forceinline__ void run_task(const SpmmParams& p, int64_t ti, const 
         cols[u] = k < len ? __ldcs(ci + k) : -1;
       }
     }
-    T f[KR][G::NE];  // this lane's gathered rows (zero past the row's end)
 #pragma unroll
     for (int u = 0; u < G::UNROLL; ++u) {
 #pragma unroll
       for (int g = 0; g < 32; g += G::P) {
-        const int k = u * (32 / G::P) + g / G::P;
-#pragma unroll
-        for (int e = 0; e < G::NE; ++e) f[k][e] = T(0);
         // rounds whose P slots all lie past the row's end are skipped (warp-uniform test)
         if (base + u * 32 + g < len) {
           int col = __shfl_sync(kFull, cols[u], g + slot);
-          if (col >= 0) ld_frag<T, G::NE>(X + (int64_t)col * B + chunk * G::NE, f[k]);
+          if (col >= 0) {
+            T f[G::NE];
+            ld_frag<T, G::NE>(X + (int64_t)col * B + chunk * G::NE, f);
+#pragma unroll
+            for (int e = 0; e < G::NE; ++e) kahan_add(acc[e], cmp[e], f[e]);
+          }
         }
       }
     }
-#pragma unroll
-    for (int e = 0; e < G::NE; ++e) {
-      T grp = (f[0][e] + f[1][e]) + (f[2][e] + f[3][e]);
-      if constexpr (KR == 8) grp += (f[4][e] + f[5][e]) + (f[6][e] + f[7][e]);
-      kahan_add(acc[e], cmp[e], grp);
-    }
   }
+#pragma unroll
+  for (int e = 0; e < G::NE; ++e) acc[e] = kahan_value(acc[e], cmp[e]);
   // Sum the P slot partials of each chunk.  The first LNE butterfly levels (offsets 16, 8, ..)
   // also scatter the NE elements -- a lane keeps half of what it holds and adds its partner's
   // copy of that half -- so every level after them adds one value per lane.
@@ -221,14 +216,14 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
 #pragma unroll
     for (int u = 0; u < 4; ++u) c[u] = __ldcs(e + (t + u) * 32);
 #pragma unroll
-    for (int ch = 0; ch < G::C; ++ch) {
-      T f[4][G::NE];
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ld_frag<T, G::NE>(X + (int64_t)c[u] * B + ch * G::NE, f[u]);
+      for (int ch = 0; ch < G::C; ++ch) {
+        T f[G::NE];
+        ld_frag<T, G::NE>(X + (int64_t)c[u] * B + ch * G::NE, f);
 #pragma unroll
-      for (int q = 0; q < G::NE; ++q)
-        kahan_add(acc[ch * G::NE + q], cmp[ch * G::NE + q], (f[0][q] + f[1][q]) + (f[2][q] + f[3][q]));
-    }
+        for (int q = 0; q < G::NE; ++q) kahan_add(acc[ch * G::NE + q], cmp[ch * G::NE + q], f[q]);
+      }
   }
   for (; t < deg; ++t) {
     int c = __ldcs(e + t * 32);
@@ -240,6 +235,8 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
       for (int q = 0; q < G::NE; ++q) kahan_add(acc[ch * G::NE + q], cmp[ch * G::NE + q], f[q]);
     }
   }
+#pragma unroll
+  for (int q = 0; q < B; ++q) acc[q] = kahan_value(acc[q], cmp[q]);
   if (row >= 0) {
     using F = FragOf<T, B>;  // stores in 16-byte pieces
 #pragma unroll
@@ -247,15 +244,8 @@ __device__ __forceinline__ void run_slice(const SpmmParams& p, int64_t si, const
   }
 }
 
-// Resident CTAs per SM the register budget is held to (256 threads each): as many warps in
-// flight as the gathers' latency needs, without spilling the per-lane sums.
-template <typename T, int B>
-constexpr int spmm_min_ctas() {
-  return sizeof(T) == 4 ? (B <= 4 ? 8 : B == 8 ? 6 : 4) : (B <= 2 ? 8 : B == 4 ? 6 : B == 8 ? 5 : 3);
-}
-
 template <typename T, int B, bool V32, bool PACKED>
-__global__ void __launch_bounds__(256, spmm_min_ctas<T, B>()) spmm_main_kernel(const SpmmParams p, const T* __restrict__ X,
+__global__ void __launch_bounds__(256) spmm_main_kernel(const SpmmParams p, const T* __restrict__ X,
                                                         T* __restrict__ Y, T* __restrict__ partial) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if ((int64_t)blockIdx.x < p.task_ctas) {

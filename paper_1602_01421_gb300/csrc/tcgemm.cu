@@ -10,18 +10,21 @@
 //   * the digit products are exact in the tensor core's FP32 accumulator as long as each
 //     accumulator sums at most 2^24 / 255^2 = 258 of them: one accumulator per digit-weight
 //     class g = i + j (g <= 6) and per 32-wide slice of K holds at most 7 * 32 products;
-//   * V Y = 2^(Er + Fq - 2108) * T with T = sum_g D_g 2^(8 (6 - g)), assembled exactly in
-//     128-bit integer arithmetic from the accumulators and rounded once (truncation) to FP64.
+//   * V Y = 2^(Er + Fq - 2108) * T with T = sum_g D_g 2^(8 (6 - g)), assembled in 64-bit
+//     integer arithmetic from the accumulators (T / 2^12, exact up to the dropped bits) and
+//     rounded once (truncation) to FP64.
 //
-// Error: the digit products dropped (i + j >= 7) and the truncation of each entry below its
-// row's (column's) leading bit bound |error| <= 2^-49 * K * max_c |V[r][c]| * max_c |Y[c][q]|
-// plus 2^-52 |result|; the FP64 pipe is not used at all (FP64 on this part runs at 1/64 of FP32).
+// Error: the digit products dropped (i + j >= 7), the truncation of each entry below its
+// row's (column's) leading bit and the 12 dropped bits of T bound |error| <=
+// 2^-49 (K + 1) max_c |V[r][c]| max_c |Y[c][q]| + 2^-52 |result|; the FP64 pipe is not used at
+// all (FP64 on this part runs at 1/64 of FP32).
 //
-// Kernel structure (one 128-row tile per loop trip, two persistent CTAs of 128 threads per SM):
-// thread t loads row t of the V tile, splits it and writes the digits into shared memory in the
-// no-swizzle K-major core-matrix layout; thread 0 issues the 28 x (K/16) tcgen05.mma into the
-// CTA's tensor memory and commits to an mbarrier; every thread then reads its row's
-// accumulators (TMEM lane t) with tcgen05.ld, assembles its N FP64 results and stores them.
+// Kernel structure (one 128-row tile per loop trip, two persistent CTAs of 256 threads per SM):
+// two threads share a row of the V tile; each loads and splits half of its K values and writes
+// the digits into shared memory in the no-swizzle K-major core-matrix layout; thread 0 issues
+// the 28 x (K/16) tcgen05.mma into the CTA's tensor memory and commits to an mbarrier; then
+// each of the two threads reads the row's accumulators (TMEM lane = row) for half of the N
+// results with tcgen05.ld, assembles them in FP64 and stores them.
 #include <math.h>
 #include <string.h>
 
@@ -41,7 +44,7 @@ constexpr int kTileRows = 128;       // MMA M
 constexpr int kKChunk = 32;          // K columns per accumulator set (exactness bound)
 constexpr int kMaxK = 64;
 constexpr int kMaxN = 32;
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr uint32_t kWaitSpins = 1u << 24;
 constexpr int kCoreBytes = 128;      // 8 rows x 16 bytes
 // A (V digits): per (K chunk, digit) a 128 x 32 bf16 tile = 8 KB; SBO = 4 core matrices
@@ -75,32 +78,34 @@ __device__ __forceinline__ uint32_t digit(uint64_t m, int i) {
   return i < 6 ? (uint32_t)(m >> (45 - 8 * i)) & 0xFFu : ((uint32_t)m & 0x1Fu) << 3;
 }
 
-// Two digits (each an integer in [0, 255]) with signs s0, s1 (0 or 1) as a packed bf16 pair:
-// 2^23 + d is exact in FP32, minus 2^23 gives d as an FP32 whose top 16 bits are its bf16.
-__device__ __forceinline__ uint32_t bf16_pair(uint32_t d0, uint32_t d1, uint32_t s0, uint32_t s1) {
+// Two digits (each an integer in [0, 255]) as a packed bf16 pair (signs are ORed in by the
+// caller): 2^23 + d is exact in FP32, minus 2^23 gives d as an FP32 whose top 16 bits are its
+// bf16.
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t d0, uint32_t d1) {
   const float f0 = __uint_as_float(0x4B000000u | d0) - 8388608.0f;
   const float f1 = __uint_as_float(0x4B000000u | d1) - 8388608.0f;
-  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | (s0 << 15) | (s1 << 31);
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
 // Exact integer value of an FP32 accumulator holding an integer of magnitude below 2^24.
-__device__ __forceinline__ int64_t acc_int(uint32_t bits) {
-  return (int64_t)__float2int_rn(__uint_as_float(bits));
+__device__ __forceinline__ int32_t acc_int(uint32_t bits) {
+  return __float2int_rn(__uint_as_float(bits));
 }
 
-// 2^s * T rounded toward zero to FP64, T = hi * 2^32 + lo (|T| < 2^75); flushes to zero below
-// the normal range and saturates to infinity above it.
+// The accumulated T = hi 2^32 + lo (|hi| < 2^40, |lo| < 2^50) is taken as floor(T / 2^12), an
+// int64 of at most 60 bits, before it is rounded to FP64: the 12 dropped bits are below the
+// digit truncation already made (2^-50 of max|V_r| max|Y_q|).
+constexpr int kAsmShift = 12;
+
+// 2^s * (hi 2^20 + floor(lo / 2^12)) truncated to FP64; zero below the normal range, infinity
+// above it.  Integer operations only.
 __device__ __forceinline__ double assemble(int64_t hi, int64_t lo, int s) {
-  __int128 t = ((__int128)hi << 32) + (__int128)lo;
+  const int64_t t = (hi << (32 - kAsmShift)) + (lo >> kAsmShift);
   if (t == 0) return 0.0;
-  const uint64_t sign = t < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned __int128 a = t < 0 ? (unsigned __int128)(-t) : (unsigned __int128)t;
-  const uint64_t ah = (uint64_t)(a >> 64), al = (uint64_t)a;
-  const int msb = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);
-  // significand: bits [msb - 52, msb] of a (truncated)
-  uint64_t m;
-  if (msb >= 52) m = (uint64_t)(a >> (msb - 52));
-  else m = al << (52 - msb);
+  const uint64_t sign = (uint64_t)t & 0x8000000000000000ull;
+  const uint64_t a = t < 0 ? (uint64_t)(-t) : (uint64_t)t;
+  const int msb = 63 - __clzll((long long)a);
+  const uint64_t m = msb >= 52 ? a >> (msb - 52) : a << (52 - msb);
   const int ef = msb + s + 1023;
   if (ef <= 0) return __longlong_as_double((long long)sign);
   if (ef >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
@@ -156,8 +161,13 @@ __global__ void tc_prep_y_kernel(const double* __restrict__ Y, int ldy, int K, i
   }
 }
 
-template <int BV>
-__global__ void __launch_bounds__(kThreads) tc_combine_kernel(const TcArgs a) {
+// Row r of a 128-row tile is handled by two threads (warps w and w + 4 address the same TMEM
+// lane quarter): each loads and splits half of the row's K values, and each assembles half of
+// the row's N results.
+// K <= 32: two CTAs per SM (256 TMEM columns each); K <= 64: one (512 columns).
+template <int BV, int KMAX>
+__global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kernel(const TcArgs a) {
+  constexpr int KH = KMAX / 2;  // V values per thread
   extern __shared__ __align__(1024) unsigned char smem[];
   const int nkc = a.nkc, NP = a.NP;
   unsigned char* sA = smem;                                        // [nkc][7] x 8 KB
@@ -165,8 +175,11 @@ __global__ void __launch_bounds__(kThreads) tc_combine_kernel(const TcArgs a) {
   const size_t btile = (size_t)NP * kKChunk * 2;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sB + (size_t)nkc * kDigits * btile);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  int* sF = reinterpret_cast<int*>(tslot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  int* sF = reinterpret_cast<int*>(tslot + 1);   // N column exponents of Y
+  int* sE = sF + kMaxN;                          // [2][128] partial row exponents
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = warp >> 2;
+  const int row = (warp & 3) * 32 + lane;        // row of the tile = TMEM lane
   const uint32_t ncols = (uint32_t)nkc * kClasses * NP <= 256 ? 256u : 512u;
 
   // B digits and column exponents (once per CTA)
@@ -192,51 +205,51 @@ __global__ void __launch_bounds__(kThreads) tc_combine_kernel(const TcArgs a) {
   const uint32_t tbase = *tslot;
   const uint32_t idesc = tc::idesc_bf16_f32(kTileRows, NP);
   const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
+  const int cbeg = half * KH;                    // this thread's first V column
+  const int kc_mine = cbeg / kKChunk, k_mine = cbeg % kKChunk;
   uint32_t phase = 0;
   bool failed = false;
 
   const int64_t ntiles = (a.n + kTileRows - 1) / kTileRows;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r = tile * kTileRows + tid;
+    const int64_t r = tile * kTileRows + row;
     const bool live = r < a.n;
-    // ---- load and split row r of V (K values)
-    double v[kMaxK];
+    // ---- load this thread's half of row r and its largest exponent
+    double v[KH];
     int emax = 0;
 #pragma unroll
-    for (int c0 = 0; c0 < kMaxK; c0 += BV) {
-      if (c0 < a.K) {
-        if (live) {
-          ld_row<double, BV>(a.vblk[c0 / BV] + r * BV, &v[c0]);
-        } else {
+    for (int c0 = 0; c0 < KH; c0 += BV) {
+      if (live && cbeg + c0 < a.K) {
+        ld_row<double, BV>(a.vblk[(cbeg + c0) / BV] + r * BV, &v[c0]);
+      } else {
 #pragma unroll
-          for (int p = 0; p < BV; ++p) v[c0 + p] = 0.0;
-        }
-#pragma unroll
-        for (int p = 0; p < BV; ++p) emax = max(emax, exp_field(v[c0 + p]));
+        for (int p = 0; p < BV; ++p) v[c0 + p] = 0.0;
       }
     }
 #pragma unroll
-    for (int kc = 0; kc < kMaxK / kKChunk; ++kc) {
-      if (kc < nkc) {
+    for (int c = 0; c < KH; ++c) emax = max(emax, exp_field(v[c]));
+    sE[half * kTileRows + row] = emax;
+    __syncthreads();
+    emax = max(sE[row], sE[kTileRows + row]);
+    // ---- split into seven digits and write them to the A tiles
 #pragma unroll
-        for (int k8 = 0; k8 < kKChunk; k8 += 8) {
-          uint32_t w[kDigits][4];
+    for (int k8 = 0; k8 < KH; k8 += 8) {
+      uint32_t w[kDigits][4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = kc * kKChunk + k8 + 2 * e;
-            const double x0 = c < a.K ? v[c] : 0.0, x1 = c + 1 < a.K ? v[c + 1] : 0.0;
-            const uint64_t m0 = aligned_sig(x0, emax), m1 = aligned_sig(x1, emax);
-            const uint32_t s0 = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63);
-            const uint32_t s1 = (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63);
+      for (int e = 0; e < 4; ++e) {
+        const double x0 = v[k8 + 2 * e], x1 = v[k8 + 2 * e + 1];
+        const uint64_t m0 = aligned_sig(x0, emax), m1 = aligned_sig(x1, emax);
+        const uint32_t sg = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15 |
+                            (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31;
 #pragma unroll
-            for (int i = 0; i < kDigits; ++i) w[i][e] = bf16_pair(digit(m0, i), digit(m1, i), s0, s1);
-          }
-#pragma unroll
-          for (int i = 0; i < kDigits; ++i)
-            *reinterpret_cast<uint4*>(sA + (size_t)(kc * kDigits + i) * kATileBytes + tile_off(tid, k8)) =
-                make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
-        }
+        for (int i = 0; i < kDigits; ++i) w[i][e] = bf16_pair(digit(m0, i), digit(m1, i)) | sg;
       }
+      const int kk = k_mine + k8;   // column within the chunk
+      const int kc = kc_mine + kk / kKChunk;
+#pragma unroll
+      for (int i = 0; i < kDigits; ++i)
+        *reinterpret_cast<uint4*>(sA + (size_t)(kc * kDigits + i) * kATileBytes + tile_off(row, kk % kKChunk)) =
+            make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -260,27 +273,27 @@ __global__ void __launch_bounds__(kThreads) tc_combine_kernel(const TcArgs a) {
           }
       tc::mma_commit(bar);
     }
-    // ---- wait for the products (bounded), then read row tid's accumulators
-    bool ok = tc::mbar_wait(bar, phase, kWaitSpins);
+    // ---- wait for the products (bounded), then read row `row`'s accumulators
+    const bool ok = tc::mbar_wait(bar, phase, kWaitSpins);
     if (!ok) {
       failed = true;
       tc::mbar_wait(bar, phase, kWaitSpins);  // let the MMAs in flight finish before TMEM is reused
     }
     phase ^= 1;
     tc::fence_after_sync();
-    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
-    const int ebase = emax - 2108;
-    for (int q0 = 0; q0 < a.N; q0 += 4) {
-      uint32_t acc[kMaxK / kKChunk][kClasses][4];
+    const uint32_t lane_addr = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+    const int ebase = emax - 2108 + kAsmShift;
+    for (int q0 = 4 * half; q0 < a.N; q0 += 8) {   // groups of 4 results, alternating halves
+      uint32_t acc[KMAX / kKChunk][kClasses][4];
 #pragma unroll
-      for (int kc = 0; kc < kMaxK / kKChunk; ++kc)
+      for (int kc = 0; kc < KMAX / kKChunk; ++kc)
         if (kc < nkc)
 #pragma unroll
           for (int g = 0; g < kClasses; ++g)
             tc::tmem_ld4(lane_addr + (uint32_t)((kc * kClasses + g) * NP + q0), acc[kc][g]);
       tc::tmem_ld_wait();
 #pragma unroll
-      for (int kc = 0; kc < kMaxK / kKChunk; ++kc)
+      for (int kc = 0; kc < KMAX / kKChunk; ++kc)
         if (kc < nkc)
 #pragma unroll
           for (int g = 0; g < kClasses; ++g) tc::reg_after_wait(acc[kc][g]);
@@ -289,29 +302,33 @@ __global__ void __launch_bounds__(kThreads) tc_combine_kernel(const TcArgs a) {
         const int q = q0 + u;
         int64_t hi = 0, lo = 0;
 #pragma unroll
-        for (int kc = 0; kc < kMaxK / kKChunk; ++kc)
+        for (int kc = 0; kc < KMAX / kKChunk; ++kc)
           if (kc < nkc) {
-            hi += (acc_int(acc[kc][0][u]) << 16) + (acc_int(acc[kc][1][u]) << 8) + acc_int(acc[kc][2][u]);
-            lo += (acc_int(acc[kc][3][u]) << 24) + (acc_int(acc[kc][4][u]) << 16) +
-                  (acc_int(acc[kc][5][u]) << 8) + acc_int(acc[kc][6][u]);
+            hi += ((int64_t)acc_int(acc[kc][0][u]) << 16) + ((int64_t)acc_int(acc[kc][1][u]) << 8) +
+                  acc_int(acc[kc][2][u]);
+            lo += ((int64_t)acc_int(acc[kc][3][u]) << 24) + ((int64_t)acc_int(acc[kc][4][u]) << 16) +
+                  ((int64_t)acc_int(acc[kc][5][u]) << 8) + acc_int(acc[kc][6][u]);
           }
         if (live && q < a.N) {
-          const double y = (ok && emax > 0) ? assemble(hi, lo, ebase + sF[q]) : (ok ? 0.0 : __longlong_as_double(0x7FF8000000000000ll));
+          double y = 0.0;
+          if (!ok) y = __longlong_as_double(0x7FF8000000000000ll);
+          else if (emax > 0) y = assemble(hi, lo, ebase + sF[q]);
           a.oblk[q / BV][r * BV + q % BV] = y;
         }
       }
     }
     tc::fence_before_sync();
-    __syncthreads();  // TMEM read and A tiles free for the next tile
+    __syncthreads();  // TMEM read, A tiles and row exponents free for the next tile
   }
-  if (failed && tid == 0) atomicExch(a.status, 1);
+  if (failed && lane == 0) atomicExch(a.status, 1);
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tbase, ncols);
 }
 
 // Shared-memory bytes of tc_combine_kernel for nkc K chunks and padded N.
 static size_t tc_smem_bytes(int nkc, int NP) {
-  return (size_t)nkc * kDigits * kATileBytes + (size_t)nkc * kDigits * NP * kKChunk * 2 + 16 + 4 * kMaxN + 64;
+  return (size_t)nkc * kDigits * kATileBytes + (size_t)nkc * kDigits * NP * kKChunk * 2 + 16 +
+         4 * kMaxN + 4 * 2 * kTileRows + 64;
 }
 
 bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt) {
@@ -320,17 +337,23 @@ bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt) {
          N >= 1 && N <= kMaxN && V.bv >= 1 && V.bv <= 16;
 }
 
-template <int BV>
+template <int BV, int KMAX>
 static int launch_tc_combine(const TcArgs& a, size_t smem, bool two_per_sm, cudaStream_t s) {
   static KernelSetup ks;
-  const void* fn = reinterpret_cast<const void*>(tc_combine_kernel<BV>);
+  const void* fn = reinterpret_cast<const void*>(tc_combine_kernel<BV, KMAX>);
   FE_TRY(kernel_configure(ks, fn, 227 * 1024));
   const int64_t ntiles = ceil_div(a.n, kTileRows);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)(two_per_sm ? 2 : 1) * num_sms()));
-  tc_combine_kernel<BV><<<(unsigned)grid, kThreads, smem, s>>>(a);
+  tc_combine_kernel<BV, KMAX><<<(unsigned)grid, kThreads, smem, s>>>(a);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;
+}
+
+template <int BV>
+static int launch_tc_combine_k(const TcArgs& a, size_t smem, bool two_per_sm, cudaStream_t s) {
+  if (a.K <= 32) return launch_tc_combine<BV, 32>(a, smem, two_per_sm, s);
+  return launch_tc_combine<BV, 64>(a, smem, two_per_sm, s);
 }
 
 // Out = V Y on the tensor cores (FP64 blocks; see tc_combine_supported for the shapes).
@@ -364,11 +387,11 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
   const bool two = a.nkc * kClasses * a.NP <= 256;
   const size_t smem = std::max(tc_smem_bytes(a.nkc, a.NP), two ? (size_t)80 * 1024 : (size_t)120 * 1024);
   switch (BV) {
-    case 1: return launch_tc_combine<1>(a, smem, two, s);
-    case 2: return launch_tc_combine<2>(a, smem, two, s);
-    case 4: return launch_tc_combine<4>(a, smem, two, s);
-    case 8: return launch_tc_combine<8>(a, smem, two, s);
-    case 16: return launch_tc_combine<16>(a, smem, two, s);
+    case 1: return launch_tc_combine_k<1>(a, smem, two, s);
+    case 2: return launch_tc_combine_k<2>(a, smem, two, s);
+    case 4: return launch_tc_combine_k<4>(a, smem, two, s);
+    case 8: return launch_tc_combine_k<8>(a, smem, two, s);
+    case 16: return launch_tc_combine_k<16>(a, smem, two, s);
   }
   return set_error(FE_ERR_INVALID, "tc_combine: block width %d", BV);
 }
