@@ -398,7 +398,7 @@ def run_ours(args):
             fp64_all = {"s": ta / 1000.0, "restarts": sta["restarts"], "spmm_blocks": sta["spmm_blocks"],
                         "converged": sta["converged"], "max_resid": sta["max_resid"],
                         "max_rel_eval_diff_vs_step": float(np.max(np.abs(eva - ev) / np.abs(ev))),
-                        "step_speedup": ta / ms_per_step}
+                        "time_vs_step": ta / ms_per_step}
         except Exception as e:
             fp64_all = {"error": str(e)}
 

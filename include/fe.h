@@ -202,11 +202,27 @@ int fe_spmm_t(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
  * V: DEVICE, nv blocks of n x bv (block j at element j*n*bv), so V^T W is (nv*bv) x bw.
  * W: DEVICE, n x bw row-major.  G: DEVICE, FP64 row-major (nv*bv) x bw, overwritten.
  * 1 <= nv <= 32, bv and bw in {1, 2, 4, 8, 16}; V and W may alias (W = one of V's blocks).
- * FP32 inputs: products and per-thread sums in FP32, cross-thread sums in FP64.
+ * FP32 inputs: products and per-thread sums in FP32, cross-thread sums in FP64.  FP64 inputs:
+ * tensor-core split products or FP64 FMA, as fe_block_gram_ex with FE_ENGINE_AUTO.
  * Errors: FE_ERR_INVALID, FE_ERR_OOM (scratch), FE_ERR_CUDA.
  */
 int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
                   fe_dtype dt, double alpha, double* G);
+
+/*
+ * fe_block_gram with a choice of arithmetic (fe_engine).  fe_block_gram is this call with
+ * FE_ENGINE_AUTO.  For FP64 blocks with nv*bv <= 36 and bw in {1, 2, 4, 8}, FE_ENGINE_TC, and
+ * FE_ENGINE_AUTO when nv*bv >= 16 (where it is the faster kernel), run on the tensor cores: within every 128-row tile each column of V and W is cut,
+ * relative to its largest exponent in the tile, into seven 8-bit digits; one MMA per 16 rows
+ * forms every digit product (exact BF16 x BF16 -> FP32 sums of 128 terms), and the tile's
+ * products are assembled in integer arithmetic and added in FP64, so that the error of a tile's
+ * contribution is at most 2^-50 * 128 * max|V[., c]| * max|W[., q]| over its rows (plus the
+ * FP64 roundings of the sums over tiles); entries must be finite, subnormals are read as zero.
+ * Otherwise, and with FE_ENGINE_FMA, the FMA kernels of fe_block_gram.  FE_ENGINE_TC with an
+ * unsupported shape or FP32 blocks: FE_ERR_INVALID.
+ */
+int fe_block_gram_ex(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
+                     fe_dtype dt, double alpha, double* G, int engine);
 
 /*
  * fe_block_gram without any device allocation.  The paper has no counterpart; this entry point
@@ -386,7 +402,9 @@ typedef struct {
   int engine;             /* FP64 restart and Ritz-vector products: FE_ENGINE_FMA = FP64 FMA,
                              FE_ENGINE_AUTO or FE_ENGINE_TC = tensor cores wherever
                              fe_block_combine supports the shape (subspace m <= 64, kept
-                             vectors <= 32), FP64 FMA elsewhere (FE_ENGINE_AUTO) */
+                             vectors <= 32), and the second Gram-Schmidt pass (update and
+                             Gram) on the tensor cores where the shapes allow (nv*b <= 36,
+                             b <= 8); FP64 FMA elsewhere (FE_ENGINE_AUTO) */
 } fe_eigs_opts;
 
 void fe_eigs_opts_default(fe_eigs_opts* opts);

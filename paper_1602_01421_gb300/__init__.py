@@ -136,16 +136,17 @@ def spmm_t(h: Csr, X, Y=None):
     return Y
 
 
-def block_gram(V, W, alpha: float = 1.0, G=None):
-    """G = alpha V^T W (fe_block_gram).  V: (nv, n, bv) blocks; W: (n, bw).  G: float64."""
+def block_gram(V, W, alpha: float = 1.0, G=None, engine: str = "auto"):
+    """G = alpha V^T W (fe_block_gram_ex).  V: (nv, n, bv) blocks; W: (n, bw).  G: float64.
+    engine: "auto" (tensor cores for supported FP64 shapes), "fma" or "tc"."""
     torch = _torch()
     nv, n, bv = V.shape
     bw = W.shape[1]
     if G is None:
         G = torch.empty((nv * bv, bw), dtype=torch.float64, device=W.device)
     _stream()
-    check(load().fe_block_gram(_dev(V, "V"), n, nv, bv, _dev(W, "W"), bw, _dt(W), float(alpha),
-                               _dev(G, "G")))
+    check(load().fe_block_gram_ex(_dev(V, "V"), n, nv, bv, _dev(W, "W"), bw, _dt(W), float(alpha),
+                                  _dev(G, "G"), _lib.ENGINE[engine]))
     return G
 
 

@@ -323,15 +323,20 @@ int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt) {
   return spmm_resident(h, X, Y, b, dt, cur_stream());
 }
 
-int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
-                  fe_dtype dt, double alpha, double* G) {
+int fe_block_gram_ex(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
+                     fe_dtype dt, double alpha, double* G, int engine) {
   FE_ARG(V && W && G, "fe_block_gram: NULL pointer");
   FE_ARG(n >= 1, "fe_block_gram: n < 1");
   FE_ARG(nv >= 1 && nv <= 32, "fe_block_gram: nv = %d not in [1, 32]", nv);
   FE_ARG(is_pow2_le16(bv) && is_pow2_le16(bw), "fe_block_gram: bv, bw must be in {1,2,4,8,16}");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_gram: bad dtype");
   BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
-  return gram(vs, n, W, bw, bw, dt, alpha, G, cur_stream());
+  return gram(vs, n, W, bw, bw, dt, alpha, G, cur_stream(), engine);
+}
+
+int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int bw,
+                  fe_dtype dt, double alpha, double* G) {
+  return fe_block_gram_ex(V, n, nv, bv, W, bw, dt, alpha, G, FE_ENGINE_AUTO);
 }
 
 int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,

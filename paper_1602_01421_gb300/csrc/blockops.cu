@@ -212,6 +212,10 @@ static int launch_gram_reduce(const double* part, int nctas, int nout, double al
   return FE_OK;
 }
 
+int gram_reduce(const double* partial, int nctas, int nout, double alpha, double* G, cudaStream_t s) {
+  return launch_gram_reduce(partial, nctas, nout, alpha, G, s);
+}
+
 // Launches gram_kernel<T, BV, NQ, TPW> with as many CTAs as fit on the GPU at once (at most one
 // staged range each per pass), then the partial reduction.  scratch == nullptr: partials in
 // the pool's slot 0; otherwise in scratch (capacity doubles), the grid shrunk to fit.
@@ -279,9 +283,22 @@ static int gram_bv(const BlockSet& V, int64_t n, const T* W, int bw, int ldw, do
 }
 
 int gram(const BlockSet& V, int64_t n, const void* W, int bw, int ldw, fe_dtype dt, double alpha,
-         double* G, cudaStream_t s) {
+         double* G, cudaStream_t s, int engine) {
   FE_ARG(V.nv >= 1 && V.nv <= kMaxBlocks, "gram: nv = %d out of range", V.nv);
   FE_ARG(is_pow2_le16(bw), "gram: bw = %d", bw);
+  FE_ARG(engine == FE_ENGINE_AUTO || engine == FE_ENGINE_FMA || engine == FE_ENGINE_TC,
+         "gram: engine = %d", engine);
+  // AUTO takes the split-product Gram where it is measured faster than the FP64 FMA kernels on
+  // this part: V with at least 16 columns (n = 2^22, 36 x 4: 0.97 against 1.55 ms; 4 x 4: 0.38
+  // against 0.31 ms)
+  if (engine != FE_ENGINE_FMA && dt == FE_F64) {
+    const bool ok = tc_gram_supported(V, bw, ldw, dt);
+    if (ok && (engine == FE_ENGINE_TC || V.nv * V.bv >= 16))
+      return tc_gram(V, n, static_cast<const double*>(W), bw, alpha, G, s);
+    FE_ARG(ok || engine == FE_ENGINE_AUTO,
+           "gram: the tensor-core engine takes FP64 V with nv*bv <= 36 and bw in {1, 2, 4, 8}");
+  }
+  FE_ARG(engine != FE_ENGINE_TC, "gram: the tensor-core engine takes FP64 blocks only");
   if (dt == FE_F32) {
     const float* w = static_cast<const float*>(W);
     switch (V.bv) {

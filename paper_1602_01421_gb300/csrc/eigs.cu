@@ -37,7 +37,7 @@ namespace fe {
 
 int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
             int update_anorm, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
-            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32);
+            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32, int engine);
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
                 double* theta, double* Y, double* rho, int* info, double* work, cudaStream_t s);
 size_t ritz_work_doubles(int m);
@@ -171,6 +171,8 @@ struct Phase {
   // engine of the restart / Ritz-vector products: FMA when asked for, otherwise tensor cores
   // wherever the shape and precision allow (FE_ENGINE_TC does not fail the solve elsewhere)
   int product_engine() const { return engine == FE_ENGINE_FMA ? FE_ENGINE_FMA : FE_ENGINE_AUTO; }
+  // engine of the second Gram-Schmidt pass (tensor cores where the shapes allow, unless FMA)
+  int orth_engine() const { return product_engine(); }
 
   BlockSet slots(int j0, int j1) const {  // slots [j0, j1)
     std::vector<const void*> v(slot.begin() + j0, slot.begin() + j1);
@@ -186,7 +188,7 @@ struct Phase {
     BlockSet none = blockset_of({}, b, b);
     // the start block's column norms seed the ||A|| scale (update_anorm = 1)
     FE_TRY(orth_ex(none, n, slot[0], b, dt, anorm, 1, seed, &rng_counter, nullptr, b, gtmp, b,
-                   &replacements, s, pass1_f32));
+                   &replacements, s, pass1_f32, orth_engine()));
     if (subspace_host)
       FE_CUDA(cudaMemcpyAsync(cache[0], slot[0], (size_t)n * b * dt_size(dt), cudaMemcpyDefault, s));
     return FE_OK;
@@ -203,7 +205,8 @@ struct Phase {
       ++spmm_blocks;
       BlockSet V = slots(0, j + 1);
       FE_TRY(orth_ex(V, n, w, b, dt, anorm, 1, seed, &rng_counter, H + (size_t)j * b, m,
-                     H + (size_t)(j + 1) * b * m + (size_t)j * b, m, &replacements, s, pass1_f32));
+                     H + (size_t)(j + 1) * b * m + (size_t)j * b, m, &replacements, s, pass1_f32,
+                     orth_engine()));
       if (subspace_host) {
         FE_CUDA(cudaMemcpyAsync(slot[j + 1], w, (size_t)n * b * dt_size(dt), cudaMemcpyDefault, s));
         std::swap(cache[0], cache[1]);

@@ -89,8 +89,10 @@ BlockSet blockset_of(const std::vector<const void*>& ptrs, int bv, int ld);
 
 // G[(j*bv + p) * bw + q] = alpha * sum_r V_j[r][p] * W[r][q]  (FP64 out, device).
 // Two phases (per-CTA partials, deterministic reduce); scratch from the gram scratch pool.
+// engine (fe_engine): FP64 V and W go to the tensor-core kernel (tcgemm.cu) when it supports
+// the shape (AUTO) or always (TC, error otherwise); FMA (default) keeps the FMA kernels.
 int gram(const BlockSet& V, int64_t n, const void* W, int bw, int ldw, fe_dtype dt,
-         double alpha, double* G, cudaStream_t s);
+         double alpha, double* G, cudaStream_t s, int engine = FE_ENGINE_FMA);
 // W[r] = beta * (W[r] M) + alpha * sum_j V_j[r] C_j   (M: bw x bw FP64 device or null = I;
 // C: (nv*bv) x bw FP64 device; nv may be 0).
 int update(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
@@ -102,8 +104,15 @@ int update(const BlockSet& V, int64_t n, const double* C, double alpha, double b
 int combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
             fe_dtype dt, cudaStream_t s, int engine = FE_ENGINE_AUTO);
 bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt);
+// Out = beta Out + alpha V Y (the beta term and the final sum in FP64; beta = 0: Out not read).
 int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
-               cudaStream_t s);
+               cudaStream_t s, double alpha = 1.0, double beta = 0.0);
+// G = alpha V^T W on the tensor cores (FP64 blocks; see tc_gram_supported for the shapes).
+bool tc_gram_supported(const BlockSet& V, int bw, int ldw, fe_dtype dt);
+int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha, double* G,
+            cudaStream_t s);
+// G[e] = alpha * sum over c < nctas of partial[c * nout + e], fixed order (deterministic).
+int gram_reduce(const double* partial, int nctas, int nout, double alpha, double* G, cudaStream_t s);
 // Small-matrix device scratch: a pool of FP64 buffers reused across calls on this thread.
 double* small_scratch(int slot, size_t count);
 int random_normal(void* X, int64_t n, int b, int ld, fe_dtype dt, uint64_t seed,

@@ -121,6 +121,7 @@ struct TcArgs {
   const uint16_t* bdig;        // global: [nkc][7][NP x 32] canonical tiles
   const int* fexp;             // global: N column exponent fields of Y
   int* status;                 // device word: 1 = an MMA wait ran out
+  double beta;                 // Out = beta Out + (alpha V Y); beta = 0: Out is not read
 };
 
 }  // namespace
@@ -128,12 +129,12 @@ struct TcArgs {
 // Y (K x N FP64, row-major, ld ldy) -> per-column exponent fields and the seven digit tiles of
 // every 32-row K chunk in the MMA's B layout (row q of B = column q of Y; rows N..NP-1 and
 // K beyond K zero).  One CTA.
-__global__ void tc_prep_y_kernel(const double* __restrict__ Y, int ldy, int K, int N, int NP, int nkc,
-                                 uint16_t* __restrict__ bdig, int* __restrict__ fexp) {
+__global__ void tc_prep_y_kernel(const double* __restrict__ Y, int ldy, double alpha, int K, int N, int NP,
+                                 int nkc, uint16_t* __restrict__ bdig, int* __restrict__ fexp) {
   __shared__ int sf[kMaxN];
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
     int f = 0;
-    for (int c = 0; c < K; ++c) f = max(f, exp_field(Y[c * ldy + q]));
+    for (int c = 0; c < K; ++c) f = max(f, exp_field(alpha * Y[c * ldy + q]));
     sf[q] = f;
     fexp[q] = f;
   }
@@ -147,7 +148,7 @@ __global__ void tc_prep_y_kernel(const double* __restrict__ Y, int ldy, int K, i
     uint64_t m = 0;
     uint32_t sgn = 0;
     if (q < N && c < K) {
-      const double y = Y[c * ldy + q];
+      const double y = alpha * Y[c * ldy + q];
       m = aligned_sig(y, sf[q]);
       sgn = (uint32_t)((uint64_t)__double_as_longlong(y) >> 63);
     }
@@ -313,7 +314,9 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
           double y = 0.0;
           if (!ok) y = __longlong_as_double(0x7FF8000000000000ll);
           else if (emax > 0) y = assemble(hi, lo, ebase + sF[q]);
-          a.oblk[q / BV][r * BV + q % BV] = y;
+          double* dst = a.oblk[q / BV] + r * BV + q % BV;
+          if (a.beta != 0.0) y = fma(a.beta, *dst, y);
+          *dst = y;
         }
       }
     }
@@ -358,7 +361,7 @@ static int launch_tc_combine_k(const TcArgs& a, size_t smem, bool two_per_sm, cu
 
 // Out = V Y on the tensor cores (FP64 blocks; see tc_combine_supported for the shapes).
 int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const BlockSet& Out,
-               cudaStream_t s) {
+               cudaStream_t s, double alpha, double beta) {
   FE_ARG(tc_combine_supported(V, Out, FE_F64), "tc_combine: unsupported shape");
   TcArgs a;
   memset(&a, 0, sizeof(a));
@@ -368,6 +371,7 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
   a.N = Out.nv * BV;
   a.NP = a.N <= 16 ? 16 : 32;
   a.nkc = (int)ceil_div(a.K, kKChunk);
+  a.beta = beta;
   for (int j = 0; j < V.nv; ++j) a.vblk[j] = static_cast<const double*>(V.blk[j]);
   for (int o = 0; o < Out.nv; ++o) a.oblk[o] = const_cast<double*>(static_cast<const double*>(Out.blk[o]));
   // scratch: B digit tiles, column exponents, status word
@@ -378,7 +382,7 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
   a.fexp = reinterpret_cast<const int*>(scr + bbytes / 8);
   a.status = reinterpret_cast<int*>(scr + bbytes / 8 + kMaxN);
   FE_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
-  tc_prep_y_kernel<<<1, 256, 0, s>>>(Y, ldy, a.K, a.N, a.NP, a.nkc, const_cast<uint16_t*>(a.bdig),
+  tc_prep_y_kernel<<<1, 256, 0, s>>>(Y, ldy, alpha, a.K, a.N, a.NP, a.nkc, const_cast<uint16_t*>(a.bdig),
                                      const_cast<int*>(a.fexp));
   count_launch();
   FE_CUDA(cudaGetLastError());
@@ -394,6 +398,287 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
     case 16: return launch_tc_combine_k<16>(a, smem, two, s);
   }
   return set_error(FE_ERR_INVALID, "tc_combine: block width %d", BV);
+}
+
+
+// ---------------------------------------------------------------- Gram V^T W (op3)
+// G = alpha V^T W for FP64 blocks on the tensor cores (Table 1 "op3", MvTransMv), the same
+// digit splitting as above with the roles of rows and columns exchanged: the contraction runs
+// over the rows, so every column of V and of W is scaled by its largest exponent within each
+// 128-row tile.  Per tile the MMA multiplies ALL digit slices at once: A holds the digit rows
+// (i, c) of V^T (7 * KV <= 252 rows, two 128-row M tiles), B the digit rows (j, q) of W^T
+// (7 * bw rows), K = the tile's 128 rows; every accumulator D[(i, c)][(j, q)] sums 128
+// products below 2^16 and is exact.  TMEM lane (i, c) then forms T_i = sum_j D 2^(8 (6 - j))
+// for each q in 64-bit integers and converts it, scaled by 2^(8 (6 - i)) and the tile's column
+// exponents, to FP64; the seven slices i are added in FP64 (smallest first) into the CTA's
+// accumulator of G, and the CTAs' partial Gram matrices are added in a fixed order.
+// Error per tile: 2^-50 * 128 * max|V[., c]| * max|W[., q]| over the tile's rows, plus the FP64
+// roundings of the sums over slices, tiles and CTAs.
+namespace {
+constexpr int kGramMaxKV = 36;                       // 7 * 36 = 252 digit rows of V^T
+constexpr int kGramMaxBW = 8;                        // 7 * 8 = 56 digit rows of W^T
+constexpr int kGramRows = 128;                       // rows per tile (MMA K = 8 x 16)
+constexpr uint32_t kGSBO = (kGramRows / 8) * kCoreBytes;  // 2048 B between 8-row groups
+constexpr int kGATile = 128 * kGramRows * 2;         // one 128-row M tile of V^T digits: 32 KB
+constexpr int kGramUnits = 4;                        // (column, 8-row group) units per thread
+
+struct TcGramArgs {
+  const double* vblk[kMaxBlocks];
+  int bv, KV;            // V: KV / bv blocks of n x bv (ld bv)
+  const double* W;
+  int bw, NP;            // W: n x bw (ld bw); NP = 7 bw padded to the MMA's N
+  int nmt;               // M tiles of V^T digits (1 or 2)
+  int64_t n;
+  double* partial;       // [gridDim.x][KV * bw]
+  int* status;
+};
+}  // namespace
+
+template <int BW>
+__global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int bw = BW;
+  constexpr int NP = (7 * BW + 15) / 16 * 16;
+  const int KV = a.KV, nmt = a.nmt;
+  const int ncol = KV + bw;
+  unsigned char* sA = smem;                                   // nmt x 32 KB
+  unsigned char* sB = sA + (size_t)nmt * kGATile;             // NP x 128 bf16
+  double* sPd = reinterpret_cast<double*>(sB + (size_t)NP * kGramRows * 2);  // [7 KV][bw]
+  int* sEx = reinterpret_cast<int*>(sPd + 7 * kGramMaxKV * kGramMaxBW);       // [2][ncol]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sEx + 2 * (kGramMaxKV + kGramMaxBW));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols_t = nmt * NP <= 32 ? 32u : nmt * NP <= 64 ? 64u : 128u;
+
+  // zero the digit tiles once (rows beyond 7 KV / 7 bw stay zero), exponents of tile 0
+  {
+    int4* z = reinterpret_cast<int4*>(smem);
+    const int n16 = (int)(((size_t)nmt * kGATile + (size_t)NP * kGramRows * 2) / 16);
+    for (int e = tid; e < n16; e += 256) z[e] = make_int4(0, 0, 0, 0);
+    for (int e = tid; e < 2 * ncol; e += 256) sEx[e] = 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, ncols_t);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+  const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
+  const int nout = KV * bw;
+  double acc[(kGramMaxKV * kGramMaxBW + 255) / 256];
+#pragma unroll
+  for (int k = 0; k < (kGramMaxKV * kGramMaxBW + 255) / 256; ++k) acc[k] = 0.0;
+  uint32_t phase = 0;
+  bool failed = false;
+  int par = 0;
+
+  // this thread's (column, 8-row group) units -- the same in every tile: column pointer and
+  // stride, and where each digit's 16-byte core-matrix row goes
+  const double* ucol[kGramUnits];
+  int ustride[kGramUnits], uc[kGramUnits], ug[kGramUnits];
+#pragma unroll
+  for (int k = 0; k < kGramUnits; ++k) {
+    const int u = tid + 256 * k;
+    uc[k] = u < ncol * 16 ? u % ncol : -1;
+    ug[k] = u / ncol;
+    ucol[k] = nullptr;
+    ustride[k] = 0;
+    if (uc[k] >= 0) {
+      const int c = uc[k];
+      ucol[k] = c < KV ? a.vblk[c / a.bv] + c % a.bv : a.W + (c - KV);
+      ustride[k] = c < KV ? a.bv : bw;
+    }
+  }
+
+  const int64_t ntiles = (a.n + kGramRows - 1) / kGramRows;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, par ^= 1) {
+    int* ex = sEx + par * ncol;          // this tile's column exponents
+    int* ex_next = sEx + (par ^ 1) * ncol;
+    const int64_t r0 = tile * kGramRows;
+    // ---- load (column, 8-row group) units and the tile's column exponents
+    double x[kGramUnits][8];
+#pragma unroll
+    for (int k = 0; k < kGramUnits; ++k) {
+      if (uc[k] >= 0) {
+        int e = 0;
+        const int64_t rb = r0 + ug[k] * 8;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int64_t r = rb + t;
+          const double v = r < a.n ? __ldg(ucol[k] + r * ustride[k]) : 0.0;
+          x[k][t] = v;
+          e = max(e, exp_field(v));
+        }
+        atomicMax(ex + uc[k], e);
+      }
+    }
+    for (int e = tid; e < ncol; e += 256) ex_next[e] = 0;   // the next tile's exponents start at 0
+    __syncthreads();
+    // ---- digits: column c's 8-row group g as one 16-byte core-matrix row per digit
+#pragma unroll
+    for (int k = 0; k < kGramUnits; ++k) {
+      if (uc[k] >= 0) {
+        const int c = uc[k], g = ug[k];
+        const int emax = ex[c];
+        uint32_t w[kDigits][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const double x0 = x[k][2 * e], x1 = x[k][2 * e + 1];
+          const uint64_t m0 = aligned_sig(x0, emax), m1 = aligned_sig(x1, emax);
+          const uint32_t sg = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15 |
+                              (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31;
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i) w[i][e] = bf16_pair(digit(m0, i), digit(m1, i)) | sg;
+        }
+#pragma unroll
+        for (int i = 0; i < kDigits; ++i) {
+          unsigned char* dst;
+          if (c < KV) {
+            const int m = i * KV + c;
+            dst = sA + (size_t)(m >> 7) * kGATile + ((m & 127) >> 3) * kGSBO + g * kCoreBytes + (m & 7) * 16;
+          } else {
+            const int nn = i * bw + (c - KV);
+            dst = sB + (nn >> 3) * kGSBO + g * kCoreBytes + (nn & 7) * 16;
+          }
+          *reinterpret_cast<uint4*>(dst) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        }
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    // ---- all digit products of the tile: D_mt = A_mt B^T over 8 K-steps of 16 rows
+    if (tid == 0) {
+      tc::fence_after_sync();
+      for (int mt = 0; mt < nmt; ++mt)
+#pragma unroll
+        for (int ks = 0; ks < kGramRows / 16; ++ks) {
+          const uint64_t ad = tc::smem_desc(sa0 + mt * kGATile + ks * 2 * kCoreBytes, kCoreBytes, kGSBO);
+          const uint64_t bd = tc::smem_desc(sb0 + ks * 2 * kCoreBytes, kCoreBytes, kGSBO);
+          tc::mma_bf16(tbase + (uint32_t)(mt * NP), ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
+      tc::mma_commit(bar);
+    }
+    const bool ok = tc::mbar_wait(bar, phase, kWaitSpins);
+    if (!ok) {
+      failed = true;
+      tc::mbar_wait(bar, phase, kWaitSpins);
+    }
+    phase ^= 1;
+    tc::fence_after_sync();
+    // ---- lane (i, c) of M tile mt: T_i for every q, to FP64 with the tile's scales
+    const int mt = warp >> 2;
+    if (mt < nmt) {
+      const int m = mt * 128 + (warp & 3) * 32 + lane;
+      const uint32_t laddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * NP);
+      uint32_t d[NP / 4][4];
+#pragma unroll
+      for (int c4 = 0; c4 < NP / 4; ++c4) tc::tmem_ld4(laddr + (uint32_t)(4 * c4), d[c4]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int c4 = 0; c4 < NP / 4; ++c4) tc::reg_after_wait(d[c4]);
+      if (m < 7 * KV) {
+        const int i = m / KV, c = m % KV;
+        const int ec = ex[c];
+#define DG(j) acc_int(d[((j) * bw + q) / 4][((j) * bw + q) % 4])
+#pragma unroll
+        for (int q = 0; q < bw; ++q) {
+          {
+            const int64_t hi = ((int64_t)DG(0) << 16) + ((int64_t)DG(1) << 8) + DG(2);
+            const int64_t lo = ((int64_t)DG(3) << 24) + ((int64_t)DG(4) << 16) + ((int64_t)DG(5) << 8) + DG(6);
+            const int fq = ex[KV + q];
+            double y = 0.0;
+            if (!ok) y = __longlong_as_double(0x7FF8000000000000ll);
+            else if (ec > 0 && fq > 0) y = assemble(hi, lo, ec + fq - 2108 + kAsmShift - 8 * i);
+            sPd[m * bw + q] = y;
+          }
+        }
+#undef DG
+      }
+    }
+    __syncthreads();
+    // ---- G[c][q] += sum over the slices i, smallest first
+#pragma unroll
+    for (int k = 0; k < (kGramMaxKV * kGramMaxBW + 255) / 256; ++k) {
+      const int o = tid + 256 * k;
+      if (o < nout) {
+        const int c = o / bw, q = o % bw;
+        double t = 0.0;
+#pragma unroll
+        for (int i = kDigits - 1; i >= 0; --i) t += sPd[(i * KV + c) * bw + q];
+        acc[k] += t;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // TMEM, digit tiles and sPd free for the next tile
+  }
+#pragma unroll
+  for (int k = 0; k < (kGramMaxKV * kGramMaxBW + 255) / 256; ++k) {
+    const int o = tid + 256 * k;
+    if (o < nout) a.partial[(int64_t)blockIdx.x * nout + o] = acc[k];
+  }
+  if (failed && lane == 0) atomicExch(a.status, 1);
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, ncols_t);
+}
+
+bool tc_gram_supported(const BlockSet& V, int bw, int ldw, fe_dtype dt) {
+  const int KV = V.nv * V.bv;
+  return dt == FE_F64 && V.ld == V.bv && ldw == bw && KV >= 1 && KV <= kGramMaxKV &&
+         (bw == 1 || bw == 2 || bw == 4 || bw == 8) && V.bv >= 1;
+}
+
+int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha, double* G,
+            cudaStream_t s) {
+  FE_ARG(tc_gram_supported(V, bw, bw, FE_F64), "tc_gram: unsupported shape");
+  TcGramArgs a;
+  memset(&a, 0, sizeof(a));
+  a.bv = V.bv;
+  a.KV = V.nv * V.bv;
+  for (int j = 0; j < V.nv; ++j) a.vblk[j] = static_cast<const double*>(V.blk[j]);
+  a.W = W;
+  a.bw = bw;
+  a.NP = (int)ceil_div(7 * bw, 16) * 16;
+  a.nmt = (int)ceil_div(7 * a.KV, 128);
+  a.n = n;
+  const size_t smem = (size_t)a.nmt * kGATile + (size_t)a.NP * kGramRows * 2 +
+                      sizeof(double) * 7 * kGramMaxKV * kGramMaxBW + 4 * 2 * (kGramMaxKV + kGramMaxBW) + 64;
+  static KernelSetup ks[4];
+  const int bi = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
+  (void)bi;
+  const void* fn = bw == 1 ? reinterpret_cast<const void*>(tc_gram_kernel<1>)
+                 : bw == 2 ? reinterpret_cast<const void*>(tc_gram_kernel<2>)
+                 : bw == 4 ? reinterpret_cast<const void*>(tc_gram_kernel<4>)
+                           : reinterpret_cast<const void*>(tc_gram_kernel<8>);
+  FE_TRY(kernel_configure(ks[bi], fn, 227 * 1024));
+  // two CTAs per SM (registers and shared memory allow it; TMEM: at most 128 columns each), so
+  // that one CTA's loads and digit work overlap the other's MMA wait and sums
+  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  const int64_t ntiles = ceil_div(n, kGramRows);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms()));
+  const int nout = a.KV * bw;
+  double* scr = small_scratch(18, (size_t)grid * nout + 2);
+  if (!scr) return FE_ERR_OOM;
+  a.partial = scr;
+  a.status = reinterpret_cast<int*>(scr + (size_t)grid * nout);
+  FE_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
+  switch (bw) {
+    case 1: tc_gram_kernel<1><<<grid, 256, smem, s>>>(a); break;
+    case 2: tc_gram_kernel<2><<<grid, 256, smem, s>>>(a); break;
+    case 4: tc_gram_kernel<4><<<grid, 256, smem, s>>>(a); break;
+    default: tc_gram_kernel<8><<<grid, 256, smem, s>>>(a); break;
+  }
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return gram_reduce(a.partial, grid, nout, alpha, G, s);
 }
 
 }  // namespace fe

@@ -1,6 +1,7 @@
-"""GPU parity of the tensor-core split-product block product (fe_block_combine, engine "tc";
-Table 1 "op1" with several output blocks, the restart product V Y of Section 3.1) against the
-oracle's MvTimesMatAddMv, and of the solver with tensor-core restart products against the
+"""GPU parity of the tensor-core split-product block operations -- fe_block_combine (Table 1
+"op1" with several output blocks, the restart product V Y of Section 3.1) against the oracle's
+MvTimesMatAddMv, fe_block_gram_ex (Table 1 "op3", MvTransMv) against the oracle's MvTransMv --
+and of the solver with tensor-core restart products and second Gram-Schmidt pass against the
 oracle's Block Krylov-Schur.
 
 Bounds: the stated worst case |err| <= 2^-49 K max_c|V[r][c]| max_c|Y[c][q]| + 2^-52 |ref|
@@ -122,18 +123,20 @@ def test_tc_engine_rejects_unsupported():
         fe.block_combine(V32, t.zeros((8, 4), dtype=t.float64, device="cuda"), 1, engine="tc")
 
 
+@pytest.mark.parametrize("engine", ["auto", "tc"])
 @pytest.mark.parametrize("name,nev,b,nb", [("rmat14", 8, 4, 8), ("rmat12", 6, 8, 8),
                                            ("er3000", 4, 2, 10)])
-def test_eigs_tensor_core_restarts_match_oracle(name, nev, b, nb):
-    """The FP64 solve with tensor-core restart / Ritz products (engine tc) against the oracle's
-    Block Krylov-Schur and against the FMA engine: eigenvalues within 1e-8 relative, explicit
-    residuals within tol * |theta_1|."""
+def test_eigs_tensor_core_restarts_match_oracle(name, nev, b, nb, engine):
+    """The FP64 solve with tensor-core restart / Ritz products (engine auto; tc also runs the
+    second Gram-Schmidt pass on the tensor cores) against the oracle's Block Krylov-Schur and
+    against the FMA engine: eigenvalues within 1e-8 relative, explicit residuals within
+    tol * |theta_1|."""
     g = {"rmat14": lambda: graphgen.rmat(14, seed=1), "rmat12": lambda: graphgen.rmat(12, seed=4),
          "er3000": lambda: graphgen.erdos_renyi(3000, 10.0, seed=2)}[name]()
     want = bks.block_krylov_schur(g.rowptr, g.colidx, nev, b, nb, 1e-8, "LM", seed=1,
                                   max_restarts=2000).evals
     with fe.Csr.from_graph(g) as h:
-        ev_tc, X, st = fe.eigs(h, nev, b, nb, 1e-8, "LM", seed=1, engine="tc", max_restarts=2000)
+        ev_tc, X, st = fe.eigs(h, nev, b, nb, 1e-8, "LM", seed=1, engine=engine, max_restarts=2000)
         ev_f, _, st_f = fe.eigs(h, nev, b, nb, 1e-8, "LM", seed=1, engine="fma", max_restarts=2000)
     assert st["converged"] and st_f["converged"]
     np.testing.assert_allclose(ev_tc, want, rtol=1e-8)
@@ -142,3 +145,82 @@ def test_eigs_tensor_core_restarts_match_oracle(name, nev, b, nb):
     from oracle import core
     R = core.spmm(g.rowptr, g.colidx, Xh) - Xh * ev_tc
     assert (np.linalg.norm(R, axis=0) <= 1e-8 * np.abs(ev_tc).max()).all()
+
+
+def _gram_check(Vh, Wh, G, tol_componentwise=1e-13):
+    AA = _flat(Vh)
+    ref = blockops.mv_trans_mv(1.0, AA, Wh)
+    err = np.abs(G - ref)
+    n = AA.shape[0]
+    # stated bound: 2^-50 * 128 * max|V_c| * max|W_q| per 128-row tile, summed over the tiles
+    stated = np.zeros_like(ref)
+    for r0 in range(0, n, 128):
+        stated += 2.0 ** -50 * 128 * np.outer(np.abs(AA[r0:r0 + 128]).max(0), np.abs(Wh[r0:r0 + 128]).max(0))
+    stated += 1e-15 * (np.abs(AA).T @ np.abs(Wh)) + 2.0 ** -1022
+    assert (err <= stated).all(), f"stated bound: worst {np.max(err - stated):.3e}"
+    if tol_componentwise is not None:
+        assert (err <= tol_componentwise * (np.abs(AA).T @ np.abs(Wh))).all()
+
+
+GRAM_SHAPES = [  # (n, nv, bv, bw)
+    (1, 1, 1, 1), (127, 8, 4, 4), (128, 9, 4, 4), (129, 9, 4, 4), (5000, 9, 4, 4), (100003, 9, 4, 4),
+    (4099, 2, 8, 8), (3001, 18, 2, 2), (777, 18, 2, 1), (1500, 32, 1, 8), (2048, 4, 4, 8), (65537, 1, 16, 4)]
+
+
+@pytest.mark.parametrize("shape", GRAM_SHAPES)
+def test_tc_gram_matches_oracle(shape):
+    """N(0,1) blocks: G = V^T W on the tensor cores within 1e-13 (|V|^T |W|) of the oracle's
+    MvTransMv and within the stated per-tile bound; 1 or 2 M tiles of digit rows, ragged tiles."""
+    n, nv, bv, bw = shape
+    rng = np.random.default_rng(n + 3 * nv + bw)
+    Vh = rng.standard_normal((nv, n, bv))
+    Wh = rng.standard_normal((n, bw))
+    G = fe.block_gram(to_dev(Vh), to_dev(Wh), engine="tc")
+    _gram_check(Vh, Wh, G.cpu().numpy())
+
+
+def test_tc_gram_integers_exact_and_alias():
+    """Integer data: every tile's digit products and their FP64 sums are exact, so G equals the
+    integer product; W may be one of V's blocks."""
+    rng = np.random.default_rng(6)
+    n, nv, bv = 30011, 9, 4
+    Vi = rng.integers(-1000, 1001, (nv, n, bv)).astype(np.float64)
+    V = to_dev(Vi)
+    G = fe.block_gram(V, V[8], engine="tc").cpu().numpy()
+    exact = _flat(Vi.astype(np.int64)) .T @ Vi[8].astype(np.int64)
+    assert np.array_equal(G, exact.astype(np.float64))
+
+
+def test_tc_gram_scales_and_alpha():
+    """Columns of very different scales within and across tiles, zero columns, alpha."""
+    rng = np.random.default_rng(12)
+    n, nv, bv, bw = 20000, 9, 4, 4
+    Vh = rng.standard_normal((nv, n, bv)) * (10.0 ** rng.uniform(-150, 150, (nv, 1, bv)))
+    Vh[:, ::97, :] *= 1e20                     # a few large rows per tile
+    Vh[3] = 0.0
+    Wh = rng.standard_normal((n, bw)) * 10.0 ** rng.uniform(-100, 100, (1, bw))
+    G = fe.block_gram(to_dev(Vh), to_dev(Wh), alpha=-2.5, engine="tc").cpu().numpy()
+    _gram_check(Vh, Wh, G / -2.5, tol_componentwise=None)
+
+
+def test_tc_gram_and_fma_agree_and_rejects():
+    rng = np.random.default_rng(13)
+    n = 200003
+    Vh = rng.standard_normal((9, n, 4))
+    Wh = rng.standard_normal((n, 4))
+    V, W = to_dev(Vh), to_dev(Wh)
+    a = fe.block_gram(V, W, engine="tc").cpu().numpy()
+    b = fe.block_gram(V, W, engine="fma").cpu().numpy()
+    c = fe.block_gram(V, W).cpu().numpy()
+    assert np.array_equal(a, c)                       # AUTO: tensor cores for 36 columns
+    V4 = to_dev(Vh[:1])
+    assert np.array_equal(fe.block_gram(V4, W).cpu().numpy(),
+                          fe.block_gram(V4, W, engine="fma").cpu().numpy())   # 4 columns: FMA
+    assert (np.abs(a - b) <= 2e-13 * (np.abs(_flat(Vh)).T @ np.abs(Wh))).all()
+    t = torch()
+    with pytest.raises(fe.FeError):
+        fe.block_gram(t.zeros((10, 64, 4), dtype=t.float64, device="cuda"),
+                      t.zeros((64, 4), dtype=t.float64, device="cuda"), engine="tc")   # 40 > 36
+    with pytest.raises(fe.FeError):
+        fe.block_gram(t.zeros((2, 64, 4), dtype=t.float64, device="cuda"),
+                      t.zeros((64, 16), dtype=t.float64, device="cuda"), engine="tc")  # bw 16
