@@ -122,6 +122,7 @@ struct TcArgs {
   const int* fexp;             // global: N column exponent fields of Y
   int* status;                 // device word: 1 = an MMA wait ran out
   double beta;                 // Out = beta Out + (alpha V Y); beta = 0: Out is not read
+  int bulk;                    // 1: every V block is 16-byte aligned (TMA bulk copies allowed)
 };
 
 }  // namespace
@@ -174,8 +175,11 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
   unsigned char* sA = smem;                                        // [nkc][7] x 8 KB
   unsigned char* sB = sA + (size_t)nkc * kDigits * kATileBytes;    // [nkc][7] x NP*64
   const size_t btile = (size_t)NP * kKChunk * 2;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + (size_t)nkc * kDigits * btile);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  double* sV = reinterpret_cast<double*>(sB + (size_t)nkc * kDigits * btile);  // [K/BV][128][BV]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sV + (size_t)kTileRows * KMAX);
+  uint64_t* lbar = bar + 1;                      // V tile copies
+  uint64_t* sDesc = bar + 2;                     // [nkc][7][2] A and B descriptors (K-step 0)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sDesc + 2 * kDigits * (KMAX / kKChunk) * 2);
   int* sF = reinterpret_cast<int*>(tslot + 1);   // N column exponents of Y
   int* sE = sF + kMaxN;                          // [2][128] partial row exponents
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -195,33 +199,69 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
     tc::tmem_alloc(tslot, ncols);
     tc::tmem_relinquish();
   }
+  const int nblk = a.K / BV;
+  const int64_t ntiles = (a.n + kTileRows - 1) / kTileRows;
+  // a tile's V rows come in by TMA bulk copies (one per block) when their byte count is a
+  // multiple of 16 (every full tile); otherwise (a ragged last tile) by plain loads
+  auto bulk_ok = [&](int64_t t) {
+    return a.bulk && ((uint64_t)min((int64_t)kTileRows, a.n - t * kTileRows) * BV * 8) % 16 == 0;
+  };
+  auto issue = [&](int64_t t) {
+    const int64_t r0 = t * kTileRows;
+    const uint32_t bytes = (uint32_t)(min((int64_t)kTileRows, a.n - r0) * BV * 8);
+    tc::mbar_arrive_expect_tx(lbar, bytes * (uint32_t)nblk);
+    for (int j = 0; j < nblk; ++j) tc::bulk_g2s(sV + (size_t)j * kTileRows * BV, a.vblk[j] + r0 * BV, bytes, lbar);
+  };
   if (tid == 0) {
     tc::mbar_init(bar, 1);
+    tc::mbar_init(lbar, 1);
     tc::mbar_fence_init();
   }
   tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles && bulk_ok(blockIdx.x)) issue(blockIdx.x);
   const uint32_t tbase = *tslot;
   const uint32_t idesc = tc::idesc_bf16_f32(kTileRows, NP);
   const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
+  if (tid == 0)
+    for (int kc = 0; kc < nkc; ++kc)
+      for (int i = 0; i < kDigits; ++i) {
+        sDesc[(kc * kDigits + i) * 2] = tc::smem_desc(sa0 + (uint32_t)((kc * kDigits + i) * kATileBytes), kLBO, kSBO);
+        sDesc[(kc * kDigits + i) * 2 + 1] = tc::smem_desc(sb0 + (uint32_t)((kc * kDigits + i) * btile), kLBO, kSBO);
+      }
   const int cbeg = half * KH;                    // this thread's first V column
   const int kc_mine = cbeg / kKChunk, k_mine = cbeg % kKChunk;
-  uint32_t phase = 0;
+  uint32_t phase = 0, lphase = 0;
   bool failed = false;
 
-  const int64_t ntiles = (a.n + kTileRows - 1) / kTileRows;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r = tile * kTileRows + row;
     const bool live = r < a.n;
-    // ---- load this thread's half of row r and its largest exponent
+    const bool bulk = bulk_ok(tile);
+    bool ok = true;
+    if (bulk) {
+      ok = tc::mbar_wait(lbar, lphase, kWaitSpins);
+      if (!ok) {
+        failed = true;
+        tc::mbar_wait(lbar, lphase, kWaitSpins);  // no copy left in flight
+      }
+      lphase ^= 1;
+    }
+    // ---- this thread's half of row r and its largest exponent
     double v[KH];
     int emax = 0;
 #pragma unroll
     for (int c0 = 0; c0 < KH; c0 += BV) {
       if (live && cbeg + c0 < a.K) {
-        ld_row<double, BV>(a.vblk[(cbeg + c0) / BV] + r * BV, &v[c0]);
+        if (bulk) {
+          const double* src = sV + ((size_t)((cbeg + c0) / BV) * kTileRows + row) * BV;
+#pragma unroll
+          for (int p = 0; p < BV; ++p) v[c0 + p] = src[p];
+        } else {
+          ld_row<double, BV>(a.vblk[(cbeg + c0) / BV] + r * BV, &v[c0]);
+        }
       } else {
 #pragma unroll
         for (int p = 0; p < BV; ++p) v[c0 + p] = 0.0;
@@ -230,7 +270,11 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
 #pragma unroll
     for (int c = 0; c < KH; ++c) emax = max(emax, exp_field(v[c]));
     sE[half * kTileRows + row] = emax;
-    __syncthreads();
+    __syncthreads();  // every thread has its V values: the staging buffer takes the next tile
+    if (tid == 0) {
+      const int64_t nt = tile + gridDim.x;
+      if (nt < ntiles && bulk_ok(nt)) issue(nt);
+    }
     emax = max(sE[row], sE[kTileRows + row]);
     // ---- split into seven digits and write them to the A tiles
 #pragma unroll
@@ -258,25 +302,26 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
     // ---- one thread issues the digit products: class g = i + j accumulates A_i B_j
     if (tid == 0) {
       tc::fence_after_sync();
+      // descriptor of K-step ks = that of K-step 0 with the start address advanced by 2 core
+      // matrices (256 bytes, 16 in the descriptor's address field)
       for (int kc = 0; kc < nkc; ++kc)
-        for (int g = 0; g < kClasses; ++g)
-          for (int i = 0; i <= g; ++i) {
-            const int j = g - i;
-            const uint32_t abase = sa0 + (uint32_t)((kc * kDigits + i) * kATileBytes);
-            const uint32_t bbase = sb0 + (uint32_t)((kc * kDigits + j) * btile);
 #pragma unroll
-            for (int ks = 0; ks < kKChunk / 16; ++ks) {
-              const uint64_t ad = tc::smem_desc(abase + ks * 2 * kLBO, kLBO, kSBO);
-              const uint64_t bd = tc::smem_desc(bbase + ks * 2 * kLBO, kLBO, kSBO);
-              tc::mma_bf16(tbase + (uint32_t)((kc * kClasses + g) * NP), ad, bd, idesc,
+        for (int g = 0; g < kClasses; ++g)
+#pragma unroll
+          for (int i = 0; i <= g; ++i) {
+            const uint64_t ad = sDesc[(kc * kDigits + i) * 2];
+            const uint64_t bd = sDesc[(kc * kDigits + (g - i)) * 2 + 1];
+            const uint32_t dt = tbase + (uint32_t)((kc * kClasses + g) * NP);
+#pragma unroll
+            for (int ks = 0; ks < kKChunk / 16; ++ks)
+              tc::mma_bf16(dt, ad + (uint64_t)(ks * 2 * kLBO >> 4), bd + (uint64_t)(ks * 2 * kLBO >> 4), idesc,
                            (i > 0 || ks > 0) ? 1u : 0u);
-            }
           }
       tc::mma_commit(bar);
     }
     // ---- wait for the products (bounded), then read row `row`'s accumulators
-    const bool ok = tc::mbar_wait(bar, phase, kWaitSpins);
-    if (!ok) {
+    if (!tc::mbar_wait(bar, phase, kWaitSpins)) {
+      ok = false;
       failed = true;
       tc::mbar_wait(bar, phase, kWaitSpins);  // let the MMAs in flight finish before TMEM is reused
     }
@@ -330,8 +375,10 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
 
 // Shared-memory bytes of tc_combine_kernel for nkc K chunks and padded N.
 static size_t tc_smem_bytes(int nkc, int NP) {
-  return (size_t)nkc * kDigits * kATileBytes + (size_t)nkc * kDigits * NP * kKChunk * 2 + 16 +
-         4 * kMaxN + 4 * 2 * kTileRows + 64;
+  const int kmax = nkc == 1 ? 32 : 64;
+  return (size_t)nkc * kDigits * kATileBytes + (size_t)nkc * kDigits * NP * kKChunk * 2 +
+         (size_t)kTileRows * kmax * 8 + 16 + 8 * 2 * kDigits * (kmax / kKChunk) * 2 + 8 + 4 * kMaxN +
+         4 * 2 * kTileRows + 64;
 }
 
 bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt) {
@@ -372,7 +419,11 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
   a.NP = a.N <= 16 ? 16 : 32;
   a.nkc = (int)ceil_div(a.K, kKChunk);
   a.beta = beta;
-  for (int j = 0; j < V.nv; ++j) a.vblk[j] = static_cast<const double*>(V.blk[j]);
+  a.bulk = 1;
+  for (int j = 0; j < V.nv; ++j) {
+    a.vblk[j] = static_cast<const double*>(V.blk[j]);
+    if (reinterpret_cast<uintptr_t>(V.blk[j]) % 16) a.bulk = 0;
+  }
   for (int o = 0; o < Out.nv; ++o) a.oblk[o] = const_cast<double*>(static_cast<const double*>(Out.blk[o]));
   // scratch: B digit tiles, column exponents, status word
   const size_t bbytes = (size_t)a.nkc * kDigits * a.NP * kKChunk * 2;
@@ -389,7 +440,7 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
   // two CTAs per SM when their TMEM (256 columns each) fits; the shared-memory request keeps a
   // third CTA off the SM, so no CTA waits in tcgen05.alloc
   const bool two = a.nkc * kClasses * a.NP <= 256;
-  const size_t smem = std::max(tc_smem_bytes(a.nkc, a.NP), two ? (size_t)80 * 1024 : (size_t)120 * 1024);
+  const size_t smem = std::max(tc_smem_bytes(a.nkc, a.NP), two ? (size_t)100 * 1024 : (size_t)120 * 1024);
   switch (BV) {
     case 1: return launch_tc_combine_k<1>(a, smem, two, s);
     case 2: return launch_tc_combine_k<2>(a, smem, two, s);
@@ -431,6 +482,7 @@ struct TcGramArgs {
   int64_t n;
   double* partial;       // [gridDim.x][KV * bw]
   int* status;
+  int bulk;              // 1: V blocks and W 16-byte aligned (TMA bulk copies allowed)
 };
 }  // namespace
 
@@ -443,10 +495,18 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
   const int ncol = KV + bw;
   unsigned char* sA = smem;                                   // nmt x 32 KB
   unsigned char* sB = sA + (size_t)nmt * kGATile;             // NP x 128 bf16
-  double* sPd = reinterpret_cast<double*>(sB + (size_t)NP * kGramRows * 2);  // [7 KV][bw]
-  int* sEx = reinterpret_cast<int*>(sPd + 7 * kGramMaxKV * kGramMaxBW);       // [2][ncol]
+  // staged rows: V block j at sX + j * XS, W at sX + nvb * XS; XS = 128 rows + 4 doubles of
+  // padding, so that the blocks' rows fall on different shared-memory banks
+  double* sX = reinterpret_cast<double*>(sB + (size_t)NP * kGramRows * 2);
+  // per-slice partial products [7 KV][bw]: they live in the A tiles, which are free from the end
+  // of a tile's MMAs to the next tile's digit writes
+  double* sPd = reinterpret_cast<double*>(sA);
+  const int XS = kGramRows * a.bv + 4;           // doubles per staged V block
+  const int nvb = KV / a.bv;
+  int* sEx = reinterpret_cast<int*>(sX + (size_t)nvb * XS + (size_t)kGramRows * BW + 4);  // [2][ncol]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sEx + 2 * (kGramMaxKV + kGramMaxBW));
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* lbar = bar + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t ncols_t = nmt * NP <= 32 ? 32u : nmt * NP <= 64 ? 64u : 128u;
 
@@ -461,14 +521,31 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
     tc::tmem_alloc(tslot, ncols_t);
     tc::tmem_relinquish();
   }
+  const int64_t ntiles = (a.n + kGramRows - 1) / kGramRows;
+  // the tile's rows of every V block and of W by TMA bulk copies (block j's rows land at
+  // sX + j * XS, W's at sX + nvb * XS) when the byte counts are multiples of 16
+  auto bulk_ok = [&](int64_t t) {
+    const int64_t rows = min((int64_t)kGramRows, a.n - t * kGramRows);
+    return a.bulk && (rows * a.bv * 8) % 16 == 0 && (rows * bw * 8) % 16 == 0;
+  };
+  auto issue = [&](int64_t t) {
+    const int64_t r0 = t * kGramRows;
+    const int64_t rows = min((int64_t)kGramRows, a.n - r0);
+    const uint32_t vb = (uint32_t)(rows * a.bv * 8), wb = (uint32_t)(rows * bw * 8);
+    tc::mbar_arrive_expect_tx(lbar, vb * (uint32_t)nvb + wb);
+    for (int j = 0; j < nvb; ++j) tc::bulk_g2s(sX + (size_t)j * XS, a.vblk[j] + r0 * a.bv, vb, lbar);
+    tc::bulk_g2s(sX + (size_t)nvb * XS, a.W + r0 * bw, wb, lbar);
+  };
   if (tid == 0) {
     tc::mbar_init(bar, 1);
+    tc::mbar_init(lbar, 1);
     tc::mbar_fence_init();
   }
   tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles && bulk_ok(blockIdx.x)) issue(blockIdx.x);
   const uint32_t tbase = *tslot;
   const uint32_t idesc = tc::idesc_bf16_f32(128, NP);
   const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
@@ -483,7 +560,7 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
   // this thread's (column, 8-row group) units -- the same in every tile: column pointer and
   // stride, and where each digit's 16-byte core-matrix row goes
   const double* ucol[kGramUnits];
-  int ustride[kGramUnits], uc[kGramUnits], ug[kGramUnits];
+  int ustride[kGramUnits], uc[kGramUnits], ug[kGramUnits], usoff[kGramUnits];
 #pragma unroll
   for (int k = 0; k < kGramUnits; ++k) {
     const int u = tid + 256 * k;
@@ -491,19 +568,31 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
     ug[k] = u / ncol;
     ucol[k] = nullptr;
     ustride[k] = 0;
+    usoff[k] = 0;
     if (uc[k] >= 0) {
       const int c = uc[k];
       ucol[k] = c < KV ? a.vblk[c / a.bv] + c % a.bv : a.W + (c - KV);
       ustride[k] = c < KV ? a.bv : bw;
+      usoff[k] = c < KV ? (c / a.bv) * XS + c % a.bv : nvb * XS + (c - KV);
     }
   }
 
-  const int64_t ntiles = (a.n + kGramRows - 1) / kGramRows;
+  uint32_t lphase = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, par ^= 1) {
     int* ex = sEx + par * ncol;          // this tile's column exponents
     int* ex_next = sEx + (par ^ 1) * ncol;
     const int64_t r0 = tile * kGramRows;
-    // ---- load (column, 8-row group) units and the tile's column exponents
+    const bool bulk = bulk_ok(tile);
+    bool ok = true;
+    if (bulk) {
+      ok = tc::mbar_wait(lbar, lphase, kWaitSpins);
+      if (!ok) {
+        failed = true;
+        tc::mbar_wait(lbar, lphase, kWaitSpins);  // no copy left in flight
+      }
+      lphase ^= 1;
+    }
+    // ---- (column, 8-row group) units and the tile's column exponents
     double x[kGramUnits][8];
 #pragma unroll
     for (int k = 0; k < kGramUnits; ++k) {
@@ -513,7 +602,8 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int64_t r = rb + t;
-          const double v = r < a.n ? __ldg(ucol[k] + r * ustride[k]) : 0.0;
+          double v = 0.0;
+          if (r < a.n) v = bulk ? sX[usoff[k] + (ug[k] * 8 + t) * ustride[k]] : __ldg(ucol[k] + r * ustride[k]);
           x[k][t] = v;
           e = max(e, exp_field(v));
         }
@@ -521,7 +611,11 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
       }
     }
     for (int e = tid; e < ncol; e += 256) ex_next[e] = 0;   // the next tile's exponents start at 0
-    __syncthreads();
+    __syncthreads();  // every unit is in registers: the staging buffer takes the next tile
+    if (tid == 0) {
+      const int64_t nt = tile + gridDim.x;
+      if (nt < ntiles && bulk_ok(nt)) issue(nt);
+    }
     // ---- digits: column c's 8-row group g as one 16-byte core-matrix row per digit
 #pragma unroll
     for (int k = 0; k < kGramUnits; ++k) {
@@ -567,8 +661,8 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
         }
       tc::mma_commit(bar);
     }
-    const bool ok = tc::mbar_wait(bar, phase, kWaitSpins);
-    if (!ok) {
+    if (!tc::mbar_wait(bar, phase, kWaitSpins)) {
+      ok = false;
       failed = true;
       tc::mbar_wait(bar, phase, kWaitSpins);
     }
@@ -598,7 +692,7 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
             double y = 0.0;
             if (!ok) y = __longlong_as_double(0x7FF8000000000000ll);
             else if (ec > 0 && fq > 0) y = assemble(hi, lo, ec + fq - 2108 + kAsmShift - 8 * i);
-            sPd[m * bw + q] = y;
+            sPd[q * (7 * KV) + m] = y;
           }
         }
 #undef DG
@@ -613,7 +707,7 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
         const int c = o / bw, q = o % bw;
         double t = 0.0;
 #pragma unroll
-        for (int i = kDigits - 1; i >= 0; --i) t += sPd[(i * KV + c) * bw + q];
+        for (int i = kDigits - 1; i >= 0; --i) t += sPd[q * (7 * KV) + i * KV + c];
         acc[k] += t;
       }
     }
@@ -646,11 +740,15 @@ int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha,
   for (int j = 0; j < V.nv; ++j) a.vblk[j] = static_cast<const double*>(V.blk[j]);
   a.W = W;
   a.bw = bw;
+  a.bulk = reinterpret_cast<uintptr_t>(W) % 16 == 0;
+  for (int j = 0; j < V.nv; ++j)
+    if (reinterpret_cast<uintptr_t>(V.blk[j]) % 16) a.bulk = 0;
   a.NP = (int)ceil_div(7 * bw, 16) * 16;
   a.nmt = (int)ceil_div(7 * a.KV, 128);
   a.n = n;
   const size_t smem = (size_t)a.nmt * kGATile + (size_t)a.NP * kGramRows * 2 +
-                      sizeof(double) * 7 * kGramMaxKV * kGramMaxBW + 4 * 2 * (kGramMaxKV + kGramMaxBW) + 64;
+                      sizeof(double) * ((size_t)(a.KV / a.bv) * (kGramRows * a.bv + 4) + (size_t)kGramRows * bw + 4) +
+                      4 * 2 * (kGramMaxKV + kGramMaxBW) + 64;
   static KernelSetup ks[4];
   const int bi = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
   (void)bi;
@@ -661,7 +759,7 @@ int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha,
   FE_TRY(kernel_configure(ks[bi], fn, 227 * 1024));
   // two CTAs per SM (registers and shared memory allow it; TMEM: at most 128 columns each), so
   // that one CTA's loads and digit work overlap the other's MMA wait and sums
-  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  const int per_sm = smem <= 113 * 1024 ? 2 : 1;   // 2 x (smem + 1 KB reserved) <= 228 KB
   const int64_t ntiles = ceil_div(n, kGramRows);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms()));
   const int nout = a.KV * bw;
