@@ -127,6 +127,10 @@ typedef struct {
    * without transpose or symmetry check; fe_spmm then reads ncols x b X and writes n x b Y, and
    * fe_eigs / fe_svds reject it. */
   int64_t ncols;
+  /* 1 = launch the SpMM of a resident handle with an L2 access-policy window over X (persisting
+   * hits, streaming misses, window up to the device's persisting set-aside, which the first such
+   * launch on a device raises to its maximum for this process).  Default 0. */
+  int l2_persist;
 } fe_csr_opts;
 
 /* Fill *opts with the defaults. */

@@ -55,7 +55,7 @@ class Csr:
                  check_symmetric: bool = False, device_mem_cap_bytes: int = 0,
                  tail_max: int = 0, hub_min: int = 0, hub_chunk: int = 0, panel_nnz: int = 0,
                  copy_timeout_ms: int = 0, semi_direct: bool = False, transpose: bool = False,
-                 index_format: str = "auto", ncols: int = 0):
+                 index_format: str = "auto", ncols: int = 0, l2_persist: bool = False):
         lib = load()
         self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(colidx, dtype=np.int32)
@@ -71,6 +71,7 @@ class Csr:
         o.transpose = int(transpose)
         o.index_format = _lib.INDEX_FORMAT[index_format]
         o.ncols = int(ncols)
+        o.l2_persist = int(l2_persist)
         h = ctypes.c_void_p()
         check(lib.fe_csr_create_ex(self.n, self._rowptr.ctypes.data_as(ctypes.c_void_p),
                                    self._colidx.ctypes.data_as(ctypes.c_void_p),

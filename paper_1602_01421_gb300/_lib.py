@@ -31,7 +31,8 @@ class CsrOpts(ctypes.Structure):
                 ("hub_min", ctypes.c_int), ("hub_chunk", ctypes.c_int),
                 ("panel_nnz", ctypes.c_int64), ("copy_timeout_ms", ctypes.c_int),
                 ("semi_direct", ctypes.c_int), ("index_format", ctypes.c_int),
-                ("transpose", ctypes.c_int), ("ncols", ctypes.c_int64)]
+                ("transpose", ctypes.c_int), ("ncols", ctypes.c_int64),
+                ("l2_persist", ctypes.c_int)]
 
 
 class CsrInfo(ctypes.Structure):

@@ -256,10 +256,12 @@ int fe_csr_create_ex(int64_t n, const int64_t* rowptr, const int32_t* colidx,
   int hub_chunk = o.hub_chunk > 0 ? o.hub_chunk : 4096;
   if (hub_min < tail_max) hub_min = tail_max;
   int rc;
+  FE_ARG(o.l2_persist == 0 || o.l2_persist == 1, "fe_csr_create: l2_persist = %d", o.l2_persist);
   if (o.device_mem_cap_bytes > 0) {
     rc = semiext_create(h, rowptr, colidx, o);
   } else {
     rc = spmm_build_plan(h, rowptr, colidx, tail_max, hub_min, hub_chunk, packed);
+    h->plan.l2_persist = o.l2_persist;
   }
   if (rc == FE_OK && o.transpose) {
     std::vector<int64_t> trp;

@@ -159,6 +159,7 @@ struct fe_spmm_plan {
   int32_t* d_hub_rows = nullptr;     // nhub
   int32_t* d_hub_task_begin = nullptr;  // nhub + 1
   int hub_min = 4096, hub_chunk = 4096;
+  int l2_persist = 0;                // fe_csr_opts.l2_persist
 };
 
 struct fe_csr_s {
@@ -224,6 +225,8 @@ struct PlanView {
   const int32_t* hub_rows;
   const int32_t* hub_task_begin;
   int64_t nhub;
+  int64_t x_rows;          // rows of X (the matrix's columns), for the L2 window
+  int l2_persist;          // 1: launch with an L2 access-policy window on X (persisting)
 };
 int build_host_plan(const int64_t* rowptr, const int32_t* colidx, int64_t r0, int64_t r1,
                     int tail_max, int hub_min, int hub_chunk, bool packed, HostPlan& hp);

@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "fe_internal.cuh"
@@ -279,6 +280,28 @@ __global__ void hub_reduce_kernel(const int32_t* __restrict__ hub_rows,
   Y[(int64_t)hub_rows[h] * B + c] = (T)(s + e);
 }
 
+// Window size for an L2 access-policy window over `bytes` of X: the device's largest window,
+// the persisting set-aside (raised once per device, in this process's context, to the device's
+// maximum) bounding it so that the whole window can persist.
+static int l2_window_bytes(size_t bytes, size_t* win) {
+  static std::mutex mu;
+  static size_t maxwin[kMaxDevices], persist[kMaxDevices];
+  const int dev = cur_device();
+  if (dev < 0) return dev;
+  std::lock_guard<std::mutex> lock(mu);
+  if (maxwin[dev] == 0) {
+    int mw = 0, mp = 0;
+    FE_CUDA(cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+    FE_CUDA(cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPersistingL2CacheSize, dev));
+    FE_ARG(mw > 0 && mp > 0, "spmm: this device has no L2 persistence control");
+    FE_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)mp));
+    maxwin[dev] = (size_t)mw;
+    persist[dev] = (size_t)mp;
+  }
+  *win = std::min(bytes, std::min(maxwin[dev], persist[dev]));
+  return FE_OK;
+}
+
 template <typename T, int B>
 static int launch_spmm(const PlanView& pv, const T* X, T* Y, T* partial, cudaStream_t s) {
   SpmmParams p;
@@ -305,14 +328,36 @@ static int launch_spmm(const PlanView& pv, const T* X, T* Y, T* partial, cudaStr
     // 256-bit gathers when an X row spans at least 32 bytes and X is 32-byte aligned
     bool v32 = false;
     if constexpr (B * sizeof(T) >= 32) v32 = ((uintptr_t)X % 32) == 0;
+    void (*kern)(const SpmmParams, const T*, T*, T*) = nullptr;
     if (v32) {
-      if constexpr (B * sizeof(T) >= 32) {
-        if (pv.packed) spmm_main_kernel<T, B, true, true><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
-        else spmm_main_kernel<T, B, true, false><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
-      }
+      if constexpr (B * sizeof(T) >= 32)
+        kern = pv.packed ? spmm_main_kernel<T, B, true, true> : spmm_main_kernel<T, B, true, false>;
     } else {
-      if (pv.packed) spmm_main_kernel<T, B, false, true><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
-      else spmm_main_kernel<T, B, false, false><<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
+      kern = pv.packed ? spmm_main_kernel<T, B, false, true> : spmm_main_kernel<T, B, false, false>;
+    }
+    if (pv.l2_persist) {
+      // L2 access-policy window on X: its lines are kept (persisting) while the streamed index
+      // arrays pass through as streaming accesses (Section 3.3.3's cache-resident dense tiles,
+      // with the GPU's L2 as the cache)
+      size_t win = 0;
+      FE_TRY(l2_window_bytes((size_t)pv.x_rows * B * sizeof(T), &win));
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+      attr[0].val.accessPolicyWindow.base_ptr = const_cast<T*>(X);
+      attr[0].val.accessPolicyWindow.num_bytes = win;
+      attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+      attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)ctas);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      FE_CUDA(cudaLaunchKernelEx(&cfg, kern, p, X, Y, partial));
+    } else {
+      kern<<<(unsigned)ctas, 256, 0, s>>>(p, X, Y, partial);
     }
     count_launch();
     FE_CUDA(cudaGetLastError());
@@ -349,6 +394,8 @@ PlanView resident_view(fe_csr h) {
   v.hub_rows = pl.d_hub_rows;
   v.hub_task_begin = pl.d_hub_task_begin;
   v.nhub = pl.nhub;
+  v.x_rows = h->ncols;
+  v.l2_persist = pl.l2_persist;
   return v;
 }
 

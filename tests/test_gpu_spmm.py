@@ -294,3 +294,13 @@ def test_spmm_f32_one_signed_full_size(fmt, kind):
             X = one_signed_block(kind, g.n, b, seed=5 + b)
             Y = fe.spmm(h, to_dev(X)).cpu().numpy()
             assert assert_spmm_close(g, X, Y, F32_BOUND, rows=rows) <= F32_BOUND
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_spmm_l2_window_same_results(graphs, prec):
+    """An L2 access-policy window on X (l2_persist) changes only cache policy: identical results."""
+    g = graphs["rmat14"]
+    for b in (1, 4, 16):
+        X = to_dev(graphgen.normal_block(g.n, b, seed=b, dtype=NP[prec]))
+        with fe.Csr.from_graph(g) as h, fe.Csr.from_graph(g, l2_persist=True) as hl:
+            assert np.array_equal(fe.spmm(h, X).cpu().numpy(), fe.spmm(hl, X).cpu().numpy())
