@@ -205,7 +205,7 @@ int fe_spmm_t(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
  * MvTransMv (Table 1, "op3"): G = alpha * V^T W.
  * V: DEVICE, nv blocks of n x bv (block j at element j*n*bv), so V^T W is (nv*bv) x bw.
  * W: DEVICE, n x bw row-major.  G: DEVICE, FP64 row-major (nv*bv) x bw, overwritten.
- * 1 <= nv <= 32, bv and bw in {1, 2, 4, 8, 16}; V and W may alias (W = one of V's blocks).
+ * 1 <= nv <= 128, bv and bw in {1, 2, 4, 8, 16}; V and W may alias (W = one of V's blocks).
  * FP32 inputs: products and per-thread sums in FP32, cross-thread sums in FP64.  FP64 inputs:
  * tensor-core split products or FP64 FMA, as fe_block_gram_ex with FE_ENGINE_AUTO.
  * Errors: FE_ERR_INVALID, FE_ERR_OOM (scratch), FE_ERR_CUDA.
@@ -248,7 +248,7 @@ int fe_block_gram_noalloc(const void* V, int64_t n, int nv, int bv, const void* 
 /*
  * MvTimesMatAddMv (Table 1, "op1"): W = beta * W + alpha * V C.
  * V: DEVICE, nv blocks of n x bv; C: DEVICE FP64 row-major (nv*bv) x bw; W: DEVICE n x bw.
- * nv = 0 gives MvScale1 (W = beta W).  W must not alias V.  1 <= nv <= 32 (or 0),
+ * nv = 0 gives MvScale1 (W = beta W).  W must not alias V.  1 <= nv <= 128 (or 0),
  * bv, bw in {1, 2, 4, 8, 16}.  Errors: FE_ERR_INVALID, FE_ERR_CUDA.
  */
 int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,
@@ -260,7 +260,7 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
  *     W <- beta * W + alpha * V C,      G = [V_0; ...; V_{nv-1}; W]^T W   (W after the update)
  * V: DEVICE, nv blocks of n x b (block after block); C: DEVICE FP64 row-major (nv*b) x b;
  * W: DEVICE n x b, updated in place; G: DEVICE FP64 row-major ((nv+1)*b) x b, rows j*b + p
- * for block j's column p, then W's b rows.  0 <= nv <= 32 (nv = 0: W = beta W, G = W^T W),
+ * for block j's column p, then W's b rows.  0 <= nv <= 128 (nv = 0: W = beta W, G = W^T W),
  * b in {1, 2, 4, 8}.  W must not alias V.  Deterministic (fixed summation order).
  * Errors: FE_ERR_INVALID, FE_ERR_OOM, FE_ERR_CUDA.
  */
@@ -273,7 +273,7 @@ int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* 
  * step (2)): output block o (n x bv) = sum_j V_j Y[j*bv:(j+1)*bv, o*bv:(o+1)*bv].
  * V: DEVICE, nv blocks of n x bv (block after block); Y: DEVICE FP64 row-major
  * (nv*bv) x (nout*bv); Out: DEVICE, nout blocks of n x bv, overwritten, must not alias V.
- * 1 <= nv <= 32, 1 <= nout <= 32, bv in {1, 2, 4, 8, 16}.
+ * 1 <= nv <= 128, 1 <= nout <= 128, bv in {1, 2, 4, 8, 16}.
  * engine (fe_engine): for FP64 with K = nv*bv <= 64 and N = nout*bv <= 32, FE_ENGINE_AUTO and
  * FE_ENGINE_TC use the tensor cores: every V row is cut, relative to its largest exponent, into
  * seven 8-bit digits, every Y column likewise; the digit products (exact in BF16 x BF16 -> FP32
@@ -432,8 +432,10 @@ typedef struct {
  * 0/1 matrix of h that come first in `which` order (FE_LM: |lambda| descending, ties ->
  * larger lambda first; FE_LA: descending; FE_SA: ascending).  block = b, nblocks = NB,
  * subspace m = b * NB; requires 1 <= nev <= m - b, m + b <= n, b in {1, 2, 4, 8, 16},
- * NB >= 2, m <= 160, NB <= 38 (m > 96: the projected eigenproblem keeps its eigenvector matrix in
- * a device workspace of 2 (m+1)^2 doubles that fe_eigs allocates).  A pair is converged when its Ritz residual estimate is at most
+ * NB >= 2, m <= 512, NB <= 130 (m > 96: the projected eigenproblem keeps its matrices in a device
+ * workspace that fe_eigs allocates, 2 (m+1)^2 doubles up to m = 160 and 5 (m+1)^2 above; above
+ * m = 160 it runs FP32 Jacobi sweeps on one CTA, FP64 matrix products and FP64 Jacobi sweeps on a
+ * cooperative grid).  A pair is converged when its Ritz residual estimate is at most
  * tol * max(|theta|, 1e-3 * max|theta|) and the explicit residual ||A x - theta x|| passes the
  * same test.  evals: HOST, nev doubles.  evecs: DEVICE, n x nev COLUMN-major FP64 (ConvLayout,
  * Table 1), may be NULL; each vector's largest-magnitude entry is positive.  Synchronous.

@@ -329,7 +329,7 @@ int fe_block_gram_ex(const void* V, int64_t n, int nv, int bv, const void* W, in
                      fe_dtype dt, double alpha, double* G, int engine) {
   FE_ARG(V && W && G, "fe_block_gram: NULL pointer");
   FE_ARG(n >= 1, "fe_block_gram: n < 1");
-  FE_ARG(nv >= 1 && nv <= 32, "fe_block_gram: nv = %d not in [1, 32]", nv);
+  FE_ARG(nv >= 1 && nv <= 128, "fe_block_gram: nv = %d not in [1, 128]", nv);
   FE_ARG(is_pow2_le16(bv) && is_pow2_le16(bw), "fe_block_gram: bv, bw must be in {1,2,4,8,16}");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_gram: bad dtype");
   BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
@@ -345,7 +345,7 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
                     double beta, void* W, int bw, fe_dtype dt) {
   FE_ARG(W, "fe_block_update: W is NULL");
   FE_ARG(n >= 1, "fe_block_update: n < 1");
-  FE_ARG(nv >= 0 && nv <= 32, "fe_block_update: nv = %d not in [0, 32]", nv);
+  FE_ARG(nv >= 0 && nv <= 128, "fe_block_update: nv = %d not in [0, 128]", nv);
   FE_ARG(nv == 0 || (V && C), "fe_block_update: NULL V or C");
   FE_ARG(is_pow2_le16(bv) && is_pow2_le16(bw), "fe_block_update: bv, bw must be in {1,2,4,8,16}");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_update: bad dtype");
@@ -364,8 +364,8 @@ int fe_block_combine(const void* V, int64_t n, int nv, int bv, const double* Y, 
                      fe_dtype dt, int engine) {
   FE_ARG(V && Y && Out, "fe_block_combine: NULL pointer");
   FE_ARG(n >= 1, "fe_block_combine: n < 1");
-  FE_ARG(nv >= 1 && nv <= 32, "fe_block_combine: nv = %d not in [1, 32]", nv);
-  FE_ARG(nout >= 1 && nout <= 32, "fe_block_combine: nout = %d not in [1, 32]", nout);
+  FE_ARG(nv >= 1 && nv <= 128, "fe_block_combine: nv = %d not in [1, 128]", nv);
+  FE_ARG(nout >= 1 && nout <= 128, "fe_block_combine: nout = %d not in [1, 128]", nout);
   FE_ARG(is_pow2_le16(bv), "fe_block_combine: bv = %d not in {1,2,4,8,16}", bv);
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_combine: bad dtype");
   {
@@ -384,7 +384,7 @@ int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* 
                          double beta, void* W, fe_dtype dt, double* G) {
   FE_ARG(W && G, "fe_block_update_gram: NULL W or G");
   FE_ARG(n >= 1, "fe_block_update_gram: n < 1");
-  FE_ARG(nv >= 0 && nv <= 32, "fe_block_update_gram: nv = %d not in [0, 32]", nv);
+  FE_ARG(nv >= 0 && nv <= 128, "fe_block_update_gram: nv = %d not in [0, 128]", nv);
   FE_ARG(nv == 0 || (V && C), "fe_block_update_gram: NULL V or C");
   FE_ARG(b == 1 || b == 2 || b == 4 || b == 8, "fe_block_update_gram: b = %d not in {1,2,4,8}", b);
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_update_gram: bad dtype");
@@ -403,7 +403,7 @@ int fe_block_orth(const void* V, int64_t n, int nv, int b, void* W, fe_dtype dt,
                   uint64_t seed, double* G, double* R, int* replaced) {
   FE_ARG(W && R, "fe_block_orth: NULL W or R");
   FE_ARG(nv == 0 || (V && G), "fe_block_orth: NULL V or G");
-  FE_ARG(n >= 1 && nv >= 0 && nv <= 32, "fe_block_orth: bad n or nv");
+  FE_ARG(n >= 1 && nv >= 0 && nv <= 128, "fe_block_orth: bad n or nv");
   FE_ARG(is_pow2_le16(b), "fe_block_orth: b must be in {1,2,4,8,16}");
   FE_ARG((int64_t)(nv + 1) * b <= n, "fe_block_orth: (nv+1)*b > n");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_orth: bad dtype");

@@ -520,15 +520,24 @@ template <typename T, int BV>
 static int launch_combine(const BlockSet& V, int64_t n, const double* Y, int ldy,
                           const BlockSet& Out, cudaStream_t s) {
   constexpr int OB = BV <= 4 ? 8 : (BV == 8 ? 4 : 2);
-  const size_t smem = (size_t)V.nv * BV * Out.nv * BV * sizeof(T);
-  FE_ARG(smem <= 200 * 1024, "combine: coefficient matrix too large");
   static KernelSetup ks;
   FE_TRY(kernel_configure(ks, reinterpret_cast<const void*>(combine_kernel<T, BV, OB>), 200 * 1024));
   int ctas = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
   ctas = std::max(ctas, 1);
-  combine_kernel<T, BV, OB><<<ctas, 256, smem, s>>>(V, Y, ldy, Out, n);
-  count_launch();
-  FE_CUDA(cudaGetLastError());
+  // the coefficients of at most `per` output blocks at a time in shared memory (large subspaces
+  // take several launches, each reading V again)
+  const size_t per_block = (size_t)V.nv * BV * BV * sizeof(T);
+  const int per = (int)std::max<size_t>(1, std::min<size_t>(Out.nv, (size_t)(160 * 1024) / per_block));
+  FE_ARG(per_block <= 200 * 1024, "combine: coefficient matrix too large");
+  for (int o0 = 0; o0 < Out.nv; o0 += per) {
+    BlockSet sub = Out;
+    sub.nv = std::min(per, Out.nv - o0);
+    for (int o = 0; o < sub.nv; ++o) sub.blk[o] = Out.blk[o0 + o];
+    const size_t smem = per_block * sub.nv;
+    combine_kernel<T, BV, OB><<<ctas, 256, smem, s>>>(V, Y + (size_t)o0 * BV, ldy, sub, n);
+    count_launch();
+    FE_CUDA(cudaGetLastError());
+  }
   return FE_OK;
 }
 

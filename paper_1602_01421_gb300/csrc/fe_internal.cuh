@@ -68,16 +68,17 @@ int kernel_occupancy(KernelSetup& ks, const void* func, int threads, size_t smem
 // A set of nv tall blocks; block j is n x bv with row stride ld (elements), starting at
 // blk[j].  The eigensolver's subspace slots, a user's contiguous V and single columns of a
 // block (bv = 1, ld = b) are all described this way.
-constexpr int kMaxBlocks = 40;
+constexpr int kMaxBlocks = 132;
 // SpMM plan: rows of degree <= tail_max (at most kMaxTailDegree) go to degree-bucketed slices.
 constexpr int kMaxTailDegree = 128;
 constexpr int kDefaultTailMax = 128;
 constexpr int kDefaultTailMaxPacked = 16;  // packed plans: most rows in the compressed tasks
 constexpr int kMaxBuckets = kMaxTailDegree + 1;
-// Rayleigh-Ritz: subspaces up to kRitzSmallMax are diagonalised entirely in shared memory,
-// larger ones (up to kRitzMax) keep the FP64 eigenvector matrix in a global workspace.
+// Rayleigh-Ritz: subspaces up to kRitzSmallMax are diagonalised entirely in shared memory by
+// one CTA, up to 160 with the FP64 eigenvector matrix in a global workspace, and up to
+// kRitzMax with FP32 sweeps on one CTA, FP64 products and cooperative FP64 sweeps on the grid.
 constexpr int kRitzSmallMax = 96;
-constexpr int kRitzMax = 160;
+constexpr int kRitzMax = 512;
 struct BlockSet {
   const void* blk[kMaxBlocks];
   int nv, bv, ld;

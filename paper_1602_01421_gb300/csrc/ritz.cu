@@ -11,6 +11,8 @@
 // block to the next basis block, since A V_m = V_m H_m + V_{NB} H[m:m+b, :]).
 #include <math.h>
 
+#include <algorithm>
+
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -332,15 +334,357 @@ size_t ritz_smem_bytes(int m) {
          (size_t)(mp / 2) * 2 * sizeof(int) + (size_t)mp * sizeof(int) + 64;
 }
 
+// ------------------------------------------------------------ large subspaces (m > kRitzMidMax)
+// For m up to kRitzMax (512) the m x m matrices no longer fit one SM's shared memory, and FP64
+// Jacobi work on one SM (2 DFMA per clock) would take tens of milliseconds per sweep.  So:
+//   1. one CTA runs the FP32 Jacobi sweeps (A32, Q32 in global memory, L2-resident) to a
+//      relative off-diagonal norm of about 1e-6;
+//   2. Q32 is made orthogonal in FP64 by two Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2
+//      (Higham, "Functions of Matrices", 8.3: quadratic convergence to the orthogonal polar
+//      factor from ||Q^T Q - I|| ~ 1e-7), and A <- Q^T T Q, all as FP64 matrix products on the
+//      whole GPU;
+//   3. FP64 parallel Jacobi sweeps on the nearly diagonal A finish it (two or three sweeps), on
+//      a cooperative grid: a step's rotations are computed by every CTA from the same entries,
+//      then the CTAs share the step's 2 x 2 block updates, with a grid barrier after each half;
+//   4. one CTA orders the pairs and writes theta, Y and the residual estimates.
+// Workspace layout (ld = mp + 1): A32, Q32 (floats, one mp x ld double-array each pair), A64,
+// Q64, W64, S64, then the barrier words and the per-CTA partial sums.
+constexpr int kRitzMidMax = 160;   // the one-CTA kernel's limit (global FP64 Q above 96)
+constexpr int kCoopCtas = 64;
+
+struct BigWork {
+  float *A32, *Q32;
+  double *A, *Q, *W, *S;
+  unsigned* bar;      // [0] arrivals, [1] generation, [2] error flag
+  double* part;       // kCoopCtas partial sums, then fro2 at [kCoopCtas]
+};
+
+__host__ __device__ inline size_t big_mat_doubles(int m) {
+  const int mp = m + (m & 1);
+  return (size_t)mp * (mp + 1);
+}
+
+__host__ __device__ inline BigWork big_work(double* w, int m) {
+  const size_t mat = big_mat_doubles(m);
+  BigWork b;
+  b.A32 = reinterpret_cast<float*>(w);
+  b.Q32 = reinterpret_cast<float*>(w) + mat;
+  b.A = w + mat;
+  b.Q = b.A + mat;
+  b.W = b.Q + mat;
+  b.S = b.W + mat;
+  b.bar = reinterpret_cast<unsigned*>(b.S + mat);
+  b.part = b.S + mat + 4;
+  return b;
+}
+
 size_t ritz_work_doubles(int m) {
   const int mp = m + (m & 1);
-  return m <= kRitzSmallMax ? 0 : (size_t)2 * mp * (mp + 1);
+  if (m <= kRitzSmallMax) return 0;
+  if (m <= kRitzMidMax) return (size_t)2 * mp * (mp + 1);
+  return 5 * big_mat_doubles(m) + 4 + kCoopCtas + 8;
+}
+
+// 1. FP32 sweeps (one CTA) and the FP64 copies of T and Q32.
+__global__ void __launch_bounds__(1024) ritz_big_fp32_kernel(const double* __restrict__ H, int m, double* work) {
+  const int mp = m + (m & 1), ld = mp + 1, np = mp / 2;
+  BigWork w = big_work(work, m);
+  __shared__ float cs[kRitzMax / 2], sn[kRitzMax / 2];
+  __shared__ int pp[kRitzMax / 2], pq[kRitzMax / 2];
+  __shared__ double red[32];
+  __shared__ bool conv;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  double v = 0.0;
+  for (int e = tid; e < mp * mp; e += nth) {
+    const int i = e / mp, j = e % mp;
+    const double a = (i < m && j < m) ? 0.5 * (H[i * m + j] + H[j * m + i]) : 0.0;
+    w.A32[i * ld + j] = (float)a;
+    w.Q32[i * ld + j] = (i == j) ? 1.f : 0.f;
+    v += a * a;
+  }
+  const double fro2 = ritz_block_sum(v, red);
+  __syncthreads();
+  jacobi_sweeps<float>(w.A32, w.Q32, ld, m, mp, 1e-12 * fro2, 20, cs, sn, pp, pq, red, &conv);
+  for (int e = tid; e < mp * mp; e += nth) {
+    const int i = e / mp, j = e % mp;
+    w.Q[i * ld + j] = (double)w.Q32[i * ld + j];
+    w.A[i * ld + j] = (i < m && j < m) ? 0.5 * (H[i * m + j] + H[j * m + i]) : 0.0;
+  }
+  if (tid == 0) w.part[kCoopCtas] = fro2;
+  (void)np;
+}
+
+// 2. C = alpha op(A) op(B) + beta C for mp x mp FP64 matrices (row stride ld); op = transpose
+// when ta / tb.  32 x 32 output tile per CTA, 256 threads with 4 outputs each.
+__global__ void __launch_bounds__(256) ritz_dgemm_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                         double* __restrict__ C, int mp, int ld, int ta, int tb,
+                                                         double alpha, double beta) {
+  __shared__ double sa[32][33], sb[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < mp; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r, k = k0 + tx;   // sa[r][tx] = op(A)[i][k]
+      sa[r][tx] = (i < mp && k < mp) ? (ta ? A[k * ld + i] : A[i * ld + k]) : 0.0;
+      const int kk = k0 + r, j = j0 + tx; // sb[r][tx] = op(B)[kk][j]
+      sb[r][tx] = (kk < mp && j < mp) ? (tb ? B[j * ld + kk] : B[kk * ld + j]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const double bv = sb[k][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(sa[ty + 8 * u][k], bv, acc[u]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty + 8 * u, j = j0 + tx;
+    if (i < mp && j < mp) C[i * ld + j] = alpha * acc[u] + (beta != 0.0 ? beta * C[i * ld + j] : 0.0);
+  }
+}
+
+// Q <- (3 Q - W) / 2 with W = Q (Q^T Q): one Newton-Schulz step.
+__global__ void ritz_ns_kernel(double* __restrict__ Q, const double* __restrict__ W, int mp, int ld) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mp * mp) return;
+  const int i = e / mp, j = e % mp;
+  Q[i * ld + j] = 1.5 * Q[i * ld + j] - 0.5 * W[i * ld + j];
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs resident): arrival counter and
+// generation word in global memory.  The wait is bounded; on a timeout the error flag is set
+// and false returned (the caller then leaves its loops).
+__device__ bool coop_barrier(unsigned* bar, unsigned& gen) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    const unsigned g = gen;
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      unsigned spins = 0;
+      while (atomicAdd(&bar[1], 0u) == g) {
+        if (++spins > (1u << 26) || atomicAdd(&bar[2], 0u) != 0u) {
+          atomicExch(&bar[2], 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    gen = g + 1;
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// 3. FP64 parallel Jacobi sweeps on A (nearly diagonal), Q <- Q J, across the grid.
+__global__ void __launch_bounds__(512) ritz_big_jacobi64_kernel(double* work, int m, double tol, int max_sweeps,
+                                                                int* info) {
+  const int mp = m + (m & 1), ld = mp + 1, np = mp / 2;
+  BigWork w = big_work(work, m);
+  __shared__ double cs[kRitzMax / 2], sn[kRitzMax / 2];
+  __shared__ int pp[kRitzMax / 2], pq[kRitzMax / 2];
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int gt = blockIdx.x * nth + tid, gn = gridDim.x * nth;
+  unsigned gen = 0;
+  const double fro2 = w.part[kCoopCtas];
+  const double thresh = tol * tol * fro2;
+  int sweeps = 0;
+  bool conv = false;
+  while (true) {
+    double v = 0.0;
+    for (int e = gt; e < mp * mp; e += gn) {
+      const int i = e / mp, j = e % mp;
+      if (i != j) v += w.A[i * ld + j] * w.A[i * ld + j];
+    }
+    v = ritz_block_sum(v, red);
+    if (tid == 0) w.part[blockIdx.x] = v;
+    if (!coop_barrier(w.bar, gen)) return;
+    double off2 = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) off2 += w.part[c];   // same order in every CTA
+    if (off2 <= thresh || sweeps >= max_sweeps) {
+      conv = off2 <= thresh;
+      break;
+    }
+    ++sweeps;
+    for (int step = 0; step < mp - 1; ++step) {
+      // every CTA forms the step's rotations from the same (stable) entries ...
+      for (int k = tid; k < np; k += nth) {
+        auto pos = [&](int i) { return i == 0 ? 0 : ((i - 1 + step) % (mp - 1)) + 1; };
+        int p = pos(k), q = pos(mp - 1 - k);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sv = 0.0;
+        if (q < m) {
+          const float t = jacobi_tan(w.A[p * ld + p], w.A[p * ld + q], w.A[q * ld + q]);
+          if (t != 0.f) jacobi_cs(t, c, sv);
+        }
+        pp[k] = p;
+        pq[k] = q;
+        cs[k] = c;
+        sn[k] = sv;
+      }
+      if (!coop_barrier(w.bar, gen)) return;   // all rotations read before any entry changes
+      // ... then the CTAs share the independent 2 x 2 block updates and Q's column pairs
+      const int nsq = np * np;
+      for (int e = gt; e < nsq + mp * np; e += gn) {
+        if (e < nsq) {
+          const int k = e / np, k2 = e - k * np;
+          if (k > k2) continue;
+          const double s1 = sn[k], s2 = sn[k2];
+          if (s1 == 0.0 && s2 == 0.0) continue;
+          const double c1 = cs[k], c2 = cs[k2];
+          const int p1 = pp[k], q1 = pq[k];
+          double* A = w.A;
+          if (k == k2) {
+            const double app = A[p1 * ld + p1], aqq = A[q1 * ld + q1], apq = A[p1 * ld + q1];
+            const double cc = c1 * c1, ss = s1 * s1, cs2 = c1 * s1;
+            A[p1 * ld + p1] = cc * app - 2.0 * cs2 * apq + ss * aqq;
+            A[q1 * ld + q1] = ss * app + 2.0 * cs2 * apq + cc * aqq;
+            const double npq = cs2 * (app - aqq) + (cc - ss) * apq;
+            A[p1 * ld + q1] = npq;
+            A[q1 * ld + p1] = npq;
+          } else {
+            const int p2 = pp[k2], q2 = pq[k2];
+            const double x00 = A[p1 * ld + p2], x01 = A[p1 * ld + q2];
+            const double x10 = A[q1 * ld + p2], x11 = A[q1 * ld + q2];
+            const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+            const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+            const double z00 = c2 * y00 - s2 * y01, z01 = s2 * y00 + c2 * y01;
+            const double z10 = c2 * y10 - s2 * y11, z11 = s2 * y10 + c2 * y11;
+            A[p1 * ld + p2] = z00;
+            A[p1 * ld + q2] = z01;
+            A[q1 * ld + p2] = z10;
+            A[q1 * ld + q2] = z11;
+            A[p2 * ld + p1] = z00;
+            A[q2 * ld + p1] = z01;
+            A[p2 * ld + q1] = z10;
+            A[q2 * ld + q1] = z11;
+          }
+        } else {
+          const int e2 = e - nsq;
+          const int i = e2 / np, k = e2 - i * np;
+          const double sk = sn[k];
+          if (sk == 0.0) continue;
+          const double ck = cs[k];
+          const int p = pp[k], q = pq[k];
+          const double vp = w.Q[i * ld + p], vq = w.Q[i * ld + q];
+          w.Q[i * ld + p] = ck * vp - sk * vq;
+          w.Q[i * ld + q] = sk * vp + ck * vq;
+        }
+      }
+      if (!coop_barrier(w.bar, gen)) return;
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) info[0] = conv ? sweeps : -1;
+}
+
+// 4. Ordering and outputs (one CTA).
+__global__ void ritz_big_out_kernel(const double* __restrict__ H, int m, int b, int which, double* work,
+                                    double* __restrict__ theta_out, double* __restrict__ Y_out,
+                                    double* __restrict__ rho_out, int* __restrict__ info) {
+  const int mp = m + (m & 1), ld = mp + 1;
+  BigWork w = big_work(work, m);
+  __shared__ int order[kRitzMax];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) {
+    for (int i = 0; i < m; ++i) order[i] = i;
+    for (int i = 1; i < m; ++i) {
+      const int x = order[i];
+      const double tx = w.A[x * ld + x];
+      int j = i - 1;
+      while (j >= 0) {
+        const double ty = w.A[order[j] * ld + order[j]];
+        bool before;
+        if (which == 0) before = fabs(tx) > fabs(ty) || (fabs(tx) == fabs(ty) && tx > ty);
+        else if (which == 1) before = tx > ty;
+        else before = tx < ty;
+        if (!before) break;
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = x;
+    }
+    if (w.bar[2] != 0u) info[0] = -2;   // a grid barrier timed out
+  }
+  __syncthreads();
+  for (int c = tid; c < m; c += nth) theta_out[c] = w.A[order[c] * ld + order[c]];
+  for (int e = tid; e < m * m; e += nth) {
+    const int i = e / m, c = e % m;
+    Y_out[e] = w.Q[i * ld + order[c]];
+  }
+  for (int c = tid; c < m; c += nth) {
+    double r2 = 0.0;
+    for (int p = 0; p < b; ++p) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += H[(m + p) * m + i] * w.Q[i * ld + order[c]];
+      r2 += s * s;
+    }
+    rho_out[c] = sqrt(r2);
+  }
+}
+
+static int launch_ritz_big(const double* H, int m, int b, int which, int max_sweeps, double tol,
+                           double* theta, double* Y, double* rho, int* info, double* work,
+                           cudaStream_t s) {
+  const int mp = m + (m & 1), ld = mp + 1;
+  BigWork w = big_work(work, m);
+  FE_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), s));
+  ritz_big_fp32_kernel<<<1, 1024, 0, s>>>(H, m, work);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  const dim3 gg((mp + 31) / 32, (mp + 31) / 32);
+  auto gemm = [&](const double* A, const double* B, double* C, int ta, int tb) -> int {
+    ritz_dgemm_kernel<<<gg, 256, 0, s>>>(A, B, C, mp, ld, ta, tb, 1.0, 0.0);
+    count_launch();
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+  };
+  for (int it = 0; it < 2; ++it) {   // Q <- Q (3 I - Q^T Q) / 2
+    FE_TRY(gemm(w.Q, w.Q, w.S, 1, 0));
+    FE_TRY(gemm(w.Q, w.S, w.W, 0, 0));
+    ritz_ns_kernel<<<(mp * mp + 255) / 256, 256, 0, s>>>(w.Q, w.W, mp, ld);
+    count_launch();
+    FE_CUDA(cudaGetLastError());
+  }
+  FE_TRY(gemm(w.A, w.Q, w.W, 0, 0));   // W = T Q
+  FE_TRY(gemm(w.Q, w.W, w.A, 1, 0));   // A = Q^T T Q
+  // cooperative launch: every CTA resident (the grid barrier relies on it)
+  static KernelSetup ks;
+  int per_sm = 0;
+  FE_TRY(kernel_occupancy(ks, reinterpret_cast<const void*>(ritz_big_jacobi64_kernel), 512, 0, 0, &per_sm));
+  const int grid = std::min(kCoopCtas, per_sm * num_sms());
+  FE_ARG(grid >= 1, "ritz: no resident CTA for the cooperative Jacobi kernel");
+  double* wk = work;
+  int mm = m, ms = max_sweeps;
+  double tl = tol;
+  void* args[] = {&wk, &mm, &tl, &ms, &info};
+  FE_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(ritz_big_jacobi64_kernel), dim3(grid),
+                                      dim3(512), args, 0, s));
+  count_launch();
+  ritz_big_out_kernel<<<1, 512, 0, s>>>(H, m, b, which, work, theta, Y, rho, info);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
 }
 
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
                 double* theta, double* Y, double* rho, int* info, double* work, cudaStream_t s) {
-  const size_t smem = ritz_smem_bytes(m);
   FE_ARG(m >= 1 && m <= kRitzMax, "ritz: subspace m = %d not in [1, %d]", m, kRitzMax);
+  if (m > kRitzMidMax) {
+    FE_ARG(work != nullptr, "ritz: m = %d needs a global workspace", m);
+    return launch_ritz_big(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, work, s);
+  }
+  const size_t smem = ritz_smem_bytes(m);
   FE_ARG(smem <= 225 * 1024, "ritz: subspace m = %d too large", m);
   const bool big = m > kRitzSmallMax;
   FE_ARG(!big || work != nullptr, "ritz: m = %d needs a global workspace", m);

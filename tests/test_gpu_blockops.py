@@ -30,7 +30,7 @@ def _as_tall(V):
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("n,nv,bv,bw", [(1, 1, 1, 1), (1000, 1, 4, 4), (5003, 9, 4, 4),
                                         (70001, 17, 4, 4), (33000, 5, 8, 8), (20000, 3, 16, 16),
-                                        (12345, 2, 2, 8), (4099, 32, 1, 2)])
+                                        (12345, 2, 2, 8), (4099, 32, 1, 2), (9001, 128, 4, 4)])
 def test_gram_parity(prec, n, nv, bv, bw):
     V = _blocks(nv, n, bv, 1, NP[prec])
     W = graphgen.normal_block(n, bw, seed=2, dtype=NP[prec])
@@ -43,7 +43,8 @@ def test_gram_parity(prec, n, nv, bv, bw):
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("n,nv,bv,bw", [(1, 1, 1, 1), (5003, 9, 4, 4), (70001, 16, 4, 4),
-                                        (33000, 8, 8, 8), (2000, 2, 16, 16), (999, 0, 4, 4)])
+                                        (33000, 8, 8, 8), (2000, 2, 16, 16), (999, 0, 4, 4),
+                                        (9001, 128, 4, 4)])
 @pytest.mark.parametrize("alpha,beta", [(-1.0, 1.0), (0.25, 0.0), (2.0, -3.0)])
 def test_update_parity(prec, n, nv, bv, bw, alpha, beta):
     t = torch()
@@ -69,7 +70,7 @@ def test_update_parity(prec, n, nv, bv, bw, alpha, beta):
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("n,nv,b", [(1, 0, 1), (999, 0, 4), (5003, 3, 4), (70001, 7, 4),
                                     (4099, 8, 4), (33000, 12, 2), (20000, 17, 4), (7777, 5, 8),
-                                    (3000, 15, 1)])
+                                    (3000, 15, 1), (6001, 128, 4)])
 @pytest.mark.parametrize("alpha,beta", [(-1.0, 1.0), (0.5, -2.0)])
 def test_update_gram_parity(prec, n, nv, b, alpha, beta):
     """fe_block_update_gram = op1 then op3 on the updated block (oracle: the two Table 1
@@ -170,3 +171,19 @@ def test_orth_breakdown_replaces_columns(prec):
     assert np.abs(Vt.T @ Q).max() < {"f32": 1e-5, "f64": 1e-12}[prec]
     recon = Vt @ G.cpu().numpy() + Q @ R
     assert np.abs(recon - W).max() < {"f32": 1e-4, "f64": 1e-10}[prec] * np.abs(W).max()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("nv,nout,bv", [(128, 64, 4), (64, 100, 4), (32, 128, 2)])
+def test_combine_many_blocks_matches_oracle(prec, nv, nout, bv):
+    """The restart product with large subspaces (up to 128 input and output blocks, several
+    launches of the coefficient-tiled FMA kernel) against the oracle's op1."""
+    n = 3001
+    V = _blocks(nv, n, bv, 7, NP[prec])
+    Y = np.random.default_rng(8).standard_normal((nv * bv, nout * bv))
+    out = fe.block_combine(to_dev(V), to_dev(Y), nout, engine="fma").cpu().numpy()
+    got = np.concatenate([out[o] for o in range(nout)], axis=1).astype(np.float64)
+    Vt = _as_tall(V)
+    ref = Vt @ Y
+    rel = {"f32": 6e-8, "f64": 1.2e-16}[prec] * (nv * bv + 2) * 2
+    assert np.all(np.abs(got - ref) <= rel * (np.abs(Vt) @ np.abs(Y)) + 1e-300)
