@@ -4,15 +4,21 @@
 Workload (default): R-MAT scale 22 (4.19M vertices, edge factor 16, a/b/c/d 0.57/0.19/0.19/
 0.05, seed 1, symmetrised, self-loops/duplicates removed, 0/1 int32 CSR).  One step = one
 plain FP64 Block Krylov-Schur solve for the 8 largest-magnitude eigenpairs, block 4, 8 blocks
-(subspace 32), tol 1e-8, counter-RNG start: SpMM, block Gram/update re-orthogonalisation,
-CholQR2, Rayleigh-Ritz, restarts and the explicit residual check, all on the GPU.
-Beside it: the SpMM sweep b in {1,2,4,8,16} x {FP32, FP64} in GB/s of compulsory bytes, the
-mixed-precision and learned-start solves, 32 eigenpairs with a 128-vector subspace, the SVD
-of a directed R-MAT graph, the semi-external SpMM, the end-to-end time through host buffers,
-and the CPU oracle.
+(subspace 32), tol 1e-8, counter-RNG start: SpMM, block Gram/update re-orthogonalisation (the
+restart product and the second Gram-Schmidt pass on the tensor cores), CholQR2, Rayleigh-Ritz,
+restarts and the explicit residual check, all on the GPU.
+Beside it (one results line): the SpMM sweep b in {1,2,4,8,16} x {FP32, FP64} in GB/s of
+compulsory bytes, the roofline of the step's dominant kernel and of the tensor-core kernels,
+the same solve with all-FP64 orthogonalisation arithmetic, the full solve at R-MAT scale 14,
+the mixed-precision and learned-start solves, 32 and 64 eigenpairs with 128- and 256-vector
+subspaces, R-MAT scale 24 (mixed vs FP64 at subspace 64; learned vs random starts), the SVD of
+a directed R-MAT graph, the semi-external SpMM, the end-to-end time through host buffers, and
+the CPU oracle on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scale S]
-    python bench.py --config mixed24|learned24|semiext27     (the larger configurations)
+    python bench.py --config mixed24|learned24|semiext27     (single configurations; semiext27
+                                                              is not in the default run: its
+                                                              graph generation alone takes ~2 min)
 
 Under torchrun (N > 1) every rank solves its own copy of the workload (replicas: one solve
 runs on one GPU and is not split across GPUs); value = all ranks' solves / the slowest rank's
@@ -38,9 +44,12 @@ NEV, BLOCK, NBLOCKS, TOL = 8, 4, 8, 1e-8
 # a run that does not converge
 MAX_RESTARTS = 5000
 NOMINAL_HBM = 8000.0
-# FP64 on GB300: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz x 2 flop = 1.26 TFLOP/s (the
-# nominal 1.25 TFLOP/s); the solve's FP64 block kernels are bound by it, not by HBM.
-FP64_PEAK_GFLOPS = 1250.0
+# FP64 on GB300: 2 FP64 operations per clock per SM x 152 SMs x 2.07 GHz = 629 G/s (1.26
+# TFLOP/s counting an FMA as two); the FP64 SpMM is bound by its adds, not by HBM.
+FP64_ADD_PEAK_G = 2 * 152 * 2.07
+# dram__bytes_read.sum + dram__bytes_write.sum of one spmm_main_kernel<double,4> launch on
+# R-MAT scale 22 (ncu, the one-launch capture of `bench.py --only spmm1 --prec f64 --b 4`)
+SPMM_F64_B4_DRAM_BYTES = 1455201024 + 109192192
 
 
 def peaks():
@@ -362,26 +371,51 @@ def run_ours(args):
                               "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                               "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
                               "bytes_per_launch": spmm_bytes(n, nnz, 4, es)}
-    # dominant kernel of the FP64 solve (launch list): update_gram_kernel<double,4,4,1>, the
-    # fused second Gram-Schmidt pass, at the solve's shape (7 blocks of n x 4): W = W - V C
-    # (2 n 28 4 flops) and G = [V; W]^T W (2 n 32 4 flops); reads V and W, writes W
-    Vg, Cg, Wg = ugram_inputs(fe, torch, n)
-    for _ in range(3):
-        fe.block_update_gram(Vg, Cg, Wg, alpha=-1.0, beta=1.0)
-    tg = statistics.median(time_cuda(lambda: fe.block_update_gram(Vg, Cg, Wg, alpha=-1.0, beta=1.0),
-                                     10, torch))
-    k = UGRAM_NV * 4
-    flops = 2.0 * n * k * 4 + 2.0 * n * (k + 4) * 4
-    ubytes = 8 * n * (k + 2 * 4)
-    gflops = flops / (tg / 1000.0) / 1e9
-    roofline = {"kernel": "update_gram_kernel<double,4,4,1> + gram_reduce_kernel (op1 + op3 fused, FP64)",
-                "bound": "alu", "achieved": round(gflops, 1), "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
-                "peak_kind": "nominal FP64 rate (unit count x clock)", "traffic": args.traffic,
-                "flops_per_launch": flops, "bytes_per_launch": ubytes,
-                "ms_per_launch": round(tg, 4), "stream": "torch current stream",
-                "hbm_frac": round(ubytes / (tg / 1000.0) / 1e9 / hbm_peak, 4)}
-    del Vg, Wg, Cg
+    # dominant kernel of the FP64 solve (launch list: 25.6% of the kernel time), the SpMM with an
+    # FP64 block of 4 columns; bound by FP64 adds (one per non-zero and column), reported against
+    # the nominal FP64 add rate
+    t64 = sweep["f64_b4"]["ms"]
+    adds = float(nnz) * 4
+    gadds = adds / (t64 / 1000.0) / 1e9
+    roofline = {"kernel": "spmm_main_kernel<double,4> + hub_reduce_kernel (FP64 SpMM, b = 4)",
+                "bound": "alu", "achieved": round(gadds, 1), "peak": FP64_ADD_PEAK_G,
+                "unit": "G FP64 adds/s", "frac": round(gadds / FP64_ADD_PEAK_G, 4),
+                "peak_kind": "nominal FP64 add rate (2 per clock per SM x 152 SMs x 2.07 GHz)",
+                "traffic": SPMM_F64_B4_DRAM_BYTES if args.scale == 22 else None,
+                "adds_per_launch": adds, "bytes_per_launch": spmm_bytes(n, nnz, 4, 8),
+                "ms_per_launch": t64, "stream": "torch current stream",
+                "hbm_frac": round(spmm_bytes(n, nnz, 4, 8) / (t64 / 1000.0) / 1e9 / hbm_peak, 4)}
+    # the tensor-core split-product kernels at the solve's shapes, against HBM: the restart
+    # product V Y (8 blocks of n x 4 into 5) and the second-pass Gram [V_0..V_7 W]^T W
+    roofline_tc = {}
+    try:
+        Vt = fe.random_normal(8 * n, 4, dtype=torch.float64, seed=5).view(8, n, 4)
+        Yt = torch.randn(32, 20, dtype=torch.float64, device=Vt.device,
+                         generator=torch.Generator(device=Vt.device).manual_seed(7))
+        Ot = fe.block_combine(Vt, Yt, 5, engine="tc")
+        tcm = statistics.median(time_cuda(lambda: fe.block_combine(Vt, Yt, 5, Out=Ot, engine="tc"), 10, torch))
+        bc = 8.0 * n * (32 + 20)
+        roofline_tc["tc_combine_kernel<4,32>"] = {
+            "bound": "hbm", "achieved": round(bc / (tcm / 1000.0) / 1e9, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(bc / (tcm / 1000.0) / 1e9 / hbm_peak, 4),
+            "bytes_per_launch": bc, "ms_per_launch": round(tcm, 4),
+            "fma_engine_ms": round(statistics.median(time_cuda(
+                lambda: fe.block_combine(Vt, Yt, 5, Out=Ot, engine="fma"), 5, torch)), 4)}
+        del Ot, Yt
+        Wt = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+        Vx = torch.cat([Vt, Wt.view(1, n, 4)], 0)
+        Gt = fe.block_gram(Vx, Wt, engine="tc")
+        tgm = statistics.median(time_cuda(lambda: fe.block_gram(Vx, Wt, G=Gt, engine="tc"), 10, torch))
+        bg = 8.0 * n * (36 + 4)
+        roofline_tc["tc_gram_kernel<4>"] = {
+            "bound": "hbm", "achieved": round(bg / (tgm / 1000.0) / 1e9, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(bg / (tgm / 1000.0) / 1e9 / hbm_peak, 4),
+            "bytes_per_launch": bg, "ms_per_launch": round(tgm, 4),
+            "fma_engine_ms": round(statistics.median(time_cuda(
+                lambda: fe.block_gram(Vx, Wt, G=Gt, engine="fma"), 5, torch)), 4)}
+        del Vt, Wt, Vx, Gt
+    except Exception as e:
+        roofline_tc = {"error": str(e)}
 
     # ---- the same FP64 solve with every orthogonalisation product in FP64 arithmetic
     # (orth_pass1 = fp64: no FP32-arithmetic first Gram-Schmidt pass or small corrections)
@@ -447,6 +481,7 @@ def run_ours(args):
 
     # ---- learned start: MLP trained on small R-MAT graphs, time to 8 pairs on this graph
     learned_res = None
+    learned_params = None
     if not args.no_learned:
         try:
             from paper_1602_01421_gb300 import learned as L
@@ -455,6 +490,7 @@ def run_ours(args):
             ex = [L.make_subspace_example(graphgen.rmat(sc, seed=100 + i))
                   for i, sc in enumerate([12, 13, 14, 15, 16, 17] * 3)]
             params, losses = L.train(ex, hidden=64, b=BLOCK, steps=1500, lr=2e-3, loss="span")
+            learned_params = params
             t_train = time.perf_counter() - t0
             out = {}
             def run_learned():
@@ -510,6 +546,23 @@ def run_ours(args):
             many["evals_8_vs_nev8_solve"] = float(np.max(np.abs(ev32[:NEV] - ev) / np.abs(ev)))
         except Exception as e:
             many = {"error": str(e)}
+
+    # ---- many eigenvalues with a 256-vector subspace (nev 64, block 4, 64 blocks), mixed mode
+    if many is not None and "error" not in many and not args.no_many:
+        try:
+            out = {}
+            def run_many256():
+                out["r"] = fe.eigs(h, 64, 4, 64, TOL, "LM", seed=1, mode="mixed",
+                                   max_restarts=MAX_RESTARTS)
+            run_many256()
+            t256 = time_cuda(run_many256, 1, torch)[0]
+            ev256, _, st256 = out["r"]
+            many["nev64_m256_mixed"] = {"s": t256 / 1000.0, "restarts": st256["restarts"],
+                                        "spmm_blocks": st256["spmm_blocks"],
+                                        "converged": st256["converged"], "max_resid": st256["max_resid"],
+                                        "evals_32_vs_nev32_solve": float(np.max(np.abs(ev256[:32] - ev32) / np.abs(ev32)))}
+        except Exception as e:
+            many["nev64_m256_mixed"] = {"error": str(e)}
 
     # ---- SVD of a directed graph (the paper's page-graph method): directed R-MAT of the same
     # scale, 8 singular values through A^T A, block 2 and 2 x 8 blocks (the paper's setting)
@@ -574,6 +627,16 @@ def run_ours(args):
         except Exception as e:
             semi = {"error": str(e)}
 
+    # ---- R-MAT scale 24: the mixed-precision solve against the plain FP64 one (block 8,
+    # subspace 64), and the learned start against random starts (block 4, subspace 32, mixed),
+    # each result with its explicit residual from the oracle's SpMM
+    scale24 = None
+    if not args.no_scale24 and args.scale == 22:
+        try:
+            scale24 = config24(args, fe, graphgen, torch, learned_params)
+        except Exception as e:
+            scale24 = {"error": str(e)}
+
     # ---- end to end through host buffers: CSR create (H2D) + solve + evecs D2H
     e2e_times = []
     for i in range(args.e2e_steps + 1):
@@ -602,8 +665,10 @@ def run_ours(args):
             "time_to_8_eigenpairs_s": ms_per_step / 1000.0,
             "eigs": {"restarts": stats[-1]["restarts"], "spmm_blocks": blocks,
                      "evals_head": [float(x) for x in ev[:3]], "max_resid": stats[-1]["max_resid"]},
-            "fp64_all_orth": fp64_all, "config1": config1, "mixed": t_mixed, "learned": learned_res, "many_eigs": many, "svd": svd_res, "semi_external": semi,
+            "fp64_all_orth": fp64_all, "config1": config1, "scale24": scale24, "mixed": t_mixed,
+            "learned": learned_res, "many_eigs": many, "svd": svd_res, "semi_external": semi,
             "spmm_sweep": sweep, "spmm_roofline": spmm_roofline, "roofline": roofline,
+            "roofline_tc": roofline_tc,
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": int(launches),
             "setup": {"graph_gen_s": round(t_gen, 2), "csr_create_s": round(t_create, 3),
@@ -616,6 +681,57 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def config24(args, fe, graphgen, torch, learned_params):
+    """R-MAT scale 24 (16.8M vertices, edge factor 16): plain FP64 vs mixed precision (nev 8,
+    block 8, 8 blocks: subspace 64, tol 1e-8), and learned vs random starts (nev 8, block 4,
+    8 blocks, mixed, tol 1e-8; the network trained on small graphs, this graph unseen)."""
+    import numpy as np
+    from oracle import core
+    t0 = time.perf_counter()
+    g = graphgen.rmat(24, seed=1)
+    res = {"workload": "rmat24-ef16", "n": g.n, "nnz": g.nnz, "gen_s": round(time.perf_counter() - t0, 1)}
+
+    def resid(ev, X):
+        Xh = X.cpu().numpy()
+        R = core.spmm(g.rowptr, g.colidx, Xh) - Xh * ev
+        return float((np.linalg.norm(R, axis=0) / np.abs(ev)).max())
+
+    with fe.Csr.from_graph(g) as h:
+        def timed(**kw):
+            out = {}
+            def run():
+                out["r"] = fe.eigs(h, max_restarts=MAX_RESTARTS, **kw)
+            t = time_cuda(run, 1, torch)[0] / 1000.0
+            return out["r"] + (t,)
+
+        ev64, X64, st64, t64 = timed(nev=8, block=8, nblocks=8, tol=TOL, which="LM", seed=1)
+        res["fp64_b8_m64"] = {"s": t64, "restarts": st64["restarts"], "spmm_blocks": st64["spmm_blocks"],
+                              "converged": st64["converged"], "max_rel_resid_oracle_spmm": resid(ev64, X64)}
+        del X64
+        evm, Xm, stm, tm = timed(nev=8, block=8, nblocks=8, tol=TOL, which="LM", seed=1, mode="mixed")
+        res["mixed_b8_m64"] = {"s": tm, "restarts": stm["restarts"], "restarts_fp32": stm["restarts_fp32"],
+                               "spmm_blocks": stm["spmm_blocks"], "converged": stm["converged"],
+                               "max_rel_resid_oracle_spmm": resid(evm, Xm),
+                               "max_rel_eval_diff_vs_fp64": float(np.max(np.abs(evm - ev64) / np.abs(ev64))),
+                               "speedup_vs_fp64": t64 / tm}
+        del Xm
+        if learned_params is not None:
+            rnd = []
+            for sd in (1, 2, 3):
+                ev, X, st, t = timed(nev=8, block=BLOCK, nblocks=NBLOCKS, tol=TOL, which="LM", seed=sd,
+                                     mode="mixed", return_vectors=False)
+                rnd.append({"seed": sd, "s": t, "spmm_blocks": st["spmm_blocks"]})
+            evl, Xl, stl, tl = timed(nev=8, block=BLOCK, nblocks=NBLOCKS, tol=TOL, which="LM", seed=1,
+                                     mode="mixed", mlp_weights=learned_params, mlp_hidden=64)
+            res["learned_start_mixed"] = {
+                "train": "span loss, 18 R-MAT graphs at scales 12-17, 1500 Adam steps (the learned leg's network)",
+                "random": rnd, "learned": {"s": tl, "spmm_blocks": stl["spmm_blocks"],
+                                           "spmm_start_calls": stl["spmm_start"],
+                                           "max_rel_resid_oracle_spmm": resid(evl, Xl)},
+                "spmm_ratio_vs_random_median": stl["spmm_blocks"] / float(np.median([x["spmm_blocks"] for x in rnd]))}
+    return res
 
 
 def run_config(args):
@@ -736,9 +852,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--sweep-reps", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-scale24", action="store_true",
+                    help="skip the R-MAT scale-24 legs (mixed vs FP64 at subspace 64, learned start)")
     ap.add_argument("--no-fp64-all", action="store_true",
                     help="skip the FP64 solve with all-FP64 orthogonalisation arithmetic")
     ap.add_argument("--no-learned", action="store_true")
@@ -750,11 +868,6 @@ def main():
     ap.add_argument("--semi-modes", default="mixed,fp64",
                     help="semiext27: solve modes to time on the semi-external handle ('' = none)")
 
-    # dram__bytes_read.sum + dram__bytes_write.sum of update_gram_kernel<double,4,4,1> at the
-    # roofline shape, one ncu capture (profiles/update_gram_f64_rmat22.md); update when that
-    # kernel changes
-    ap.add_argument("--traffic", type=float, default=1.073919e9 + 126.096384e6,
-                    help="ncu DRAM bytes per launch of the roofline kernel")
     ap.add_argument("--ref-cycles", type=int, default=2,
                     help="reference arm: Krylov-Schur cycles of the oracle per timed sample")
     ap.add_argument("--no-config1", action="store_true",
