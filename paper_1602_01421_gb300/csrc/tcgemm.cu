@@ -78,6 +78,29 @@ __device__ __forceinline__ uint32_t digit(uint64_t m, int i) {
   return i < 6 ? (uint32_t)(m >> (45 - 8 * i)) & 0xFFu : ((uint32_t)m & 0x1Fu) << 3;
 }
 
+// The aligned significand shifted up by 3 bits (56 bits): digit i is then byte 6 - i.
+__device__ __forceinline__ uint64_t aligned_sig56(double x, int emax) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const int sh = emax - e;
+  if (e == 0 || sh > 52) return 0;
+  return (((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 3) >> sh;
+}
+
+// Digits i of two 56-bit significands as a packed bf16 pair: one byte permute moves the digit
+// byte under the FP32 exponent of 2^23 (0x4B), one FP32 subtraction of 2^23 leaves the digit as
+// an exact FP32 whose top half is its bf16; a second permute packs the two top halves.
+template <int I>
+__device__ __forceinline__ uint32_t digit_pair56(uint64_t m0, uint64_t m1) {
+  constexpr int k = 6 - I;                            // byte of the 64-bit significand
+  constexpr uint32_t sel = 0x7540u | (uint32_t)(k & 3);
+  const uint32_t w0 = k < 4 ? (uint32_t)m0 : (uint32_t)(m0 >> 32);
+  const uint32_t w1 = k < 4 ? (uint32_t)m1 : (uint32_t)(m1 >> 32);
+  const float f0 = __uint_as_float(__byte_perm(w0, 0x4B000000u, sel)) - 8388608.0f;
+  const float f1 = __uint_as_float(__byte_perm(w1, 0x4B000000u, sel)) - 8388608.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
 // Two digits (each an integer in [0, 255]) as a packed bf16 pair (signs are ORed in by the
 // caller): 2^23 + d is exact in FP32, minus 2^23 gives d as an FP32 whose top 16 bits are its
 // bf16.
@@ -283,11 +306,16 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const double x0 = v[k8 + 2 * e], x1 = v[k8 + 2 * e + 1];
-        const uint64_t m0 = aligned_sig(x0, emax), m1 = aligned_sig(x1, emax);
+        const uint64_t m0 = aligned_sig56(x0, emax), m1 = aligned_sig56(x1, emax);
         const uint32_t sg = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15 |
                             (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31;
-#pragma unroll
-        for (int i = 0; i < kDigits; ++i) w[i][e] = bf16_pair(digit(m0, i), digit(m1, i)) | sg;
+        w[0][e] = digit_pair56<0>(m0, m1) | sg;
+        w[1][e] = digit_pair56<1>(m0, m1) | sg;
+        w[2][e] = digit_pair56<2>(m0, m1) | sg;
+        w[3][e] = digit_pair56<3>(m0, m1) | sg;
+        w[4][e] = digit_pair56<4>(m0, m1) | sg;
+        w[5][e] = digit_pair56<5>(m0, m1) | sg;
+        w[6][e] = digit_pair56<6>(m0, m1) | sg;
       }
       const int kk = k_mine + k8;   // column within the chunk
       const int kc = kc_mine + kk / kKChunk;
@@ -350,10 +378,11 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
 #pragma unroll
         for (int kc = 0; kc < KMAX / kKChunk; ++kc)
           if (kc < nkc) {
-            hi += ((int64_t)acc_int(acc[kc][0][u]) << 16) + ((int64_t)acc_int(acc[kc][1][u]) << 8) +
-                  acc_int(acc[kc][2][u]);
-            lo += ((int64_t)acc_int(acc[kc][3][u]) << 24) + ((int64_t)acc_int(acc[kc][4][u]) << 16) +
-                  ((int64_t)acc_int(acc[kc][5][u]) << 8) + acc_int(acc[kc][6][u]);
+            // 32 x 32 -> 64-bit multiply-adds by powers of two
+            hi += (int64_t)acc_int(acc[kc][0][u]) * 65536 + (int64_t)acc_int(acc[kc][1][u]) * 256 +
+                  (int64_t)acc_int(acc[kc][2][u]);
+            lo += (int64_t)acc_int(acc[kc][3][u]) * 16777216 + (int64_t)acc_int(acc[kc][4][u]) * 65536 +
+                  (int64_t)acc_int(acc[kc][5][u]) * 256 + (int64_t)acc_int(acc[kc][6][u]);
           }
         if (live && q < a.N) {
           double y = 0.0;
@@ -626,11 +655,16 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const double x0 = x[k][2 * e], x1 = x[k][2 * e + 1];
-          const uint64_t m0 = aligned_sig(x0, emax), m1 = aligned_sig(x1, emax);
+          const uint64_t m0 = aligned_sig56(x0, emax), m1 = aligned_sig56(x1, emax);
           const uint32_t sg = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15 |
                               (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31;
-#pragma unroll
-          for (int i = 0; i < kDigits; ++i) w[i][e] = bf16_pair(digit(m0, i), digit(m1, i)) | sg;
+          w[0][e] = digit_pair56<0>(m0, m1) | sg;
+          w[1][e] = digit_pair56<1>(m0, m1) | sg;
+          w[2][e] = digit_pair56<2>(m0, m1) | sg;
+          w[3][e] = digit_pair56<3>(m0, m1) | sg;
+          w[4][e] = digit_pair56<4>(m0, m1) | sg;
+          w[5][e] = digit_pair56<5>(m0, m1) | sg;
+          w[6][e] = digit_pair56<6>(m0, m1) | sg;
         }
 #pragma unroll
         for (int i = 0; i < kDigits; ++i) {
