@@ -223,6 +223,8 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
     tc::tmem_relinquish();
   }
   const int nblk = a.K / BV;
+  const bool add_out = a.beta != 0.0;   // decided once: an FP64 compare per result would
+                                        // occupy the FP64 pipe
   const int64_t ntiles = (a.n + kTileRows - 1) / kTileRows;
   // a tile's V rows come in by TMA bulk copies (one per block) when their byte count is a
   // multiple of 16 (every full tile); otherwise (a ragged last tile) by plain loads
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
           if (!ok) y = __longlong_as_double(0x7FF8000000000000ll);
           else if (emax > 0) y = assemble(hi, lo, ebase + sF[q]);
           double* dst = a.oblk[q / BV] + r * BV + q % BV;
-          if (a.beta != 0.0) y = fma(a.beta, *dst, y);
+          if (add_out) y = fma(a.beta, *dst, y);
           *dst = y;
         }
       }
