@@ -255,6 +255,18 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
                     double beta, void* W, int bw, fe_dtype dt);
 
 /*
+ * fe_block_update with a choice of arithmetic (fe_engine); fe_block_update is this call with
+ * FE_ENGINE_FMA.  For FP64 with nv >= 1, bv == bw, K = nv*bv <= 64 and bw <= 32,
+ * FE_ENGINE_AUTO and FE_ENGINE_TC form alpha V C on the tensor cores as fe_block_combine does
+ * (split products, the same error bound, with alpha folded into C before it is split) and add
+ * it to beta W in FP64 (one rounding); the update of the second Gram-Schmidt pass, W - V G1.
+ * Otherwise, and for FE_ENGINE_FMA, FMA kernels in dt.  Errors: as fe_block_update, and
+ * FE_ERR_INVALID for FE_ENGINE_TC with an unsupported shape or dtype.  Asynchronous.
+ */
+int fe_block_update_ex(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,
+                       double beta, void* W, int bw, fe_dtype dt, int engine);
+
+/*
  * MvTimesMatAddMv followed by MvTransMv on its result (Table 1 "op1" then "op3"), the pair the
  * second classical Gram-Schmidt pass of Section 3.1 issues, fused into one sweep over the rows:
  *     W <- beta * W + alpha * V C,      G = [V_0; ...; V_{nv-1}; W]^T W   (W after the update)

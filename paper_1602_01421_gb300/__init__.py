@@ -166,8 +166,9 @@ def block_combine(V, Y, nout: int, Out=None, engine: str = "auto"):
     return Out
 
 
-def block_update(V, C, W, alpha: float = 1.0, beta: float = 1.0):
-    """W = beta W + alpha V C (fe_block_update).  V: (nv, n, bv) or None; C: float64."""
+def block_update(V, C, W, alpha: float = 1.0, beta: float = 1.0, engine: str = "fma"):
+    """W = beta W + alpha V C (fe_block_update_ex).  V: (nv, n, bv) or None; C: float64.
+    engine: "fma" (FMA kernels), "auto" or "tc" (tensor-core split products for FP64, bv == bw)."""
     n, bw = W.shape
     if V is None:
         nv, bv, vp, cp = 0, bw, None, None
@@ -175,8 +176,8 @@ def block_update(V, C, W, alpha: float = 1.0, beta: float = 1.0):
         nv, _, bv = V.shape
         vp, cp = _dev(V, "V"), _dev(C, "C")
     _stream()
-    check(load().fe_block_update(vp, n, nv, bv, cp, float(alpha), float(beta), _dev(W, "W"), bw,
-                                 _dt(W)))
+    check(load().fe_block_update_ex(vp, n, nv, bv, cp, float(alpha), float(beta), _dev(W, "W"), bw,
+                                    _dt(W), _lib.ENGINE[engine]))
     return W
 
 

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
                               ctypes.POINTER(EigsStats)]),
             "fe_block_gram": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp]),
             "fe_block_update": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, i32]),
+            "fe_block_update_ex": (i32, [vp, i64, i32, i32, vp, dbl, dbl, vp, i32, i32, i32]),
             "fe_block_combine": (i32, [vp, i64, i32, i32, vp, i32, vp, i32, i32]),
             "fe_block_gram_ex": (i32, [vp, i64, i32, i32, vp, i32, i32, dbl, vp, i32]),
             "fe_partition_rows": (i32, [i64, vp, i32, vp]),

@@ -343,6 +343,11 @@ int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int b
 
 int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,
                     double beta, void* W, int bw, fe_dtype dt) {
+  return fe_block_update_ex(V, n, nv, bv, C, alpha, beta, W, bw, dt, FE_ENGINE_FMA);
+}
+
+int fe_block_update_ex(const void* V, int64_t n, int nv, int bv, const double* C, double alpha,
+                       double beta, void* W, int bw, fe_dtype dt, int engine) {
   FE_ARG(W, "fe_block_update: W is NULL");
   FE_ARG(n >= 1, "fe_block_update: n < 1");
   FE_ARG(nv >= 0 && nv <= 128, "fe_block_update: nv = %d not in [0, 128]", nv);
@@ -356,7 +361,17 @@ int fe_block_update(const void* V, int64_t n, int nv, int bv, const double* C, d
     FE_ARG(wa + n * bw * es <= va || va + (size_t)nv * n * bv * es <= wa,
            "fe_block_update: W aliases V");
   }
+  FE_ARG(engine == FE_ENGINE_AUTO || engine == FE_ENGINE_FMA || engine == FE_ENGINE_TC,
+         "fe_block_update_ex: engine = %d", engine);
   BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
+  if (engine != FE_ENGINE_FMA) {
+    BlockSet ws = make_blockset(W, 1, bw, bw, n * bw, dt);
+    const bool tc = dt == FE_F64 && nv >= 1 && tc_combine_supported(vs, ws, dt);
+    if (tc) return tc_combine(vs, n, C, bw, ws, cur_stream(), alpha, beta);
+    FE_ARG(engine == FE_ENGINE_AUTO,
+           "fe_block_update_ex: the tensor-core engine takes FP64 blocks with nv >= 1, bv == bw, "
+           "nv*bv <= 64 and bw <= 32");
+  }
   return update(vs, n, C, alpha, beta, nullptr, W, bw, bw, dt, cur_stream());
 }
 

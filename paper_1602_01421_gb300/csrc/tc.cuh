@@ -44,6 +44,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// Plain arrive (release semantics at CTA scope) on the mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One bounded wait in which the thread sleeps until the phase with the given parity completes
+// (or at most about `hint_ns` per poll): true when it completed, false after max_polls polls.
+// Waiting warps then take no issue slots from the working ones.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t max_polls,
+                                                uint32_t hint_ns) {
+  const uint32_t a = smem_addr(bar);
+  for (uint32_t i = 0; i < max_polls; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(hint_ns)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // Arrive on the mbarrier and add `bytes` to the transaction count its phase waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -108,11 +133,18 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | ((uint32_t)(N >> 3) << 17)   // N
          | ((uint32_t)(M >> 4) << 24);  // M
 }
+// The same with FP16 A and B (format code 0).
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | ((uint32_t)(N >> 3) << 17)   // N
+         | ((uint32_t)(M >> 4) << 24);  // M
+}
 
 // ---------------------------------------------------------------- MMA, commit, loads
 // D[tmem] = A x B^T (accumulate = 0) or D += A x B^T (accumulate = 1); A is M x 16, B is N x 16
-// (both K-major bf16), D is M x N FP32 (lane = row, column = n for M = 128).
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// (both K-major, both FP16 or both BF16 as the instruction descriptor says), D is M x N FP32
+// (lane = row, column = n for M = 128).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -134,6 +166,11 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
+// The same for 2 consecutive columns.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
+__device__ __forceinline__ void reg_after_wait(uint32_t (&r)[2]) { asm volatile("" : "+r"(r[0]), "+r"(r[1])); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // Pins registers filled by tmem_ld4 after the tmem_ld_wait that precedes this call: volatile
 // asm statements keep their order, so no use of r can be scheduled before the wait.

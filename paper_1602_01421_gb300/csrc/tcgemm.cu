@@ -45,7 +45,9 @@ constexpr int kKChunk = 32;          // K columns per accumulator set (exactness
 constexpr int kMaxK = 64;
 constexpr int kMaxN = 32;
 constexpr int kThreads = 256;
-constexpr uint32_t kWaitSpins = 1u << 24;
+// Sleeping waits: at most 2^16 polls of up to 32 us each (about 2 s in all).
+constexpr uint32_t kPipePolls = 1u << 16;
+constexpr uint32_t kPipeSleepNs = 32768;
 constexpr int kCoreBytes = 128;      // 8 rows x 16 bytes
 // A (V digits): per (K chunk, digit) a 128 x 32 bf16 tile = 8 KB; SBO = 4 core matrices
 constexpr int kATileBytes = kTileRows * kKChunk * 2;
@@ -87,27 +89,41 @@ __device__ __forceinline__ uint64_t aligned_sig56(double x, int emax) {
   return (((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 3) >> sh;
 }
 
-// Digits i of two 56-bit significands as a packed bf16 pair: one byte permute moves the digit
-// byte under the FP32 exponent of 2^23 (0x4B), one FP32 subtraction of 2^23 leaves the digit as
-// an exact FP32 whose top half is its bf16; a second permute packs the two top halves.
-template <int I>
-__device__ __forceinline__ uint32_t digit_pair56(uint64_t m0, uint64_t m1) {
-  constexpr int k = 6 - I;                            // byte of the 64-bit significand
-  constexpr uint32_t sel = 0x7540u | (uint32_t)(k & 3);
-  const uint32_t w0 = k < 4 ? (uint32_t)m0 : (uint32_t)(m0 >> 32);
-  const uint32_t w1 = k < 4 ? (uint32_t)m1 : (uint32_t)(m1 >> 32);
-  const float f0 = __uint_as_float(__byte_perm(w0, 0x4B000000u, sel)) - 8388608.0f;
-  const float f1 = __uint_as_float(__byte_perm(w1, 0x4B000000u, sel)) - 8388608.0f;
-  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+// FP16 x2 fused multiply-add on packed halves (round to nearest).
+__device__ __forceinline__ uint32_t hfma2_u32(uint32_t x, uint32_t y, uint32_t z) {
+  uint32_t d;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(y), "r"(z));
+  return d;
 }
 
-// Two digits (each an integer in [0, 255]) as a packed bf16 pair (signs are ORed in by the
-// caller): 2^23 + d is exact in FP32, minus 2^23 gives d as an FP32 whose top 16 bits are its
-// bf16.
-__device__ __forceinline__ uint32_t bf16_pair(uint32_t d0, uint32_t d1) {
-  const float f0 = __uint_as_float(0x4B000000u | d0) - 8388608.0f;
-  const float f1 = __uint_as_float(0x4B000000u | d1) - 8388608.0f;
-  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+// The seven digits of two FP64 values x0, x1 relative to the exponent field emax (>= theirs),
+// as packed FP16 pairs: w[i][e] holds digit i of x0 (low half) and of x1 (high half), each with
+// its value's sign.  Per digit pair: a byte permute takes the two digit bytes of the 56-bit
+// significands, a LOP3 puts each under the FP16 exponent of 1024 (1024 + d is exact for
+// d < 1024), and one FP16 FMA forms (1024 + d) s - 1024 s = s d exactly (s = +-1).
+__device__ __forceinline__ void split_pair_f16(double x0, double x1, int emax, uint32_t (&w)[kDigits][4],
+                                               int e) {
+  const uint64_t m0 = aligned_sig56(x0, emax), m1 = aligned_sig56(x1, emax);
+  const uint32_t h0 = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 32);
+  const uint32_t h1 = (uint32_t)((uint64_t)__double_as_longlong(x1) >> 32);
+  const uint32_t s2 = 0x3C003C00u | ((h0 >> 16) & 0x8000u) | (h1 & 0x80000000u);  // (+-1, +-1)
+  const uint32_t c2 = s2 ^ 0xD800D800u;                                          // -1024 (+-1)
+#pragma unroll
+  for (int i = 0; i < kDigits; ++i) {
+    const int k = 6 - i;   // byte of the 56-bit significand holding digit i
+    const uint32_t lo0 = (uint32_t)m0, hi0 = (uint32_t)(m0 >> 32);
+    const uint32_t lo1 = (uint32_t)m1, hi1 = (uint32_t)(m1 >> 32);
+    const uint32_t pa = k < 4 ? lo0 : hi0, pb = k < 4 ? lo1 : hi1;
+    const uint32_t sel = (uint32_t)((k & 3) | ((4 + (k & 3)) << 8));
+    const uint32_t r = (__byte_perm(pa, pb, sel) & 0x00FF00FFu) | 0x64006400u;
+    w[i][e] = hfma2_u32(r, s2, c2);
+  }
+}
+
+// The FP16 bits of s d for a digit d in [0, 255] and a sign bit (the same exact FMA).
+__device__ __forceinline__ uint16_t digit_f16(uint32_t d, uint32_t sign) {
+  const uint32_t s2 = 0x3C00u | (sign << 15);
+  return (uint16_t)(hfma2_u32(0x6400u | d, s2, s2 ^ 0xD800u) & 0xFFFFu);
 }
 
 // Exact integer value of an FP32 accumulator holding an integer of magnitude below 2^24.
@@ -121,18 +137,24 @@ __device__ __forceinline__ int32_t acc_int(uint32_t bits) {
 constexpr int kAsmShift = 12;
 
 // 2^s * (hi 2^20 + floor(lo / 2^12)) truncated to FP64; zero below the normal range, infinity
-// above it.  Integer operations only.
+// above it.  Integer operations only, without branches.
 __device__ __forceinline__ double assemble(int64_t hi, int64_t lo, int s) {
   const int64_t t = (hi << (32 - kAsmShift)) + (lo >> kAsmShift);
-  if (t == 0) return 0.0;
   const uint64_t sign = (uint64_t)t & 0x8000000000000000ull;
   const uint64_t a = t < 0 ? (uint64_t)(-t) : (uint64_t)t;
-  const int msb = 63 - __clzll((long long)a);
-  const uint64_t m = msb >= 52 ? a >> (msb - 52) : a << (52 - msb);
-  const int ef = msb + s + 1023;
-  if (ef <= 0) return __longlong_as_double((long long)sign);
-  if (ef >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-  return __longlong_as_double((long long)(sign | ((uint64_t)ef << 52) | (m & 0xFFFFFFFFFFFFFull)));
+  const int lz = __clzll((long long)a);                 // 64 when a == 0
+  const uint64_t m = a << (lz & 63);                    // leading one at bit 63
+  const int ef = 63 - lz + s + 1023;
+  uint64_t bits = sign | ((uint64_t)(uint32_t)ef << 52) | ((m >> 11) & 0xFFFFFFFFFFFFFull);
+  bits = (a == 0 || ef <= 0) ? sign : bits;
+  bits = ef >= 2047 ? (sign | 0x7FF0000000000000ull) : bits;
+  return __longlong_as_double((long long)bits);
+}
+
+// Bounded wait that sleeps until the phase completes: waiting threads take no issue slots from
+// the other CTA on the SM.  True when the phase completed.
+__device__ __forceinline__ bool wait_sleep(uint64_t* bar, uint32_t parity) {
+  return tc::mbar_wait(bar, parity, 1) || tc::mbar_wait_sleep(bar, parity, kPipePolls, kPipeSleepNs);
 }
 
 struct TcArgs {
@@ -146,6 +168,7 @@ struct TcArgs {
   int* status;                 // device word: 1 = an MMA wait ran out
   double beta;                 // Out = beta Out + (alpha V Y); beta = 0: Out is not read
   int bulk;                    // 1: every V block is 16-byte aligned (TMA bulk copies allowed)
+  int ovec;                    // 1: every output block is 16-byte aligned (vector stores allowed)
 };
 
 }  // namespace
@@ -177,9 +200,7 @@ __global__ void tc_prep_y_kernel(const double* __restrict__ Y, int ldy, double a
       sgn = (uint32_t)((uint64_t)__double_as_longlong(y) >> 63);
     }
     for (int j = 0; j < kDigits; ++j) {
-      const uint32_t d = digit(m, j);
-      const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
-      const uint16_t bits = (uint16_t)((__float_as_uint(f) >> 16) | (sgn << 15));
+      const uint16_t bits = digit_f16(digit(m, j), sgn);
       char* tile = reinterpret_cast<char*>(bdig) + (size_t)(kc * kDigits + j) * per_tile * 2;
       *reinterpret_cast<uint16_t*>(tile + tile_off(q, k)) = bits;
     }
@@ -248,7 +269,6 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
   tc::fence_after_sync();
   if (tid == 0 && (int64_t)blockIdx.x < ntiles && bulk_ok(blockIdx.x)) issue(blockIdx.x);
   const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_bf16_f32(kTileRows, NP);
   const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
   if (tid == 0)
     for (int kc = 0; kc < nkc; ++kc)
@@ -267,10 +287,10 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
     const bool bulk = bulk_ok(tile);
     bool ok = true;
     if (bulk) {
-      ok = tc::mbar_wait(lbar, lphase, kWaitSpins);
+      ok = wait_sleep(lbar, lphase);
       if (!ok) {
         failed = true;
-        tc::mbar_wait(lbar, lphase, kWaitSpins);  // no copy left in flight
+        wait_sleep(lbar, lphase);  // no copy left in flight
       }
       lphase ^= 1;
     }
@@ -308,16 +328,7 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const double x0 = v[k8 + 2 * e], x1 = v[k8 + 2 * e + 1];
-        const uint64_t m0 = aligned_sig56(x0, emax), m1 = aligned_sig56(x1, emax);
-        const uint32_t sg = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15 |
-                            (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31;
-        w[0][e] = digit_pair56<0>(m0, m1) | sg;
-        w[1][e] = digit_pair56<1>(m0, m1) | sg;
-        w[2][e] = digit_pair56<2>(m0, m1) | sg;
-        w[3][e] = digit_pair56<3>(m0, m1) | sg;
-        w[4][e] = digit_pair56<4>(m0, m1) | sg;
-        w[5][e] = digit_pair56<5>(m0, m1) | sg;
-        w[6][e] = digit_pair56<6>(m0, m1) | sg;
+        split_pair_f16(x0, x1, emax, w, e);
       }
       const int kk = k_mine + k8;   // column within the chunk
       const int kc = kc_mine + kk / kKChunk;
@@ -334,26 +345,27 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
       tc::fence_after_sync();
       // descriptor of K-step ks = that of K-step 0 with the start address advanced by 2 core
       // matrices (256 bytes, 16 in the descriptor's address field)
+      // digit i of A against the B digit tiles 0..6-i of the chunk stacked as one operand of
+      // (7-i) NP rows: column block j of the product accumulates into class i + j
       for (int kc = 0; kc < nkc; ++kc)
 #pragma unroll
-        for (int g = 0; g < kClasses; ++g)
+        for (int i = 0; i < kDigits; ++i) {
+          const uint64_t ad = sDesc[(kc * kDigits + i) * 2];
+          const uint64_t bd = sDesc[(kc * kDigits) * 2 + 1];
+          const uint32_t dt = tbase + (uint32_t)((kc * kClasses + i) * NP);
+          const uint32_t id = tc::idesc_f16_f32(kTileRows, (kDigits - i) * NP);
 #pragma unroll
-          for (int i = 0; i <= g; ++i) {
-            const uint64_t ad = sDesc[(kc * kDigits + i) * 2];
-            const uint64_t bd = sDesc[(kc * kDigits + (g - i)) * 2 + 1];
-            const uint32_t dt = tbase + (uint32_t)((kc * kClasses + g) * NP);
-#pragma unroll
-            for (int ks = 0; ks < kKChunk / 16; ++ks)
-              tc::mma_bf16(dt, ad + (uint64_t)(ks * 2 * kLBO >> 4), bd + (uint64_t)(ks * 2 * kLBO >> 4), idesc,
-                           (i > 0 || ks > 0) ? 1u : 0u);
-          }
+          for (int ks = 0; ks < kKChunk / 16; ++ks)
+            tc::mma_f16(dt, ad + (uint64_t)(ks * 2 * kLBO >> 4), bd + (uint64_t)(ks * 2 * kLBO >> 4), id,
+                         (i > 0 || ks > 0) ? 1u : 0u);
+        }
       tc::mma_commit(bar);
     }
     // ---- wait for the products (bounded), then read row `row`'s accumulators
-    if (!tc::mbar_wait(bar, phase, kWaitSpins)) {
+    if (!wait_sleep(bar, phase)) {
       ok = false;
       failed = true;
-      tc::mbar_wait(bar, phase, kWaitSpins);  // let the MMAs in flight finish before TMEM is reused
+      wait_sleep(bar, phase);  // let the MMAs in flight finish before TMEM is reused
     }
     phase ^= 1;
     tc::fence_after_sync();
@@ -412,6 +424,426 @@ static size_t tc_smem_bytes(int nkc, int NP) {
          4 * 2 * kTileRows + 64;
 }
 
+// ---------------------------------------------------------------- pipelined form (K <= 32)
+// The same product with the phases of consecutive tiles overlapped.  One persistent CTA per SM
+// with four warp roles:
+//   warps 0-7   split V rows into digits: a unit is 8 columns of one row, unit u = row
+//               + 128 cb (cb < ceil(K / 8)), thread t takes units t and t + 256, so the work
+//               follows K; units write the digit tiles of buffer t % 2;
+//   warp 16     (one thread) issues the TMA copies of tile t's V rows into staging buffer t % 2;
+//   warp 17     (one thread) issues tile t's MMAs into TMEM buffer t % 2 and owns the TMEM
+//               allocation;
+//   warps 8-15  read tile t's accumulators (TMEM lane quarter = warp % 4, two threads per row,
+//               alternate groups of four results), assemble and store them; with beta != 0 and
+//               N <= 16 the rows of Out for tile t + 1 are loaded while tile t is assembled.
+// V staging, digit tiles and accumulators are double-buffered, so tile t + 1 is split while tile
+// t's products run and its results are assembled.  Five mbarrier pairs hand each buffer on:
+// vfull (TMA -> splitters), vempty (splitters -> TMA), afull (splitters -> MMA and
+// epilogue: digits and row exponents written), mdone (tcgen05.commit -> splitters and
+// epilogue: products complete, digit tiles free), tempty (epilogue -> MMA and splitters: TMEM
+// and row exponents read).  The k-th use of a buffer waits for phase parity k & 1; a
+// barrier cannot run two phases ahead of a waiter because every phase of it needs a phase the
+// waiter itself completes first.  The splitters meet twice per tile at a named barrier that
+// also ORs their wait failures, so they leave the loop together.  Every wait is bounded; a
+// wait that runs out marks the CTA aborted, the other roles stop at their next wait, the
+// epilogue writes NaN to the rows of the tiles it has not finished, and the TMA copies and MMAs
+// in flight are waited for (again bounded) before TMEM is freed.
+namespace {
+constexpr int kPipeWarps = 18;
+constexpr int kPipeThreads = kPipeWarps * 32;
+constexpr int kSplitWarps = 8, kEpiWarps = 8;
+constexpr int kSplitThreads = kSplitWarps * 32;
+constexpr int kProdWarp = 16, kMmaWarp = 17;
+
+struct PipeBars {
+  uint64_t vfull[2], vempty[2], afull[2], mdone[2], tempty[2];
+};
+
+// Shared-memory bytes of tc_combine_pipe_kernel for padded N.
+constexpr size_t pipe_smem_bytes(int NP) {
+  return (size_t)2 * kDigits * kATileBytes + (size_t)kDigits * NP * kKChunk * 2 +
+         (size_t)2 * kTileRows * kKChunk * 8 + sizeof(PipeBars) + 8 + 4 * kMaxN + 4 * 6 * kTileRows + 64;
+}
+}  // namespace
+
+// Bounded wait for one phase of a pipeline barrier, sleeping between polls; false when the CTA
+// has aborted or the polls ran out, which also marks it aborted.  The warp form gives every
+// lane the same answer.
+__device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  bool ok = tc::mbar_wait(bar, parity, 1);   // a completed phase returns at once
+  for (uint32_t r = 0; r < kPipePolls && !ok; ++r) {
+    ok = tc::mbar_wait_sleep(bar, parity, 1, kPipeSleepNs);
+    if (!ok && *abort_flag) break;
+  }
+  if (!ok) *abort_flag = 1;
+  return ok;
+}
+__device__ __forceinline__ bool pipe_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  return __all_sync(0xffffffffu, pipe_wait(bar, parity, abort_flag));
+}
+
+// Named barrier `id` over `nthreads` threads that returns the OR of every thread's `p`.
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+template <int BV, int NP>
+__global__ void __launch_bounds__(kPipeThreads, 1) tc_combine_pipe_kernel(const TcArgs a) {
+  constexpr uint32_t kBufCols = NP == 32 ? 256u : 128u;  // TMEM columns per buffer (7 NP used)
+  constexpr size_t kBTile = (size_t)NP * kKChunk * 2;
+  constexpr int kVBuf = kTileRows * kKChunk;              // doubles per V staging buffer
+  constexpr int W = BV < 8 ? BV : 8;                      // columns of one block read per step
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;                                        // [2][7] x 8 KB
+  unsigned char* sB = sA + 2 * kDigits * kATileBytes;              // [7] x NP*64
+  double* sV = reinterpret_cast<double*>(sB + kDigits * kBTile);   // [2][32 / BV][128][BV]
+  PipeBars* bars = reinterpret_cast<PipeBars*>(sV + 2 * kVBuf);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  int* sF = reinterpret_cast<int*>(tslot + 2);                     // N column exponents of Y
+  int* sE = sF + kMaxN;                                            // [2][128] row exponents
+  int* sEp = sE + 2 * kTileRows;                                   // [4][128] unit exponents
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.bdig);
+    int4* dst = reinterpret_cast<int4*>(sB);
+    for (int e = tid; e < (int)(kDigits * kBTile / 16); e += kPipeThreads) dst[e] = src[e];
+    for (int q = tid; q < a.N; q += kPipeThreads) sF[q] = a.fexp[q];
+    // digit columns at or beyond K stay zero in both buffers
+    int4* z = reinterpret_cast<int4*>(sA);
+    for (int e = tid; e < 2 * kDigits * kATileBytes / 16; e += kPipeThreads) z[e] = make_int4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars->vfull[b], 1);
+      tc::mbar_init(&bars->vempty[b], kSplitWarps);
+      tc::mbar_init(&bars->afull[b], kSplitWarps);
+      tc::mbar_init(&bars->mdone[b], 1);
+      tc::mbar_init(&bars->tempty[b], kEpiWarps);
+    }
+    *abort_flag = 0;
+    tc::mbar_fence_init();
+  }
+  if (warp == kMmaWarp) {
+    tc::tmem_alloc(tslot, 2 * kBufCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int64_t ntiles = (a.n + kTileRows - 1) / kTileRows;
+  const int64_t cnt = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto tile_of = [&](int64_t it) { return (int64_t)blockIdx.x + it * gridDim.x; };
+  auto bulk_ok = [&](int64_t t) {
+    return a.bulk && ((uint64_t)min((int64_t)kTileRows, a.n - t * kTileRows) * BV * 8) % 16 == 0;
+  };
+
+  if (warp == kProdWarp) {
+    // ---- TMA: V rows of tile `it` into staging buffer it % 2
+    int64_t issued = 0;
+    if (lane == 0) {
+      const int nblk = a.K / BV;
+      for (int64_t it = 0; it < cnt; ++it) {
+        const int b = (int)(it & 1);
+        const uint32_t k = (uint32_t)(it >> 1);
+        if (k > 0 && !pipe_wait(&bars->vempty[b], (k - 1) & 1, abort_flag)) break;
+        const int64_t r0 = tile_of(it) * kTileRows;
+        if (bulk_ok(tile_of(it))) {
+          const uint32_t bytes = (uint32_t)(min((int64_t)kTileRows, a.n - r0) * BV * 8);
+          tc::mbar_arrive_expect_tx(&bars->vfull[b], bytes * (uint32_t)nblk);
+          for (int j = 0; j < nblk; ++j)
+            tc::bulk_g2s(sV + (size_t)b * kVBuf + (size_t)j * kTileRows * BV, a.vblk[j] + r0 * BV, bytes,
+                         &bars->vfull[b]);
+        } else {
+          tc::mbar_arrive(&bars->vfull[b]);   // ragged or unaligned tile: splitters load V directly
+        }
+        issued = it + 1;
+      }
+      // copies in flight complete before the CTA exits (immediate unless the CTA aborted)
+      for (int b = 0; b < 2; ++b) {
+        const int64_t uses = (issued + 1 - b) / 2;
+        if (uses > 0) wait_sleep(&bars->vfull[b], (uint32_t)((uses - 1) & 1));
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- MMA issue: digit i of A against the B digit tiles 0..6-i stacked as one (7-i) NP-row
+    // operand; the product's column block j lands on class i + j's accumulator (TMEM column
+    // (i + j) NP of buffer it % 2)
+    int64_t committed = 0;
+    if (lane == 0) {
+      const int ksteps = a.K <= 16 ? 1 : 2;   // K-steps of 16 holding non-zero digits
+      const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
+      const uint64_t bd = tc::smem_desc(sb0, kLBO, kSBO);
+      for (int64_t it = 0; it < cnt; ++it) {
+        const int b = (int)(it & 1);
+        const uint32_t k = (uint32_t)(it >> 1);
+        if (!pipe_wait(&bars->afull[b], k & 1, abort_flag)) break;
+        if (k > 0 && !pipe_wait(&bars->tempty[b], (k - 1) & 1, abort_flag)) break;
+        tc::fence_after_sync();
+        const uint32_t dbase = tbase + (uint32_t)b * kBufCols;
+#pragma unroll
+        for (int i = 0; i < kDigits; ++i) {
+          const uint64_t ad = tc::smem_desc(sa0 + (uint32_t)((b * kDigits + i) * kATileBytes), kLBO, kSBO);
+          const uint32_t idesc = tc::idesc_f16_f32(kTileRows, (kDigits - i) * NP);
+          for (int ks = 0; ks < ksteps; ++ks)
+            tc::mma_f16(dbase + (uint32_t)(i * NP), ad + (uint64_t)(ks * 2 * kLBO >> 4),
+                        bd + (uint64_t)(ks * 2 * kLBO >> 4), idesc, (i > 0 || ks > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&bars->mdone[b]);
+        committed = it + 1;
+      }
+      for (int b = 0; b < 2; ++b) {
+        const int64_t uses = (committed + 1 - b) / 2;
+        if (uses > 0) wait_sleep(&bars->mdone[b], (uint32_t)((uses - 1) & 1));
+      }
+    }
+  } else if (warp < kSplitWarps) {
+    // ---- split: units of 8 columns of one row
+    const int nunits = kTileRows * ((a.K + 7) >> 3);
+    for (int64_t it = 0; it < cnt; ++it) {
+      const int b = (int)(it & 1);
+      const uint32_t k = (uint32_t)(it >> 1);
+      const int64_t tile = tile_of(it);
+      const bool bulk = bulk_ok(tile);
+      const bool ok = pipe_wait_warp(&bars->vfull[b], k & 1, abort_flag);
+      double v[2][8];
+      int emax[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int u = tid + kSplitThreads * j;
+        if (u < nunits) {
+          const int row = u & (kTileRows - 1), cb = u >> 7;
+          const int64_t r = tile * kTileRows + row;
+          const bool live = r < a.n;
+#pragma unroll
+          for (int c0 = 0; c0 < 8; c0 += W) {
+            const int c = cb * 8 + c0;
+            if (live && c < a.K) {
+              const double* src = bulk ? sV + (size_t)b * kVBuf + ((size_t)(c / BV) * kTileRows + row) * BV + c % BV
+                                       : a.vblk[c / BV] + r * BV + c % BV;
+              if (bulk && W % 2 == 0) {
+#pragma unroll
+                for (int p = 0; p < W; p += 2) {
+                  const double2 x = *reinterpret_cast<const double2*>(src + p);
+                  v[j][c0 + p] = x.x;
+                  v[j][c0 + p + 1] = x.y;
+                }
+              } else {
+#pragma unroll
+                for (int p = 0; p < W; ++p) v[j][c0 + p] = src[p];
+              }
+            } else {
+#pragma unroll
+              for (int p = 0; p < W; ++p) v[j][c0 + p] = 0.0;
+            }
+          }
+          int e = 0;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) e = max(e, exp_field(v[j][c]));
+          sEp[cb * kTileRows + row] = e;
+        }
+      }
+      if (bar_or(1, kSplitThreads, !ok)) break;   // V read, unit exponents written
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->vempty[b]);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int u = tid + kSplitThreads * j;
+        if (u < nunits) {
+          const int row = u & (kTileRows - 1);
+          for (int c = 0; c < nunits / kTileRows; ++c) emax[j] = max(emax[j], sEp[c * kTileRows + row]);
+        }
+      }
+      // digit tiles and row exponents of this buffer are free once tile it - 2's products and
+      // results are done
+      bool ok2 = true;
+      if (k > 0) ok2 = pipe_wait_warp(&bars->mdone[b], (k - 1) & 1, abort_flag) &&
+                       pipe_wait_warp(&bars->tempty[b], (k - 1) & 1, abort_flag);
+      if (bar_or(1, kSplitThreads, !ok2)) break;  // unit exponents read
+      unsigned char* sAb = sA + (size_t)b * kDigits * kATileBytes;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int u = tid + kSplitThreads * j;
+        if (u < nunits) {
+          const int row = u & (kTileRows - 1), cb = u >> 7;
+          if (cb == 0) sE[b * kTileRows + row] = emax[j];
+          uint32_t w[kDigits][4];
+          split_pair_f16(v[j][0], v[j][1], emax[j], w, 0);
+          split_pair_f16(v[j][2], v[j][3], emax[j], w, 1);
+          split_pair_f16(v[j][4], v[j][5], emax[j], w, 2);
+          split_pair_f16(v[j][6], v[j][7], emax[j], w, 3);
+          const uint32_t off = tile_off(row, cb * 8);
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i)
+            *reinterpret_cast<uint4*>(sAb + (size_t)i * kATileBytes + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        }
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->afull[b]);
+    }
+  } else {
+    // ---- epilogue: warps 8-15, TMEM lane quarter warp % 4; the two warps of a quarter take
+    // alternate groups of two results (q0 = 2 half + 4 jj)
+    const int quarter = warp & 3, half = (warp - kSplitWarps) >> 2;
+    const int row = quarter * 32 + lane;
+    const bool add_out = a.beta != 0.0;
+    const int ngroups = (a.N - 2 * half + 3) / 4;        // this thread's groups of two results
+    // rows of Out loaded ahead of their tile: one group per thread (N <= 4) two tiles ahead into
+    // slot it % 2, two groups (N <= 8) one tile ahead into slot = group
+    const int pf = !add_out ? 0 : ngroups <= 1 ? 2 : ngroups == 2 ? 1 : 0;
+    double opf[2][2];
+    auto load_grp = [&](int64_t it, int jj, int slot) {
+      const int64_t r = tile_of(it) * kTileRows + row;
+      const int q0 = 2 * half + 4 * jj;
+      if (r >= a.n || q0 >= a.N) return;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + u;
+        const double x = q < a.N ? a.oblk[q / BV][r * BV + q % BV] : 0.0;
+        if (slot == 0) opf[0][u] = x;
+        else opf[1][u] = x;
+      }
+    };
+    if (pf == 2) {
+      if (cnt > 0) load_grp(0, 0, 0);
+      if (cnt > 1) load_grp(1, 0, 1);
+    } else if (pf == 1 && cnt > 0) {
+      load_grp(0, 0, 0);
+      load_grp(0, 1, 1);
+    }
+    int64_t it = 0;
+    for (; it < cnt; ++it) {
+      const int b = (int)(it & 1);
+      const uint32_t k = (uint32_t)(it >> 1);
+      if (!pipe_wait_warp(&bars->afull[b], k & 1, abort_flag)) break;
+      if (!pipe_wait_warp(&bars->mdone[b], k & 1, abort_flag)) break;
+      tc::fence_after_sync();
+      const int64_t r = tile_of(it) * kTileRows + row;
+      const bool live = r < a.n;
+      const int emax = sE[b * kTileRows + row];
+      const int ebase = emax - 2108 + kAsmShift;
+      const uint32_t lane_addr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * kBufCols;
+      // the accumulators of group jj + 1 are loaded while group jj is assembled
+      uint32_t nxt[kClasses][2];
+      if (ngroups > 0) {
+#pragma unroll
+        for (int g = 0; g < kClasses; ++g) tc::tmem_ld2(lane_addr + (uint32_t)(g * NP + 2 * half), nxt[g]);
+      }
+      for (int jj = 0; jj < ngroups; ++jj) {
+        const int q0 = 2 * half + 4 * jj;
+        tc::tmem_ld_wait();
+        uint32_t acc[kClasses][2];
+#pragma unroll
+        for (int g = 0; g < kClasses; ++g) {
+          tc::reg_after_wait(nxt[g]);
+          acc[g][0] = nxt[g][0];
+          acc[g][1] = nxt[g][1];
+        }
+        if (jj + 1 < ngroups) {
+#pragma unroll
+          for (int g = 0; g < kClasses; ++g) tc::tmem_ld2(lane_addr + (uint32_t)(g * NP + q0 + 4), nxt[g]);
+        }
+        if (jj == ngroups - 1) {
+          // TMEM buffer and row exponent read: the buffer goes back to the MMA issuer
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+        }
+        double y[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int64_t hi = (int64_t)acc_int(acc[0][u]) * 65536 + (int64_t)acc_int(acc[1][u]) * 256 +
+                             (int64_t)acc_int(acc[2][u]);
+          const int64_t lo = (int64_t)acc_int(acc[3][u]) * 16777216 + (int64_t)acc_int(acc[4][u]) * 65536 +
+                             (int64_t)acc_int(acc[5][u]) * 256 + (int64_t)acc_int(acc[6][u]);
+          const double x = assemble(hi, lo, ebase + sF[min(q0 + u, kMaxN - 1)]);
+          y[u] = emax > 0 ? x : 0.0;
+        }
+        if (live) {
+          if (add_out) {
+            if (pf != 0) {
+              const bool s1 = pf == 2 ? (it & 1) != 0 : jj != 0;
+#pragma unroll
+              for (int u = 0; u < 2; ++u) y[u] = fma(a.beta, s1 ? opf[1][u] : opf[0][u], y[u]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int q = q0 + u;
+                if (q < a.N) y[u] = fma(a.beta, a.oblk[q / BV][r * BV + q % BV], y[u]);
+              }
+            }
+          }
+          if (BV >= 2 && q0 + 2 <= a.N && a.ovec) {
+            *reinterpret_cast<double2*>(a.oblk[q0 / BV] + r * BV + q0 % BV) = make_double2(y[0], y[1]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int q = q0 + u;
+              if (q < a.N) a.oblk[q / BV][r * BV + q % BV] = y[u];
+            }
+          }
+        }
+      }
+      if (ngroups == 0) {
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      }
+      if (pf == 2 && it + 2 < cnt) load_grp(it + 2, 0, (int)(it & 1));
+      if (pf == 1 && it + 1 < cnt) {
+        load_grp(it + 1, 0, 0);
+        load_grp(it + 1, 1, 1);
+      }
+    }
+    // after an abort: the rows of every tile not finished read NaN
+    for (; it < cnt; ++it) {
+      const int64_t r = tile_of(it) * kTileRows + row;
+      if (r < a.n)
+        for (int jj = 0; jj < ngroups; ++jj)
+          for (int q = 2 * half + 4 * jj; q < min(a.N, 2 * half + 4 * jj + 2); ++q)
+            a.oblk[q / BV][r * BV + q % BV] = __longlong_as_double(0x7FF8000000000000ll);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid == 0 && *abort_flag) atomicExch(a.status, 1);
+  if (warp == kMmaWarp) tc::tmem_dealloc(tbase, 2 * kBufCols);
+}
+
+template <int BV, int NP>
+static int launch_tc_combine_pipe_np(const TcArgs& a, cudaStream_t s) {
+  static KernelSetup ks;
+  const void* fn = reinterpret_cast<const void*>(tc_combine_pipe_kernel<BV, NP>);
+  constexpr size_t smem = pipe_smem_bytes(NP);
+  FE_TRY(kernel_configure(ks, fn, (int)smem));
+  const int64_t ntiles = ceil_div(a.n, kTileRows);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms()));
+  tc_combine_pipe_kernel<BV, NP><<<(unsigned)grid, kPipeThreads, smem, s>>>(a);
+  count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+template <int BV>
+static int launch_tc_combine_pipe(const TcArgs& a, cudaStream_t s) {
+  if (a.NP == 16) return launch_tc_combine_pipe_np<BV, 16>(a, s);
+  return launch_tc_combine_pipe_np<BV, 32>(a, s);
+}
+
 bool tc_combine_supported(const BlockSet& V, const BlockSet& Out, fe_dtype dt) {
   const int K = V.nv * V.bv, N = Out.nv * Out.bv;
   return dt == FE_F64 && V.bv == Out.bv && V.ld == V.bv && Out.ld == Out.bv && K >= 1 && K <= kMaxK &&
@@ -455,7 +887,11 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
     a.vblk[j] = static_cast<const double*>(V.blk[j]);
     if (reinterpret_cast<uintptr_t>(V.blk[j]) % 16) a.bulk = 0;
   }
-  for (int o = 0; o < Out.nv; ++o) a.oblk[o] = const_cast<double*>(static_cast<const double*>(Out.blk[o]));
+  a.ovec = 1;
+  for (int o = 0; o < Out.nv; ++o) {
+    a.oblk[o] = const_cast<double*>(static_cast<const double*>(Out.blk[o]));
+    if (reinterpret_cast<uintptr_t>(Out.blk[o]) % 16) a.ovec = 0;
+  }
   // scratch: B digit tiles, column exponents, status word
   const size_t bbytes = (size_t)a.nkc * kDigits * a.NP * kKChunk * 2;
   double* scr = small_scratch(17, bbytes / 8 + kMaxN + 2);
@@ -468,6 +904,15 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
                                      const_cast<int*>(a.fexp));
   count_launch();
   FE_CUDA(cudaGetLastError());
+  if (a.nkc == 1) {
+    switch (BV) {
+      case 1: return launch_tc_combine_pipe<1>(a, s);
+      case 2: return launch_tc_combine_pipe<2>(a, s);
+      case 4: return launch_tc_combine_pipe<4>(a, s);
+      case 8: return launch_tc_combine_pipe<8>(a, s);
+      case 16: return launch_tc_combine_pipe<16>(a, s);
+    }
+  }
   // two CTAs per SM when their TMEM (256 columns each) fits; the shared-memory request keeps a
   // third CTA off the SM, so no CTA waits in tcgen05.alloc
   const bool two = a.nkc * kClasses * a.NP <= 256;
@@ -578,7 +1023,7 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
   tc::fence_after_sync();
   if (tid == 0 && (int64_t)blockIdx.x < ntiles && bulk_ok(blockIdx.x)) issue(blockIdx.x);
   const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+  const uint32_t idesc = tc::idesc_f16_f32(128, NP);
   const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
   const int nout = KV * bw;
   double acc[(kGramMaxKV * kGramMaxBW + 255) / 256];
@@ -616,10 +1061,10 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
     const bool bulk = bulk_ok(tile);
     bool ok = true;
     if (bulk) {
-      ok = tc::mbar_wait(lbar, lphase, kWaitSpins);
+      ok = wait_sleep(lbar, lphase);
       if (!ok) {
         failed = true;
-        tc::mbar_wait(lbar, lphase, kWaitSpins);  // no copy left in flight
+        wait_sleep(lbar, lphase);  // no copy left in flight
       }
       lphase ^= 1;
     }
@@ -657,16 +1102,7 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const double x0 = x[k][2 * e], x1 = x[k][2 * e + 1];
-          const uint64_t m0 = aligned_sig56(x0, emax), m1 = aligned_sig56(x1, emax);
-          const uint32_t sg = (uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15 |
-                              (uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31;
-          w[0][e] = digit_pair56<0>(m0, m1) | sg;
-          w[1][e] = digit_pair56<1>(m0, m1) | sg;
-          w[2][e] = digit_pair56<2>(m0, m1) | sg;
-          w[3][e] = digit_pair56<3>(m0, m1) | sg;
-          w[4][e] = digit_pair56<4>(m0, m1) | sg;
-          w[5][e] = digit_pair56<5>(m0, m1) | sg;
-          w[6][e] = digit_pair56<6>(m0, m1) | sg;
+          split_pair_f16(x0, x1, emax, w, e);
         }
 #pragma unroll
         for (int i = 0; i < kDigits; ++i) {
@@ -693,14 +1129,14 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
         for (int ks = 0; ks < kGramRows / 16; ++ks) {
           const uint64_t ad = tc::smem_desc(sa0 + mt * kGATile + ks * 2 * kCoreBytes, kCoreBytes, kGSBO);
           const uint64_t bd = tc::smem_desc(sb0 + ks * 2 * kCoreBytes, kCoreBytes, kGSBO);
-          tc::mma_bf16(tbase + (uint32_t)(mt * NP), ad, bd, idesc, ks > 0 ? 1u : 0u);
+          tc::mma_f16(tbase + (uint32_t)(mt * NP), ad, bd, idesc, ks > 0 ? 1u : 0u);
         }
       tc::mma_commit(bar);
     }
-    if (!tc::mbar_wait(bar, phase, kWaitSpins)) {
+    if (!wait_sleep(bar, phase)) {
       ok = false;
       failed = true;
-      tc::mbar_wait(bar, phase, kWaitSpins);
+      wait_sleep(bar, phase);
     }
     phase ^= 1;
     tc::fence_after_sync();

@@ -111,6 +111,77 @@ def test_tc_and_fma_engines_agree():
     assert (np.abs(a - b) <= 2e-13 * absprod).all()
 
 
+UPDATE_SHAPES = [  # (n, nv, bv): W (n x bv) = W - V C, K = nv*bv
+    (1, 1, 4), (129, 8, 4), (4097, 3, 4), (65536, 8, 4), (10001, 5, 8), (3000, 2, 16),
+    (777, 17, 1), (2050, 12, 2), (5000, 9, 4), (300, 16, 4)]
+
+
+@pytest.mark.parametrize("shape", UPDATE_SHAPES)
+@pytest.mark.parametrize("aligned", [True, False])
+def test_tc_update_matches_oracle(shape, aligned):
+    """W <- W - V C on the tensor cores (the second Gram-Schmidt pass's update, alpha = -1,
+    beta = 1; fe_block_update_ex) against the oracle's MvTimesMatAddMv: within the stated
+    split-product bound plus the rounding of the FP64 addition, and within 1e-13 (|V||C| + |W|).
+    `aligned` False places W 8 bytes off a 16-byte boundary (scalar stores)."""
+    t = torch()
+    n, nv, bv = shape
+    rng = np.random.default_rng(n + 31 * nv + bv)
+    Vh = rng.standard_normal((nv, n, bv))
+    Ch = rng.standard_normal((nv * bv, bv))
+    Wh = rng.standard_normal((n, bv))
+    buf = t.zeros(n * bv + 2, dtype=t.float64, device="cuda")
+    off = 0 if aligned else 1
+    W = buf[off:off + n * bv].view(n, bv)
+    W.copy_(t.from_numpy(Wh))
+    fe.block_update(to_dev(Vh), to_dev(Ch), W, alpha=-1.0, beta=1.0, engine="tc")
+    t.cuda.synchronize()
+    got = W.cpu().numpy()
+    AA = _flat(Vh)
+    ref = blockops.mv_times_mat_add_mv(-1.0, AA, Ch, 1.0, Wh.copy())
+    K = AA.shape[1]
+    err = np.abs(got - ref)
+    vc = np.abs(AA) @ np.abs(Ch)
+    stated = (2.0 ** -49 * K * np.abs(AA).max(axis=1)[:, None] * np.abs(Ch).max(axis=0)[None, :]
+              + 2.0 ** -52 * (vc + np.abs(Wh)) + 2.0 ** -1022)
+    assert (err <= stated).all(), f"stated bound: worst {np.max(err - stated):.3e}"
+    assert (err <= 1e-13 * (vc + np.abs(Wh))).all()
+    assert buf[:off].abs().sum().item() == 0 and buf[off + n * bv:].abs().sum().item() == 0
+
+
+def test_tc_update_engines_agree_and_reject():
+    """fma and tc routes of fe_block_update_ex agree to 2e-13 (|V||C| + |W|); the tensor-core
+    route rejects bv != bw, K > 64 and FP32 blocks, and auto falls back to the FMA kernels."""
+    t = torch()
+    rng = np.random.default_rng(3)
+    n, nv, bv = 50000, 8, 4
+    Vh = rng.standard_normal((nv, n, bv))
+    Ch = rng.standard_normal((nv * bv, bv))
+    Wh = rng.standard_normal((n, bv))
+    outs = {}
+    for eng in ("fma", "tc", "auto"):
+        W = to_dev(Wh)
+        fe.block_update(to_dev(Vh), to_dev(Ch), W, alpha=0.5, beta=-2.0, engine=eng)
+        outs[eng] = W.cpu().numpy()
+    assert np.array_equal(outs["tc"], outs["auto"])
+    bound = 2e-13 * (np.abs(_flat(Vh)) @ np.abs(Ch) * 0.5 + 2.0 * np.abs(Wh))
+    assert (np.abs(outs["tc"] - outs["fma"]) <= bound).all()
+    W8 = t.zeros((64, 8), dtype=t.float64, device="cuda")
+    with pytest.raises(fe.FeError):   # bv != bw
+        fe.block_update(t.zeros((2, 64, 4), dtype=t.float64, device="cuda"),
+                        t.zeros((8, 8), dtype=t.float64, device="cuda"), W8, engine="tc")
+    with pytest.raises(fe.FeError):   # K = 68
+        fe.block_update(t.zeros((17, 64, 4), dtype=t.float64, device="cuda"),
+                        t.zeros((68, 4), dtype=t.float64, device="cuda"),
+                        t.zeros((64, 4), dtype=t.float64, device="cuda"), engine="tc")
+    fe.block_update(t.zeros((17, 64, 4), dtype=t.float64, device="cuda"),
+                    t.zeros((68, 4), dtype=t.float64, device="cuda"),
+                    t.zeros((64, 4), dtype=t.float64, device="cuda"), engine="auto")
+    with pytest.raises(fe.FeError):   # FP32 blocks
+        fe.block_update(t.zeros((2, 64, 4), dtype=t.float32, device="cuda"),
+                        t.zeros((8, 4), dtype=t.float64, device="cuda"),
+                        t.zeros((64, 4), dtype=t.float32, device="cuda"), engine="tc")
+
+
 def test_tc_engine_rejects_unsupported():
     t = torch()
     V = t.zeros((17, 64, 4), dtype=t.float64, device="cuda")     # K = 68 > 64
