@@ -56,7 +56,7 @@ typedef enum { FE_START_RANDOM = 0, FE_START_USER = 1, FE_START_LEARNED = 2 } fe
 /* Arithmetic of the FP64 dense block products that support it (fe_block_combine and the
  * solver's restart and Ritz-vector products): FE_ENGINE_AUTO = tensor cores where the shape is
  * supported, FMA otherwise; FE_ENGINE_FMA = FP64 fused multiply-adds; FE_ENGINE_TC = tensor
- * cores (exact BF16 digit products, see fe_block_combine), FE_ERR_INVALID where unsupported. */
+ * cores (exact FP16 digit products, see fe_block_combine), FE_ERR_INVALID where unsupported. */
 typedef enum { FE_ENGINE_AUTO = 0, FE_ENGINE_FMA = 1, FE_ENGINE_TC = 2 } fe_engine;
 
 /* Message for the last failing call on this thread ("" if none).  Never NULL. */
@@ -218,7 +218,7 @@ int fe_block_gram(const void* V, int64_t n, int nv, int bv, const void* W, int b
  * FE_ENGINE_AUTO.  For FP64 blocks with nv*bv <= 36 and bw in {1, 2, 4, 8}, FE_ENGINE_TC, and
  * FE_ENGINE_AUTO when nv*bv >= 16 (where it is the faster kernel), run on the tensor cores: within every 128-row tile each column of V and W is cut,
  * relative to its largest exponent in the tile, into seven 8-bit digits; one MMA per 16 rows
- * forms every digit product (exact BF16 x BF16 -> FP32 sums of 128 terms), and the tile's
+ * forms every digit product (exact FP16 x FP16 -> FP32 sums of 128 terms), and the tile's
  * products are assembled in integer arithmetic and added in FP64, so that the error of a tile's
  * contribution is at most 2^-50 * 128 * max|V[., c]| * max|W[., q]| over its rows (plus the
  * FP64 roundings of the sums over tiles); entries must be finite, subnormals are read as zero.
@@ -288,7 +288,7 @@ int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* 
  * 1 <= nv <= 128, 1 <= nout <= 128, bv in {1, 2, 4, 8, 16}.
  * engine (fe_engine): for FP64 with K = nv*bv <= 64 and N = nout*bv <= 32, FE_ENGINE_AUTO and
  * FE_ENGINE_TC use the tensor cores: every V row is cut, relative to its largest exponent, into
- * seven 8-bit digits, every Y column likewise; the digit products (exact in BF16 x BF16 -> FP32
+ * seven 8-bit digits, every Y column likewise; the digit products (exact in FP16 x FP16 -> FP32
  * for K <= 32 per accumulator) of weight classes i + j <= 6 are summed on the tensor cores and
  * assembled in 128-bit integer arithmetic, so that |error| <= 2^-49 K max_c|V[r][c]|
  * max_c|Y[c][q]| + 2^-52 |result| (results below 2^-1022 flush to zero; entries must be finite,

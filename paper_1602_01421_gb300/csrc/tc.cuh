@@ -6,7 +6,7 @@
 //     thread, completion signalled on an mbarrier by tcgen05.commit;
 //   * tcgen05.ld: each warp of a warpgroup reads its 32 TMEM lanes into registers.
 // Operand tiles use the no-swizzle K-major canonical layout: 8 x 16-byte "core matrices"
-// (8 rows of 8 bf16), element (row, k) at (row / 8) * SBO + (k / 8) * LBO + (row % 8) * 16 +
+// (8 rows of 8 16-bit values), element (row, k) at (row / 8) * SBO + (k / 8) * LBO + (row % 8) * 16 +
 // (k % 8) * 2 bytes; the shared-memory matrix descriptor carries start address, LBO and SBO.
 #pragma once
 #include <stdint.h>
@@ -166,6 +166,13 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
+// The same for 1 column.
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  return r;
+}
+__device__ __forceinline__ void reg_after_wait(uint32_t& r) { asm volatile("" : "+r"(r)); }
 // The same for 2 consecutive columns.
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));

@@ -1,11 +1,11 @@
-// FP64 tall-skinny products on the BF16 tensor cores by exact digit splitting ("split
+// FP64 tall-skinny products on the FP16 tensor cores by exact digit splitting ("split
 // products"; the Ozaki scheme, Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012), for
 // the restart / Ritz-vector product of the Block Krylov-Schur solver (Table 1 "op1" shape,
 // V_out = V Y with V n x K, Y K x N, K <= 64 and N <= 32):
 //
 //   * every V row is scaled by its largest binary exponent and its 53-bit aligned significands
 //     are cut into seven 8-bit digits (sign-magnitude, so every digit is an integer in
-//     [-255, 255] and exact in BF16): V[r][c] = 2^(Er - 1075) sum_i d_i[r][c] 2^(45 - 8 i);
+//     [-255, 255] and exact in FP16): V[r][c] = 2^(Er - 1075) sum_i d_i[r][c] 2^(45 - 8 i);
 //   * every Y column likewise by its largest exponent: Y[c][q] = 2^(Fq - 1075) sum_j e_j 2^(45-8j);
 //   * the digit products are exact in the tensor core's FP32 accumulator as long as each
 //     accumulator sums at most 2^24 / 255^2 = 258 of them: one accumulator per digit-weight
@@ -49,12 +49,12 @@ constexpr int kThreads = 256;
 constexpr uint32_t kPipePolls = 1u << 16;
 constexpr uint32_t kPipeSleepNs = 32768;
 constexpr int kCoreBytes = 128;      // 8 rows x 16 bytes
-// A (V digits): per (K chunk, digit) a 128 x 32 bf16 tile = 8 KB; SBO = 4 core matrices
+// A (V digits): per (K chunk, digit) a 128 x 32 FP16 tile = 8 KB; SBO = 4 core matrices
 constexpr int kATileBytes = kTileRows * kKChunk * 2;
 constexpr uint32_t kLBO = kCoreBytes;               // next core matrix along K
 constexpr uint32_t kSBO = (kKChunk / 8) * kCoreBytes;  // next 8-row group
 
-// Byte offset of element (row, k) of a [rows x 32] bf16 K-major tile (k < 32).
+// Byte offset of element (row, k) of a [rows x 32] 16-bit K-major tile (k < 32).
 __host__ __device__ inline uint32_t tile_off(int row, int k) {
   return (uint32_t)((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
 }
@@ -938,7 +938,8 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
 // products below 2^16 and is exact.  TMEM lane (i, c) then forms T_i = sum_j D 2^(8 (6 - j))
 // for each q in 64-bit integers and converts it, scaled by 2^(8 (6 - i)) and the tile's column
 // exponents, to FP64; the seven slices i are added in FP64 (smallest first) into the CTA's
-// accumulator of G, and the CTAs' partial Gram matrices are added in a fixed order.
+// accumulator of G, and the CTAs' partial Gram matrices are added in a fixed order.  (The
+// pipelined form below adds the slices exactly in 128-bit integers and rounds once per tile.)
 // Error per tile: 2^-50 * 128 * max|V[., c]| * max|W[., q]| over the tile's rows, plus the FP64
 // roundings of the sums over slices, tiles and CTAs.
 namespace {
@@ -970,7 +971,7 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
   const int KV = a.KV, nmt = a.nmt;
   const int ncol = KV + bw;
   unsigned char* sA = smem;                                   // nmt x 32 KB
-  unsigned char* sB = sA + (size_t)nmt * kGATile;             // NP x 128 bf16
+  unsigned char* sB = sA + (size_t)nmt * kGATile;             // NP x 128 FP16
   // staged rows: V block j at sX + j * XS, W at sX + nvb * XS; XS = 128 rows + 4 doubles of
   // padding, so that the blocks' rows fall on different shared-memory banks
   double* sX = reinterpret_cast<double*>(sB + (size_t)NP * kGramRows * 2);
@@ -1196,6 +1197,332 @@ __global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
   if (warp == 0) tc::tmem_dealloc(tbase, ncols_t);
 }
 
+// ---------------------------------------------------------------- pipelined Gram
+// The same Gram with its phases overlapped, in the warp roles of the pipelined block product:
+//   warps 0-11  split: unit u = 16 c + g (column c of [V W], 8-row group g), thread t takes
+//               units t and t + 384; the 16 lanes of a half-warp hold one column, so its
+//               exponent over the tile is a 4-step shuffle maximum; digits go to the A / B tiles
+//               of buffer t % 2;
+//   warp 16     (one thread) TMA copies of the tile's rows into the (single) staging buffer;
+//   warp 17     (one thread) the nmt x 8 MMAs of a tile into TMEM buffer t % 2;
+//   warps 12-15 (TMEM lane quarter = warp % 4) for every lane (i, c) and column q:
+//               T_i = sum_j D[(i,c)][(j,q)] 2^(8 (6 - j)) as an integer (the 12 low bits
+//               dropped), into shared memory; after a barrier of the four warps, each output
+//               (c, q) sums its seven slices exactly in 128-bit integers, sum_i T_i 2^(8 (6 - i)),
+//               converts once (truncation) to FP64 with the tile's column scales and adds it to
+//               the thread's FP64 partial of G.
+// Barriers: xfull / xempty (staging), afull / mdone / tempty per buffer, as in the block
+// product; the splitters meet twice per tile and the epilogue warps twice, at named barriers
+// that OR their wait failures.
+namespace {
+constexpr int kGSplitWarps = 12, kGEpiWarps = 4;
+constexpr int kGSplitThreads = kGSplitWarps * 32;
+constexpr int kGEpiThreads = kGEpiWarps * 32;
+constexpr int kGProdWarp = 16, kGMmaWarp = 17;
+constexpr int kGPipeThreads = 18 * 32;
+
+struct GramBars {
+  uint64_t xfull, xempty, afull[2], mdone[2], tempty[2];
+};
+constexpr int kGramMaxCols = kGramMaxKV + kGramMaxBW;
+
+struct GramPipeLayout {
+  size_t a, b, x, t, e, bars, total;
+};
+__host__ __device__ inline GramPipeLayout gram_pipe_layout(int nmt, int NP, int nvb, int bv, int bw, int KV) {
+  GramPipeLayout L;
+  L.a = 0;
+  L.b = L.a + (size_t)2 * nmt * kGATile;
+  L.x = L.b + (size_t)2 * NP * kGramRows * 2;
+  const size_t xd = (size_t)nvb * (kGramRows * bv + 4) + (size_t)kGramRows * bw + 4;
+  L.t = L.x + ((xd * 8 + 15) & ~(size_t)15);
+  L.e = L.t + (size_t)7 * KV * bw * 8;
+  L.bars = (L.e + (size_t)4 * kGramMaxCols * 4 + 15) & ~(size_t)15;
+  L.total = L.bars + sizeof(GramBars) + 16;
+  return L;
+}
+
+// |v| < 2^127 times 2^s, truncated to FP64 (zero below the normal range, infinity above it).
+__device__ __forceinline__ double i128_to_double(__int128 v, int s) {
+  const uint64_t sign = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned __int128 a = v < 0 ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
+  const int lz = hi != 0 ? __clzll((long long)hi) : 64 + __clzll((long long)lo);   // 128 for 0
+  const unsigned __int128 nrm = a << (lz & 127);
+  const uint64_t m = (uint64_t)(nrm >> 64);
+  const int ef = 127 - lz + s + 1023;
+  uint64_t bits = sign | ((uint64_t)(uint32_t)ef << 52) | ((m >> 11) & 0xFFFFFFFFFFFFFull);
+  bits = (a == 0 || ef <= 0) ? sign : bits;
+  bits = ef >= 2047 ? (sign | 0x7FF0000000000000ull) : bits;
+  return __longlong_as_double((long long)bits);
+}
+}  // namespace
+
+template <int BW>
+__global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const TcGramArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int bw = BW;
+  constexpr int NP = (7 * BW + 15) / 16 * 16;
+  const int KV = a.KV, nmt = a.nmt, bv = a.bv;
+  const int ncol = KV + bw;
+  const int nvb = KV / bv;
+  const int XS = kGramRows * bv + 4;           // doubles per staged V block (padded)
+  const GramPipeLayout L = gram_pipe_layout(nmt, NP, nvb, bv, bw, KV);
+  unsigned char* sA = smem + L.a;              // [2][nmt] x 32 KB
+  unsigned char* sB = smem + L.b;              // [2] x NP x 128 FP16
+  double* sX = reinterpret_cast<double*>(smem + L.x);
+  int64_t* sT = reinterpret_cast<int64_t*>(smem + L.t);   // [bw][7][KV] slice integers
+  int* sEx = reinterpret_cast<int*>(smem + L.e);          // [2][ncol] column exponents by buffer
+  int* sExw = sEx + 2 * kGramMaxCols;                      // [2][ncol] maxima being formed
+  GramBars* bars = reinterpret_cast<GramBars*>(smem + L.bars);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bufcols = nmt * NP <= 64 ? 64u : 128u;
+
+  {
+    int4* z = reinterpret_cast<int4*>(smem);
+    for (int e = tid; e < (int)(L.x / 16); e += kGPipeThreads) z[e] = make_int4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bars->xfull, 1);
+    tc::mbar_init(&bars->xempty, kGSplitWarps);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars->afull[b], kGSplitWarps);
+      tc::mbar_init(&bars->mdone[b], 1);
+      tc::mbar_init(&bars->tempty[b], kGEpiWarps);
+    }
+    *abort_flag = 0;
+    tc::mbar_fence_init();
+  }
+  if (warp == kGMmaWarp) {
+    tc::tmem_alloc(tslot, 2 * bufcols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int64_t ntiles = (a.n + kGramRows - 1) / kGramRows;
+  const int64_t cnt = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto tile_of = [&](int64_t it) { return (int64_t)blockIdx.x + it * gridDim.x; };
+  auto bulk_ok = [&](int64_t t) {
+    const int64_t rows = min((int64_t)kGramRows, a.n - t * kGramRows);
+    return a.bulk && (rows * bv * 8) % 16 == 0 && (rows * bw * 8) % 16 == 0;
+  };
+
+  if (warp == kGProdWarp) {
+    int64_t issued = 0;
+    if (lane == 0) {
+      for (int64_t it = 0; it < cnt; ++it) {
+        if (it > 0 && !pipe_wait(&bars->xempty, (uint32_t)((it - 1) & 1), abort_flag)) break;
+        const int64_t t = tile_of(it), r0 = t * kGramRows;
+        if (bulk_ok(t)) {
+          const int64_t rows = min((int64_t)kGramRows, a.n - r0);
+          const uint32_t vb = (uint32_t)(rows * bv * 8), wb = (uint32_t)(rows * bw * 8);
+          tc::mbar_arrive_expect_tx(&bars->xfull, vb * (uint32_t)nvb + wb);
+          for (int j = 0; j < nvb; ++j) tc::bulk_g2s(sX + (size_t)j * XS, a.vblk[j] + r0 * bv, vb, &bars->xfull);
+          tc::bulk_g2s(sX + (size_t)nvb * XS, a.W + r0 * bw, wb, &bars->xfull);
+        } else {
+          tc::mbar_arrive(&bars->xfull);   // ragged or unaligned tile: splitters load directly
+        }
+        issued = it + 1;
+      }
+      if (issued > 0) wait_sleep(&bars->xfull, (uint32_t)((issued - 1) & 1));
+    }
+  } else if (warp == kGMmaWarp) {
+    int64_t committed = 0;
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16_f32(128, NP);
+      const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
+      for (int64_t it = 0; it < cnt; ++it) {
+        const int b = (int)(it & 1);
+        const uint32_t k = (uint32_t)(it >> 1);
+        if (!pipe_wait(&bars->afull[b], k & 1, abort_flag)) break;
+        if (k > 0 && !pipe_wait(&bars->tempty[b], (k - 1) & 1, abort_flag)) break;
+        tc::fence_after_sync();
+        for (int mt = 0; mt < nmt; ++mt)
+#pragma unroll
+          for (int ks = 0; ks < kGramRows / 16; ++ks) {
+            const uint64_t ad = tc::smem_desc(sa0 + (uint32_t)((b * nmt + mt) * kGATile + ks * 2 * kCoreBytes),
+                                              kCoreBytes, kGSBO);
+            const uint64_t bd = tc::smem_desc(sb0 + (uint32_t)(b * NP * kGramRows * 2 + ks * 2 * kCoreBytes),
+                                              kCoreBytes, kGSBO);
+            tc::mma_f16(tbase + (uint32_t)b * bufcols + (uint32_t)(mt * NP), ad, bd, idesc, ks > 0 ? 1u : 0u);
+          }
+        tc::mma_commit(&bars->mdone[b]);
+        committed = it + 1;
+      }
+      for (int b = 0; b < 2; ++b) {
+        const int64_t uses = (committed + 1 - b) / 2;
+        if (uses > 0) wait_sleep(&bars->mdone[b], (uint32_t)((uses - 1) & 1));
+      }
+    }
+  } else if (warp < kGSplitWarps) {
+    // ---- split: units (column c, 8-row group g) with u = g ncol + c, so that a warp's lanes read
+    // and write neighbouring columns (no shared-memory bank conflicts); the column exponents
+    // are maxima over the 16 groups through shared-memory atomics (double-buffered by tile)
+    const int nunits = ncol * 16;
+    for (int e = tid; e < 2 * kGramMaxCols; e += kGSplitThreads) sExw[e] = 0;
+    bar_or(1, kGSplitThreads, false);
+    for (int64_t it = 0; it < cnt; ++it) {
+      const int b = (int)(it & 1);
+      const uint32_t k = (uint32_t)(it >> 1);
+      const int64_t t = tile_of(it), r0 = t * kGramRows;
+      const bool bulk = bulk_ok(t);
+      int* exw = sExw + (it & 1) * kGramMaxCols;
+      const bool ok = pipe_wait_warp(&bars->xfull, (uint32_t)(it & 1), abort_flag);
+      double x[2][8];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int u = tid + kGSplitThreads * j;
+        if (u < nunits) {
+          const int c = u % ncol, g = u / ncol;
+          const bool isv = c < KV;
+          const int str = isv ? bv : bw;
+          const double* gcol = isv ? a.vblk[c / bv] + c % bv : a.W + (c - KV);
+          const double* scol = isv ? sX + (size_t)(c / bv) * XS + c % bv : sX + (size_t)nvb * XS + (c - KV);
+          int e = 0;
+          if (bulk) {
+#pragma unroll
+            for (int tt = 0; tt < 8; ++tt) {
+              const double v = scol[(g * 8 + tt) * str];   // in the staging buffer in any case
+              x[j][tt] = r0 + g * 8 + tt < a.n ? v : 0.0;
+            }
+          } else {
+#pragma unroll
+            for (int tt = 0; tt < 8; ++tt) {
+              const int64_t r = r0 + g * 8 + tt;
+              x[j][tt] = r < a.n ? __ldg(gcol + r * str) : 0.0;
+            }
+          }
+#pragma unroll
+          for (int tt = 0; tt < 8; ++tt) e = max(e, exp_field(x[j][tt]));
+          if (e > 0) atomicMax(exw + c, e);
+        }
+      }
+      if (bar_or(1, kGSplitThreads, !ok)) break;   // staging buffer read, exponent maxima formed
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->xempty);
+      int emax[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int u = tid + kGSplitThreads * j;
+        if (u < nunits) emax[j] = exw[u % ncol];
+      }
+      // the other buffer of maxima (read by everyone before the previous tile's second barrier)
+      // starts the next tile at zero
+      for (int e = tid; e < ncol; e += kGSplitThreads) sExw[((it + 1) & 1) * kGramMaxCols + e] = 0;
+      bool ok2 = true;
+      if (k > 0) ok2 = pipe_wait_warp(&bars->mdone[b], (k - 1) & 1, abort_flag) &&
+                       pipe_wait_warp(&bars->tempty[b], (k - 1) & 1, abort_flag);
+      if (bar_or(1, kGSplitThreads, !ok2)) break;  // digit tiles and exponents of buffer b free
+      unsigned char* sAb = sA + (size_t)b * nmt * kGATile;
+      unsigned char* sBb = sB + (size_t)b * NP * kGramRows * 2;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int u = tid + kGSplitThreads * j;
+        if (u < nunits) {
+          const int c = u % ncol, g = u / ncol;
+          if (g == 0) sEx[b * kGramMaxCols + c] = emax[j];
+          uint32_t w[kDigits][4];
+          split_pair_f16(x[j][0], x[j][1], emax[j], w, 0);
+          split_pair_f16(x[j][2], x[j][3], emax[j], w, 1);
+          split_pair_f16(x[j][4], x[j][5], emax[j], w, 2);
+          split_pair_f16(x[j][6], x[j][7], emax[j], w, 3);
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i) {
+            unsigned char* dst;
+            if (c < KV) {
+              const int m = i * KV + c;
+              dst = sAb + (size_t)(m >> 7) * kGATile + ((m & 127) >> 3) * kGSBO + g * kCoreBytes + (m & 7) * 16;
+            } else {
+              const int nn = i * bw + (c - KV);
+              dst = sBb + (nn >> 3) * kGSBO + g * kCoreBytes + (nn & 7) * 16;
+            }
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+          }
+        }
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->afull[b]);
+    }
+  } else if (warp < kGSplitWarps + kGEpiWarps) {
+    // ---- epilogue: TMEM lane quarter warp % 4 of each M tile
+    const int quarter = warp & 3, et = tid - kGSplitThreads;
+    const int nout = KV * bw;
+    double acc[3] = {0.0, 0.0, 0.0};   // outputs et, et + 128, et + 256 (nout <= 288)
+    for (int64_t it = 0; it < cnt; ++it) {
+      const int b = (int)(it & 1);
+      const uint32_t k = (uint32_t)(it >> 1);
+      const bool ok = pipe_wait_warp(&bars->afull[b], k & 1, abort_flag) &&
+                      pipe_wait_warp(&bars->mdone[b], k & 1, abort_flag);
+      if (bar_or(2, kGEpiThreads, !ok)) break;
+      tc::fence_after_sync();
+      // this thread's output scales, read before the buffer's exponents are handed back
+      const int* ex = sEx + b * kGramMaxCols;
+      int scl[3];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        const int o = et + kGEpiThreads * kk;
+        scl[kk] = 0;
+        if (o < nout) {
+          const int ec = ex[o / bw], fq = ex[KV + o % bw];
+          scl[kk] = ec > 0 && fq > 0 ? ec + fq : 0;
+        }
+      }
+      for (int mt = 0; mt < nmt; ++mt) {
+        const int m = mt * 128 + quarter * 32 + lane;
+        const uint32_t laddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * bufcols + (uint32_t)(mt * NP);
+#pragma unroll
+        for (int q = 0; q < bw; ++q) {
+          uint32_t d[kDigits];
+#pragma unroll
+          for (int jd = 0; jd < kDigits; ++jd) d[jd] = tc::tmem_ld1(laddr + (uint32_t)(jd * bw + q));
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int jd = 0; jd < kDigits; ++jd) tc::reg_after_wait(d[jd]);
+          if (m < 7 * KV) {
+            const int64_t hi = (int64_t)acc_int(d[0]) * 65536 + (int64_t)acc_int(d[1]) * 256 + (int64_t)acc_int(d[2]);
+            const int64_t lo = (int64_t)acc_int(d[3]) * 16777216 + (int64_t)acc_int(d[4]) * 65536 +
+                               (int64_t)acc_int(d[5]) * 256 + (int64_t)acc_int(d[6]);
+            // T_i / 2^12 (floor), i = m / KV, c = m % KV
+            sT[q * 7 * KV + m] = (hi << (32 - kAsmShift)) + (lo >> kAsmShift);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      bar_or(2, kGEpiThreads, false);   // slice integers written
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        const int o = et + kGEpiThreads * kk;
+        if (o < nout) {
+          const int c = o / bw, q = o % bw;
+          __int128 sum = 0;
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i) sum += (__int128)sT[q * 7 * KV + i * KV + c] << (8 * (6 - i));
+          if (scl[kk] > 0) acc[kk] += i128_to_double(sum, scl[kk] - 2108 + kAsmShift - 48);
+        }
+      }
+      bar_or(2, kGEpiThreads, false);   // slice integers read: the next tile may overwrite them
+    }
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      const int o = et + kGEpiThreads * kk;
+      if (o < nout) a.partial[(int64_t)blockIdx.x * nout + o] = *abort_flag ? __longlong_as_double(0x7FF8000000000000ll) : acc[kk];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid == 0 && *abort_flag) atomicExch(a.status, 1);
+  if (warp == kGMmaWarp) tc::tmem_dealloc(tbase, 2 * bufcols);
+}
+
 bool tc_gram_supported(const BlockSet& V, int bw, int ldw, fe_dtype dt) {
   const int KV = V.nv * V.bv;
   return dt == FE_F64 && V.ld == V.bv && ldw == bw && KV >= 1 && KV <= kGramMaxKV &&
@@ -1218,6 +1545,35 @@ int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha,
   a.NP = (int)ceil_div(7 * bw, 16) * 16;
   a.nmt = (int)ceil_div(7 * a.KV, 128);
   a.n = n;
+  {
+    const GramPipeLayout L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV);
+    if (L.total <= 227 * 1024 && a.KV * bw <= 3 * kGEpiThreads) {
+      static KernelSetup kp[4];
+      const int bj = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
+      const void* fp = bw == 1 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<1>)
+                     : bw == 2 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<2>)
+                     : bw == 4 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<4>)
+                               : reinterpret_cast<const void*>(tc_gram_pipe_kernel<8>);
+      FE_TRY(kernel_configure(kp[bj], fp, 227 * 1024));
+      const int64_t nt = ceil_div(n, kGramRows);
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)num_sms()));
+      const int nout = a.KV * bw;
+      double* scr = small_scratch(18, (size_t)grid * nout + 2);
+      if (!scr) return FE_ERR_OOM;
+      a.partial = scr;
+      a.status = reinterpret_cast<int*>(scr + (size_t)grid * nout);
+      FE_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
+      switch (bw) {
+        case 1: tc_gram_pipe_kernel<1><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+        case 2: tc_gram_pipe_kernel<2><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+        case 4: tc_gram_pipe_kernel<4><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+        default: tc_gram_pipe_kernel<8><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+      }
+      count_launch();
+      FE_CUDA(cudaGetLastError());
+      return gram_reduce(a.partial, grid, nout, alpha, G, s);
+    }
+  }
   const size_t smem = (size_t)a.nmt * kGATile + (size_t)a.NP * kGramRows * 2 +
                       sizeof(double) * ((size_t)(a.KV / a.bv) * (kGramRows * a.bv + 4) + (size_t)kGramRows * bw + 4) +
                       4 * 2 * (kGramMaxKV + kGramMaxBW) + 64;
