@@ -960,6 +960,7 @@ struct TcGramArgs {
   double* partial;       // [gridDim.x][KV * bw]
   int* status;
   int bulk;              // 1: V blocks and W 16-byte aligned (TMA bulk copies allowed)
+  int nxb;               // staging buffers of the pipelined kernel (1 or 2)
 };
 }  // namespace
 
@@ -1222,20 +1223,24 @@ constexpr int kGProdWarp = 16, kGMmaWarp = 17;
 constexpr int kGPipeThreads = 18 * 32;
 
 struct GramBars {
-  uint64_t xfull, xempty, afull[2], mdone[2], tempty[2];
+  uint64_t xfull[2], xempty[2], afull[2], mdone[2], tempty[2];
 };
 constexpr int kGramMaxCols = kGramMaxKV + kGramMaxBW;
 
 struct GramPipeLayout {
-  size_t a, b, x, t, e, bars, total;
+  size_t a, b, x, xbuf, t, e, bars, total;
+  int nxb;   // staging buffers: 2 when they fit, else 1
 };
-__host__ __device__ inline GramPipeLayout gram_pipe_layout(int nmt, int NP, int nvb, int bv, int bw, int KV) {
+__host__ __device__ inline GramPipeLayout gram_pipe_layout(int nmt, int NP, int nvb, int bv, int bw, int KV,
+                                                          int nxb) {
   GramPipeLayout L;
+  L.nxb = nxb;
   L.a = 0;
   L.b = L.a + (size_t)2 * nmt * kGATile;
   L.x = L.b + (size_t)2 * NP * kGramRows * 2;
   const size_t xd = (size_t)nvb * (kGramRows * bv + 4) + (size_t)kGramRows * bw + 4;
-  L.t = L.x + ((xd * 8 + 15) & ~(size_t)15);
+  L.xbuf = (xd * 8 + 15) & ~(size_t)15;
+  L.t = L.x + (size_t)nxb * L.xbuf;
   L.e = L.t + (size_t)7 * KV * bw * 8;
   L.bars = (L.e + (size_t)4 * kGramMaxCols * 4 + 15) & ~(size_t)15;
   L.total = L.bars + sizeof(GramBars) + 16;
@@ -1267,7 +1272,8 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
   const int ncol = KV + bw;
   const int nvb = KV / bv;
   const int XS = kGramRows * bv + 4;           // doubles per staged V block (padded)
-  const GramPipeLayout L = gram_pipe_layout(nmt, NP, nvb, bv, bw, KV);
+  const GramPipeLayout L = gram_pipe_layout(nmt, NP, nvb, bv, bw, KV, a.nxb);
+  const int nxb = a.nxb;
   unsigned char* sA = smem + L.a;              // [2][nmt] x 32 KB
   unsigned char* sB = smem + L.b;              // [2] x NP x 128 FP16
   double* sX = reinterpret_cast<double*>(smem + L.x);
@@ -1285,9 +1291,9 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
     for (int e = tid; e < (int)(L.x / 16); e += kGPipeThreads) z[e] = make_int4(0, 0, 0, 0);
   }
   if (tid == 0) {
-    tc::mbar_init(&bars->xfull, 1);
-    tc::mbar_init(&bars->xempty, kGSplitWarps);
     for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars->xfull[b], 1);
+      tc::mbar_init(&bars->xempty[b], kGSplitWarps);
       tc::mbar_init(&bars->afull[b], kGSplitWarps);
       tc::mbar_init(&bars->mdone[b], 1);
       tc::mbar_init(&bars->tempty[b], kGEpiWarps);
@@ -1316,20 +1322,26 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
     int64_t issued = 0;
     if (lane == 0) {
       for (int64_t it = 0; it < cnt; ++it) {
-        if (it > 0 && !pipe_wait(&bars->xempty, (uint32_t)((it - 1) & 1), abort_flag)) break;
+        const int xb = nxb == 2 ? (int)(it & 1) : 0;
+        const int64_t xk = nxb == 2 ? (it >> 1) : it;
+        if (xk > 0 && !pipe_wait(&bars->xempty[xb], (uint32_t)((xk - 1) & 1), abort_flag)) break;
         const int64_t t = tile_of(it), r0 = t * kGramRows;
+        double* sXb = sX + (size_t)xb * (L.xbuf / 8);
         if (bulk_ok(t)) {
           const int64_t rows = min((int64_t)kGramRows, a.n - r0);
           const uint32_t vb = (uint32_t)(rows * bv * 8), wb = (uint32_t)(rows * bw * 8);
-          tc::mbar_arrive_expect_tx(&bars->xfull, vb * (uint32_t)nvb + wb);
-          for (int j = 0; j < nvb; ++j) tc::bulk_g2s(sX + (size_t)j * XS, a.vblk[j] + r0 * bv, vb, &bars->xfull);
-          tc::bulk_g2s(sX + (size_t)nvb * XS, a.W + r0 * bw, wb, &bars->xfull);
+          tc::mbar_arrive_expect_tx(&bars->xfull[xb], vb * (uint32_t)nvb + wb);
+          for (int j = 0; j < nvb; ++j) tc::bulk_g2s(sXb + (size_t)j * XS, a.vblk[j] + r0 * bv, vb, &bars->xfull[xb]);
+          tc::bulk_g2s(sXb + (size_t)nvb * XS, a.W + r0 * bw, wb, &bars->xfull[xb]);
         } else {
-          tc::mbar_arrive(&bars->xfull);   // ragged or unaligned tile: splitters load directly
+          tc::mbar_arrive(&bars->xfull[xb]);   // ragged or unaligned tile: splitters load directly
         }
         issued = it + 1;
       }
-      if (issued > 0) wait_sleep(&bars->xfull, (uint32_t)((issued - 1) & 1));
+      for (int xb = 0; xb < nxb; ++xb) {
+        const int64_t uses = nxb == 2 ? (issued + 1 - xb) / 2 : issued;
+        if (uses > 0) wait_sleep(&bars->xfull[xb], (uint32_t)((uses - 1) & 1));
+      }
     }
   } else if (warp == kGMmaWarp) {
     int64_t committed = 0;
@@ -1364,6 +1376,20 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
     // and write neighbouring columns (no shared-memory bank conflicts); the column exponents
     // are maxima over the 16 groups through shared-memory atomics (double-buffered by tile)
     const int nunits = ncol * 16;
+    // this thread's units, the same in every tile: column, row group, column pointer and stride
+    int uc[2], ug[2], ustr[2], usoff[2];
+    const double* ucol[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int u = tid + kGSplitThreads * j;
+      uc[j] = u < nunits ? u % ncol : 0;
+      ug[j] = u < nunits ? u / ncol : 0;
+      const int c = uc[j];
+      const bool isv = c < KV;
+      ustr[j] = isv ? bv : bw;
+      ucol[j] = isv ? a.vblk[c / bv] + c % bv : a.W + (c - KV);
+      usoff[j] = isv ? (c / bv) * XS + c % bv : nvb * XS + (c - KV);
+    }
     for (int e = tid; e < 2 * kGramMaxCols; e += kGSplitThreads) sExw[e] = 0;
     bar_or(1, kGSplitThreads, false);
     for (int64_t it = 0; it < cnt; ++it) {
@@ -1372,17 +1398,17 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
       const int64_t t = tile_of(it), r0 = t * kGramRows;
       const bool bulk = bulk_ok(t);
       int* exw = sExw + (it & 1) * kGramMaxCols;
-      const bool ok = pipe_wait_warp(&bars->xfull, (uint32_t)(it & 1), abort_flag);
+      const int xb = nxb == 2 ? (int)(it & 1) : 0;
+      const double* sXb = sX + (size_t)xb * (L.xbuf / 8);
+      const bool ok = pipe_wait_warp(&bars->xfull[xb], (uint32_t)((nxb == 2 ? (it >> 1) : it) & 1), abort_flag);
       double x[2][8];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int u = tid + kGSplitThreads * j;
         if (u < nunits) {
-          const int c = u % ncol, g = u / ncol;
-          const bool isv = c < KV;
-          const int str = isv ? bv : bw;
-          const double* gcol = isv ? a.vblk[c / bv] + c % bv : a.W + (c - KV);
-          const double* scol = isv ? sX + (size_t)(c / bv) * XS + c % bv : sX + (size_t)nvb * XS + (c - KV);
+          const int c = uc[j], g = ug[j], str = ustr[j];
+          const double* gcol = ucol[j];
+          const double* scol = sXb + usoff[j];
           int e = 0;
           if (bulk) {
 #pragma unroll
@@ -1404,12 +1430,12 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
       }
       if (bar_or(1, kGSplitThreads, !ok)) break;   // staging buffer read, exponent maxima formed
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars->xempty);
+      if (lane == 0) tc::mbar_arrive(&bars->xempty[xb]);
       int emax[2] = {0, 0};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int u = tid + kGSplitThreads * j;
-        if (u < nunits) emax[j] = exw[u % ncol];
+        if (u < nunits) emax[j] = exw[uc[j]];
       }
       // the other buffer of maxima (read by everyone before the previous tile's second barrier)
       // starts the next tile at zero
@@ -1424,7 +1450,7 @@ __global__ void __launch_bounds__(kGPipeThreads, 1) tc_gram_pipe_kernel(const Tc
       for (int j = 0; j < 2; ++j) {
         const int u = tid + kGSplitThreads * j;
         if (u < nunits) {
-          const int c = u % ncol, g = u / ncol;
+          const int c = uc[j], g = ug[j];
           if (g == 0) sEx[b * kGramMaxCols + c] = emax[j];
           uint32_t w[kDigits][4];
           split_pair_f16(x[j][0], x[j][1], emax[j], w, 0);
@@ -1546,7 +1572,9 @@ int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha,
   a.nmt = (int)ceil_div(7 * a.KV, 128);
   a.n = n;
   {
-    const GramPipeLayout L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV);
+    GramPipeLayout L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV, 2);
+    if (L.total > 227 * 1024) L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV, 1);
+    a.nxb = L.nxb;
     if (L.total <= 227 * 1024 && a.KV * bw <= 3 * kGEpiThreads) {
       static KernelSetup kp[4];
       const int bj = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
