@@ -89,7 +89,7 @@ __device__ __forceinline__ void gram_tile_rows(const T* __restrict__ vb, int ldv
 #pragma unroll
       for (int p = 0; p < BV; ++p)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[p][q] = fma((TC)v[u][p], w[q], acc[p][q]);
+        for (int q = 0; q < NQ; ++q) acc[p][q] = fma(to_arith<TC>(v[u][p]), w[q], acc[p][q]);
     }
   }
   for (; r < rows; r += 32) {
@@ -99,7 +99,7 @@ __device__ __forceinline__ void gram_tile_rows(const T* __restrict__ vb, int ldv
 #pragma unroll
     for (int p = 0; p < BV; ++p)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) acc[p][q] = fma((TC)v[p], w[q], acc[p][q]);
+      for (int q = 0; q < NQ; ++q) acc[p][q] = fma(to_arith<TC>(v[p]), w[q], acc[p][q]);
   }
 }
 
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(256) gram_kernel(const BlockSet V, const T* __
       const int n16 = (int)(((size_t)rows * bw * sizeof(T)) / 16);
       for (int e = threadIdx.x; e < n16; e += blockDim.x) dst[e] = src[e];
     } else {
-      const int tot = rows * bw;
-      for (int e = threadIdx.x; e < tot; e += blockDim.x) sW[e] = (TC)W[(r0 + e / bw) * ldw + e % bw];
+      for (int rr = threadIdx.x; rr < rows; rr += blockDim.x)
+        for (int q = 0; q < bw; ++q) sW[rr * bw + q] = to_arith<TC>(W[(r0 + rr) * ldw + q]);
     }
     __syncthreads();
     if (TPW > 0) {
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(TPW > 0 ? 512 : 256) update_gram_kernel(const 
           }
         }
 #pragma unroll
-        for (int q = 0; q < BW; ++q) a[q] += (T)a32[q];
+        for (int q = 0; q < BW; ++q) a[q] += (T)f32_to_f64_flush(a32[q]);
       } else {
         for (int j0 = 0; j0 < V.nv; j0 += UJ) {
           T v[UJ][BV];
@@ -1026,7 +1026,7 @@ __global__ void __launch_bounds__(256) update_tri_gram_kernel(const BlockSet V, 
         }
       }
 #pragma unroll
-      for (int q = 0; q < B; ++q) a[q] += (double)a32[q];
+      for (int q = 0; q < B; ++q) a[q] += f32_to_f64_flush(a32[q]);
     } else {
       for (int j = 0; j < V.nv; ++j) {
         double v[B];

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256) right_mult_kernel(T* __restrict__ W, int6
         float c = 0.f;
 #pragma unroll
         for (int p = 0; p < B; ++p) c = fmaf(wf[p], sD[p * B + q], c);
-        out[q] = w[q] + (T)c;
+        out[q] = w[q] + (T)f32_to_f64_flush(c);
       }
     } else {
 #pragma unroll

@@ -98,4 +98,23 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(bits);
 }
 
+// FP32 -> FP64 by integer operations (exact for normal values, infinities and NaN; subnormal
+// inputs give a signed zero), keeping the conversion off the FP64 pipe.
+__device__ __forceinline__ double f32_to_f64_flush(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned long long bits = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long ef = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  if (e != 0) bits |= (ef << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// Conversion of a block element to the Gram's arithmetic type: FP64 -> FP32 by integer
+// truncation (f64_to_f32_trunc), otherwise a plain cast.
+template <typename TC, typename T>
+__device__ __forceinline__ TC to_arith(T x) {
+  if constexpr (sizeof(T) == 8 && sizeof(TC) == 4) return f64_to_f32_trunc((double)x);
+  else return (TC)x;
+}
+
 }  // namespace fe
