@@ -968,18 +968,19 @@ static int launch_update_gram(const BlockSet& V, int64_t n, const double* C, dou
   return launch_update_gram_tpw<T, BV, BW, 0>(V, n, C, alpha, beta, M, W, gram_v, skip, vc32, G, 256, s);
 }
 
-// The second Gram-Schmidt pass's closing sweep for FP64 blocks of width B <= 4, with M upper
+// The second Gram-Schmidt pass's closing sweep for blocks of width B <= 4, with M upper
 // triangular (M = R1^{-1} of the CholeskyQR pass): W = beta W M + alpha V C and S = W^T W (after
-// the update).  Thread per row: the triangle of M (B (B + 1) / 2 FMAs instead of B^2), the
-// correction V C in FP32 arithmetic when *vc32 (its entries are tiny; V read through an
-// integer truncation to FP32, added to the FP64 W M in FP64), otherwise in FP64, and the upper
-// triangle of S in per-thread FP64 accumulators over the rows the thread visits (a grid-stride
-// loop), reduced over the CTA and written as the CTA's full B x B partial.  *skip: nothing done.
-template <int B>
+// the update).  Thread per row: the triangle of M (B (B + 1) / 2 FMAs instead of B^2); for FP64
+// blocks the correction V C in FP32 arithmetic when *vc32 (its entries are tiny; V read through
+// an integer truncation to FP32, added to the FP64 W M in FP64), otherwise in T; the upper
+// triangle of S in per-thread accumulators (T) over the rows the thread visits (a grid-stride
+// loop), reduced over the CTA in FP64 and written as the CTA's full B x B partial.  *skip:
+// nothing done.
+template <typename T, int B>
 __global__ void __launch_bounds__(256) update_tri_gram_kernel(const BlockSet V, const double* __restrict__ C,
                                                              double alpha, double beta,
                                                              const double* __restrict__ M,
-                                                             double* __restrict__ W, int64_t n,
+                                                             T* __restrict__ W, int64_t n,
                                                              const int* __restrict__ skip,
                                                              const int* __restrict__ vc32,
                                                              double* __restrict__ partial) {
@@ -987,26 +988,26 @@ __global__ void __launch_bounds__(256) update_tri_gram_kernel(const BlockSet V, 
   constexpr int NS = B * (B + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k = V.nv * B;
-  double* sC = reinterpret_cast<double*>(smem_raw);   // k x B
-  double* sM = sC + (size_t)k * B;                     // B x B
-  double* sR = sM + B * B;                             // [warps][NS] reduction
-  float* sC32 = reinterpret_cast<float*>(sR + (blockDim.x / 32) * NS);
-  const bool use32 = vc32 != nullptr && *vc32 != 0;
+  double* sR = reinterpret_cast<double*>(smem_raw);            // [warps][NS] reduction
+  T* sC = reinterpret_cast<T*>(sR + (blockDim.x / 32) * NS);   // k x B
+  T* sM = sC + (size_t)k * B;                                  // B x B
+  float* sC32 = reinterpret_cast<float*>(sM + B * B);
+  const bool use32 = sizeof(T) == 8 && vc32 != nullptr && *vc32 != 0;
   for (int e = threadIdx.x; e < k * B; e += blockDim.x) {
-    sC[e] = alpha * C[e];
+    sC[e] = (T)(alpha * C[e]);
     sC32[e] = (float)(alpha * C[e]);
   }
-  for (int e = threadIdx.x; e < B * B; e += blockDim.x) sM[e] = beta * M[e];
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) sM[e] = (T)(beta * M[e]);
   __syncthreads();
-  double acc[NS];
+  T acc[NS];
 #pragma unroll
-  for (int e = 0; e < NS; ++e) acc[e] = 0.0;
+  for (int e = 0; e < NS; ++e) acc[e] = T(0);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    double w[B], a[B];
-    ld_row_rw<double, B>(W + r * B, w);
+    T w[B], a[B];
+    ld_row_rw<T, B>(W + r * B, w);
 #pragma unroll
     for (int q = 0; q < B; ++q) {
-      double x = 0.0;
+      T x = T(0);
 #pragma unroll
       for (int p = 0; p <= q; ++p) x = fma(w[p], sM[p * B + q], x);
       a[q] = x;
@@ -1016,39 +1017,39 @@ __global__ void __launch_bounds__(256) update_tri_gram_kernel(const BlockSet V, 
 #pragma unroll
       for (int q = 0; q < B; ++q) a32[q] = 0.f;
       for (int j = 0; j < V.nv; ++j) {
-        double v[B];
-        ld_row<double, B>(reinterpret_cast<const double*>(V.blk[j]) + r * B, v);
+        T v[B];
+        ld_row<T, B>(reinterpret_cast<const T*>(V.blk[j]) + r * B, v);
 #pragma unroll
         for (int p = 0; p < B; ++p) {
-          const float vp = f64_to_f32_trunc(v[p]);
+          const float vp = to_arith<float>(v[p]);
 #pragma unroll
           for (int q = 0; q < B; ++q) a32[q] = fmaf(vp, sC32[(j * B + p) * B + q], a32[q]);
         }
       }
 #pragma unroll
-      for (int q = 0; q < B; ++q) a[q] += f32_to_f64_flush(a32[q]);
+      for (int q = 0; q < B; ++q) a[q] += (T)f32_to_f64_flush(a32[q]);
     } else {
       for (int j = 0; j < V.nv; ++j) {
-        double v[B];
-        ld_row<double, B>(reinterpret_cast<const double*>(V.blk[j]) + r * B, v);
+        T v[B];
+        ld_row<T, B>(reinterpret_cast<const T*>(V.blk[j]) + r * B, v);
 #pragma unroll
         for (int p = 0; p < B; ++p)
 #pragma unroll
           for (int q = 0; q < B; ++q) a[q] = fma(v[p], sC[(j * B + p) * B + q], a[q]);
       }
     }
-    st_row<double, B>(W + r * B, a);
+    st_row<T, B>(W + r * B, a);
     int e = 0;
 #pragma unroll
     for (int p = 0; p < B; ++p)
 #pragma unroll
       for (int q = p; q < B; ++q, ++e) acc[e] = fma(a[p], a[q], acc[e]);
   }
-  // CTA reduction of the triangle (warp shuffles, then the warps' sums in a fixed order)
+  // CTA reduction of the triangle in FP64 (warp shuffles, then the warps' sums in a fixed order)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int e = 0; e < NS; ++e) {
-    double x = acc[e];
+    double x = (double)acc[e];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     if (lane == 0) sR[warp * NS + e] = x;
@@ -1065,20 +1066,18 @@ __global__ void __launch_bounds__(256) update_tri_gram_kernel(const BlockSet V, 
   }
 }
 
-// W = beta W M + alpha V C, S = W^T W for FP64 n x b blocks, b in {1, 2, 4}, M upper triangular
-// (see update_tri_gram_kernel); S: DEVICE b x b.
-int update_tri_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
-                    const double* M, double* W, int b, const int* skip, const int* vc32, double* S,
-                    cudaStream_t s) {
-  FE_ARG(b == 1 || b == 2 || b == 4, "update_tri_gram: b = %d", b);
-  FE_ARG(V.nv == 0 || (V.bv == b && V.ld == b), "update_tri_gram: blocks must be n x b");
+template <typename T>
+static int launch_update_tri_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
+                                  const double* M, T* W, int b, const int* skip, const int* vc32, double* S,
+                                  cudaStream_t s) {
   const int k = V.nv * b;
   const int threads = 256;
   const int NS = b * (b + 1) / 2;
-  const size_t smem = ((size_t)k * b + b * b + (threads / 32) * NS) * sizeof(double) + (size_t)k * b * sizeof(float);
-  const void* fn = b == 1 ? reinterpret_cast<const void*>(update_tri_gram_kernel<1>)
-                 : b == 2 ? reinterpret_cast<const void*>(update_tri_gram_kernel<2>)
-                          : reinterpret_cast<const void*>(update_tri_gram_kernel<4>);
+  const size_t smem = (size_t)(threads / 32) * NS * sizeof(double) + ((size_t)k * b + b * b) * sizeof(T) +
+                      (size_t)k * b * sizeof(float);
+  const void* fn = b == 1 ? reinterpret_cast<const void*>(update_tri_gram_kernel<T, 1>)
+                 : b == 2 ? reinterpret_cast<const void*>(update_tri_gram_kernel<T, 2>)
+                          : reinterpret_cast<const void*>(update_tri_gram_kernel<T, 4>);
   static KernelSetup ks[3];
   const int bi = b == 1 ? 0 : b == 2 ? 1 : 2;
   FE_TRY(kernel_configure(ks[bi], fn, 96 * 1024));
@@ -1088,13 +1087,25 @@ int update_tri_gram(const BlockSet& V, int64_t n, const double* C, double alpha,
   double* part = small_scratch(0, (size_t)nctas * b * b);
   if (!part) return FE_ERR_OOM;
   switch (b) {
-    case 1: update_tri_gram_kernel<1><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, skip, vc32, part); break;
-    case 2: update_tri_gram_kernel<2><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, skip, vc32, part); break;
-    default: update_tri_gram_kernel<4><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, skip, vc32, part); break;
+    case 1: update_tri_gram_kernel<T, 1><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, skip, vc32, part); break;
+    case 2: update_tri_gram_kernel<T, 2><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, skip, vc32, part); break;
+    default: update_tri_gram_kernel<T, 4><<<nctas, threads, smem, s>>>(V, C, alpha, beta, M, W, n, skip, vc32, part); break;
   }
   count_launch();
   FE_CUDA(cudaGetLastError());
   return launch_gram_reduce(part, nctas, b * b, 1.0, S, s);
+}
+
+// W = beta W M + alpha V C, S = W^T W for n x b blocks of dt, b in {1, 2, 4}, M upper triangular
+// (see update_tri_gram_kernel); S: DEVICE b x b.
+int update_tri_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
+                    const double* M, void* W, int b, fe_dtype dt, const int* skip, const int* vc32, double* S,
+                    cudaStream_t s) {
+  FE_ARG(b == 1 || b == 2 || b == 4, "update_tri_gram: b = %d", b);
+  FE_ARG(V.nv == 0 || (V.bv == b && V.ld == b), "update_tri_gram: blocks must be n x b");
+  if (dt == FE_F64)
+    return launch_update_tri_gram<double>(V, n, C, alpha, beta, M, static_cast<double*>(W), b, skip, vc32, S, s);
+  return launch_update_tri_gram<float>(V, n, C, alpha, beta, M, static_cast<float*>(W), b, skip, nullptr, S, s);
 }
 
 // W = beta W M + alpha V C; G = [V; W]^T W (gram_v) or W^T W, rows (j*b + p) then W's b rows.

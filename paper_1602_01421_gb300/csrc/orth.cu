@@ -33,8 +33,8 @@ int update_skip(const BlockSet& V, int64_t n, const double* C, double alpha, dou
 int gram_f32_arith(const BlockSet& V, int64_t n, const double* W, int b, double alpha, double* G,
                    cudaStream_t s);
 int update_tri_gram(const BlockSet& V, int64_t n, const double* C, double alpha, double beta,
-                    const double* M, double* W, int b, const int* skip, const int* vc32, double* S,
-                    cudaStream_t s);
+                    const double* M, void* W, int b, fe_dtype dt, const int* skip, const int* vc32,
+                    double* S, cudaStream_t s);
 
 constexpr double kRelPivot = 1e-6;      // pivot below 1e-6 * column norm: nearly dependent
 constexpr double kAbsBreakdown = 1e-12; // remainder below 1e-12 * ||A||: breakdown
@@ -390,11 +390,12 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   count_launch();
   FE_CUDA(cudaGetLastError());
   // W <- (W - V G2) R1^{-1} and S2 = W^T W in one sweep (skipped after a failed pivot check)
-  if (fused && dt == FE_F64 && b <= 4) {
+  if (fused && b <= 4) {
     // M = R1^{-1} is upper triangular: thread-per-row sweep over its triangle, S2 = W^T W in
-    // per-thread accumulators; the correction V C in FP32 arithmetic when it is tiny
-    FE_TRY(update_tri_gram(V, n, sC, 1.0, 1.0, sM, static_cast<double*>(W), b, status,
-                           pass1_f32 ? status + 1 : nullptr, sS2, s));
+    // per-thread accumulators; for FP64 blocks the correction V C in FP32 arithmetic when it
+    // is tiny
+    FE_TRY(update_tri_gram(V, n, sC, 1.0, 1.0, sM, W, b, dt, status,
+                           (pass1_f32 && dt == FE_F64) ? status + 1 : nullptr, sS2, s));
   } else if (fused) {
     // the correction V C in FP32 arithmetic when it is tiny (FP64 subspace, pass1_f32 mode)
     FE_TRY(update_gram(V, n, sC, 1.0, 1.0, sM, W, b, dt, 0, status, sS2, s,
