@@ -73,6 +73,27 @@ __device__ double ritz_block_sum(double v, double* red) {
   return s;
 }
 
+// e / d for 0 <= e < 2^22 and 1 <= d < 2^11, with inv = 1 / d: an FP32 estimate corrected once
+// (an integer division would be a long instruction sequence inside the work loops).
+__device__ __forceinline__ int small_div(int e, int d, float inv) {
+  int q = (int)((float)e * inv);
+  const int r = e - q * d;
+  q += r < 0 ? -1 : (r >= d ? 1 : 0);
+  return q;
+}
+
+// The e-th of the pairs (k, k2), k <= k2 < np (the upper triangle of the step's 2 x 2 blocks,
+// np (np + 1) / 2 of them), from a triangular-number inversion in FP32 corrected in integers.
+__device__ __forceinline__ void tri_pair(int e, int np, int& k, int& k2) {
+  const int f = np * (np + 1) / 2 - 1 - e;   // reversed index: row r holds r + 1 items
+  int r = (int)((sqrtf(8.f * (float)f + 1.f) - 1.f) * 0.5f);
+  if ((r + 1) * (r + 2) / 2 <= f) ++r;
+  if (r * (r + 1) / 2 > f) --r;
+  const int o = f - r * (r + 1) / 2;
+  k = np - 1 - r;
+  k2 = np - 1 - o;
+}
+
 // Parallel cyclic Jacobi sweeps on the symmetric mp x mp matrix A (row stride ld), with
 // Q <- Q J accumulated, until the off-diagonal Frobenius norm squared is <= thresh or after
 // max_sweeps.  Returns the sweeps run; *conv tells whether the threshold was met.
@@ -81,11 +102,13 @@ __device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, i
                              T* cs, T* sn, int* pp, int* pq, double* red, bool* conv) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int np = mp / 2;
+  const float inv_mp = 1.f / (float)mp, inv_np = 1.f / (float)np;
+  const int ntri = np * (np + 1) / 2;
   int sweeps = 0;
   while (true) {
     double v = 0.0;
     for (int e = tid; e < mp * mp; e += nth) {
-      const int i = e / mp, j = e - (e / mp) * mp;
+      const int i = small_div(e, mp, inv_mp), j = e - i * mp;
       if (i != j) v += (double)A[i * ld + j] * (double)A[i * ld + j];
     }
     const double off2 = ritz_block_sum(v, red);
@@ -114,11 +137,10 @@ __device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, i
       // A <- J^T A J as independent 2 x 2 blocks (rows of pair k, columns of pair k2, k <= k2,
       // mirrored to the lower triangle), and Q <- Q J by column pairs: the step's pairs are
       // disjoint, so no two work items touch the same entry and one barrier suffices.
-      const int nsq = np * np;
-      for (int e = tid; e < nsq + mp * np; e += nth) {
-        if (e < nsq) {
-          const int k = e / np, k2 = e - k * np;
-          if (k > k2) continue;
+      for (int e = tid; e < ntri + mp * np; e += nth) {
+        if (e < ntri) {
+          int k, k2;
+          tri_pair(e, np, k, k2);
           const T s1 = sn[k], s2 = sn[k2];
           if (s1 == T(0) && s2 == T(0)) continue;
           const T c1 = cs[k], c2 = cs[k2];
@@ -150,8 +172,8 @@ __device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, i
             A[q2 * ld + q1] = z11;
           }
         } else {
-          const int e2 = e - nsq;
-          const int i = e2 / np, k = e2 - i * np;
+          const int e2 = e - ntri;
+          const int i = small_div(e2, np, inv_np), k = e2 - i * np;
           const T sk = sn[k];
           if (sk == T(0)) continue;
           const T ck = cs[k];
@@ -179,7 +201,7 @@ __device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, i
 // transformed by it (Q^T T Q, an exact orthogonal similarity), and FP64 sweeps finish from there
 // -- two or three, since Jacobi converges quadratically once the off-diagonal part is small.
 template <bool BIG>
-__global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int which, int max_sweeps,
+__global__ void __launch_bounds__(1024) ritz_kernel(const double* __restrict__ H, int m, int b, int which, int max_sweeps,
                             double tol, double* __restrict__ theta_out, double* __restrict__ Y_out,
                             double* __restrict__ rho_out, int* __restrict__ info, double* gwork) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -223,43 +245,43 @@ __global__ void ritz_kernel(const double* __restrict__ H, int m, int b, int whic
   // FP32 sweeps
   int sweeps = jacobi_sweeps<float>(A32, Q32, ld, m, mp, 1e-12 * fro2, 15, reinterpret_cast<float*>(cs),
                                     reinterpret_cast<float*>(sn), pp, pq, red, &conv32);
-  // Q = chol-QR(Q32) in FP64: S = Q^T Q (in W after Q32 is copied out), S = R^T R, Q <- Q R^-1
+  // Q32 made orthogonal in FP64 by two Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2 (Higham,
+  // "Functions of Matrices", 8.3: quadratic convergence to the orthogonal polar factor from
+  // ||Q^T Q - I|| ~ 1e-6, to FP64 rounding in two steps); S and the factor in W, each new row
+  // of Q formed by one warp (all of its entries read before any is written)
+  const float inv_mp = 1.f / (float)mp;
   for (int e = tid; e < mp * mp; e += nth) {
-    const int i = e / mp, j = e % mp;
+    const int i = small_div(e, mp, inv_mp), j = e - i * mp;
     Q[i * ld + j] = (double)Q32[i * ld + j];
   }
   __syncthreads();
-  for (int e = tid; e < mp * mp; e += nth) {
-    const int i = e / mp, j = e % mp;
-    if (i > j) continue;
-    double s = 0.0;
-    for (int r = 0; r < mp; ++r) s += Q[r * ld + i] * Q[r * ld + j];
-    W[i * ld + j] = s;
-  }
-  __syncthreads();
-  for (int j = 0; j < mp; ++j) {
-    if (tid == 0) {
-      double d = W[j * ld + j];
-      for (int l = 0; l < j; ++l) d -= W[l * ld + j] * W[l * ld + j];
-      W[j * ld + j] = d > 0.0 ? sqrt(d) : 1.0;  // Q32 is orthogonal to ~1e-7: d ~ 1
+  for (int it = 0; it < 2; ++it) {
+    for (int e = tid; e < mp * mp; e += nth) {
+      const int i = small_div(e, mp, inv_mp), j = e - i * mp;
+      if (i > j) continue;
+      double sv = 0.0;
+      for (int r = 0; r < mp; ++r) sv = fma(Q[r * ld + i], Q[r * ld + j], sv);
+      const double f = (i == j ? 1.5 : 0.0) - 0.5 * sv;
+      W[i * ld + j] = f;
+      W[j * ld + i] = f;
     }
     __syncthreads();
-    const double rjj = W[j * ld + j];
-    for (int i = j + 1 + tid; i < mp; i += nth) {
-      double s = W[j * ld + i];
-      for (int l = 0; l < j; ++l) s -= W[l * ld + j] * W[l * ld + i];
-      W[j * ld + i] = s / rjj;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
+    for (int r = warp; r < mp; r += nwarps) {
+      double x[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // columns lane + 32 t (mp <= 160)
+      for (int l = 0; l < mp; ++l) {
+        const double q = Q[r * ld + l];
+#pragma unroll
+        for (int t = 0; t < 5; ++t)
+          if (lane + 32 * t < mp) x[t] = fma(q, W[l * ld + lane + 32 * t], x[t]);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 5; ++t)
+        if (lane + 32 * t < mp) Q[r * ld + lane + 32 * t] = x[t];
     }
     __syncthreads();
   }
-  for (int r = tid; r < mp; r += nth) {
-    for (int j = 0; j < mp; ++j) {
-      double x = Q[r * ld + j];
-      for (int l = 0; l < j; ++l) x -= Q[r * ld + l] * W[l * ld + j];
-      Q[r * ld + j] = x / W[j * ld + j];
-    }
-  }
-  __syncthreads();
   if (BIG) {  // the FP32 pair is dead: A64 takes its region back
     for (int e = tid; e < mp * mp; e += nth) {
       const int i = e / mp, j = e % mp;
@@ -693,11 +715,12 @@ int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double
                                        : reinterpret_cast<const void*>(ritz_kernel<false>),
                           225 * 1024));
   // one CTA: a rotation step is (m/2)^2 / 2 2 x 2 blocks plus m^2 / 2 Q updates between two
-  // barriers; FP64 work on one SM runs at 2 DFMA per clock, hence the FP32 sweeps first
+  // barriers; FP64 work on one SM runs at 2 DFMA per clock, hence the FP32 sweeps first, and
+  // 1024 threads, so that many independent FP64 chains hide the FP64 pipe's latency
   if (big)
-    ritz_kernel<true><<<1, 512, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, work);
+    ritz_kernel<true><<<1, 1024, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, work);
   else
-    ritz_kernel<false><<<1, 256, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, nullptr);
+    ritz_kernel<false><<<1, 1024, smem, s>>>(H, m, b, which, max_sweeps, tol, theta, Y, rho, info, nullptr);
   count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;
