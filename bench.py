@@ -401,19 +401,30 @@ def run_ours(args):
         Ot = fe.block_combine(Vt, Yt, 5, engine="tc")
         tcm = statistics.median(time_cuda(lambda: fe.block_combine(Vt, Yt, 5, Out=Ot, engine="tc"), 10, torch))
         bc = 8.0 * n * (32 + 20)
-        roofline_tc["tc_combine_kernel<4,32>"] = {
+        roofline_tc["tc_combine_pipe_kernel<4,32> (restart V Y, 8 -> 5 blocks)"] = {
             "bound": "hbm", "achieved": round(bc / (tcm / 1000.0) / 1e9, 1), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(bc / (tcm / 1000.0) / 1e9 / hbm_peak, 4),
             "bytes_per_launch": bc, "ms_per_launch": round(tcm, 4),
             "fma_engine_ms": round(statistics.median(time_cuda(
                 lambda: fe.block_combine(Vt, Yt, 5, Out=Ot, engine="fma"), 5, torch)), 4)}
-        del Ot, Yt
+        del Ot
+        # the second pass's update W <- W - V G1 at its largest shape (8 blocks into 1)
         Wt = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+        Ct = Yt[:, :4].contiguous() * 1e-3
+        tum = statistics.median(time_cuda(lambda: fe.block_update(Vt, Ct, Wt, -1.0, 1.0, engine="tc"), 10, torch))
+        bu = 8.0 * n * (32 + 4 + 4)
+        roofline_tc["tc_combine_pipe_kernel<4,16> (update W - V G1, 8 blocks)"] = {
+            "bound": "hbm", "achieved": round(bu / (tum / 1000.0) / 1e9, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(bu / (tum / 1000.0) / 1e9 / hbm_peak, 4),
+            "bytes_per_launch": bu, "ms_per_launch": round(tum, 4),
+            "fma_engine_ms": round(statistics.median(time_cuda(
+                lambda: fe.block_update(Vt, Ct, Wt, -1.0, 1.0, engine="fma"), 5, torch)), 4)}
+        del Ct, Yt
         Vx = torch.cat([Vt, Wt.view(1, n, 4)], 0)
         Gt = fe.block_gram(Vx, Wt, engine="tc")
         tgm = statistics.median(time_cuda(lambda: fe.block_gram(Vx, Wt, G=Gt, engine="tc"), 10, torch))
         bg = 8.0 * n * (36 + 4)
-        roofline_tc["tc_gram_kernel<4>"] = {
+        roofline_tc["tc_gram_pipe_kernel<4> ([V_0..V_7 W]^T W)"] = {
             "bound": "hbm", "achieved": round(bg / (tgm / 1000.0) / 1e9, 1), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(bg / (tgm / 1000.0) / 1e9 / hbm_peak, 4),
             "bytes_per_launch": bg, "ms_per_launch": round(tgm, 4),
