@@ -142,7 +142,8 @@ __device__ __forceinline__ double assemble(int64_t hi, int64_t lo, int s) {
   const int64_t t = (hi << (32 - kAsmShift)) + (lo >> kAsmShift);
   const uint64_t sign = (uint64_t)t & 0x8000000000000000ull;
   const uint64_t a = t < 0 ? (uint64_t)(-t) : (uint64_t)t;
-  const int lz = __clzll((long long)a);                 // 64 when a == 0
+  const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
+  const int lz = ah != 0 ? __clz(ah) : 32 + __clz(al);  // 64 when a == 0 (32-bit counts)
   const uint64_t m = a << (lz & 63);                    // leading one at bit 63
   const int ef = 63 - lz + s + 1023;
   uint64_t bits = sign | ((uint64_t)(uint32_t)ef << 52) | ((m >> 11) & 0xFFFFFFFFFFFFFull);
@@ -1252,7 +1253,8 @@ __device__ __forceinline__ double i128_to_double(__int128 v, int s) {
   const uint64_t sign = v < 0 ? 0x8000000000000000ull : 0ull;
   const unsigned __int128 a = v < 0 ? (unsigned __int128)(-v) : (unsigned __int128)v;
   const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
-  const int lz = hi != 0 ? __clzll((long long)hi) : 64 + __clzll((long long)lo);   // 128 for 0
+  const uint32_t w3 = (uint32_t)(hi >> 32), w2 = (uint32_t)hi, w1 = (uint32_t)(lo >> 32), w0 = (uint32_t)lo;
+  const int lz = w3 != 0 ? __clz(w3) : w2 != 0 ? 32 + __clz(w2) : w1 != 0 ? 64 + __clz(w1) : 96 + __clz(w0);
   const unsigned __int128 nrm = a << (lz & 127);
   const uint64_t m = (uint64_t)(nrm >> 64);
   const int ef = 127 - lz + s + 1023;
