@@ -285,6 +285,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         print(json.dumps({"only": "gram1", "n": n, "nv": 7, "b": 4}))
         return
+    if args.only in ("tcrestart", "tcupdate", "tcgram"):
+        # the tensor-core kernels at the FP64 solve's shapes: the restart product (8 blocks of
+        # n x 4 into 5), the second pass's update W - V G1 (8 blocks into 1), its Gram (9 blocks
+        # against n x 4)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        Vt = fe.random_normal((9 if args.only == "tcgram" else 8) * n, 4, dtype=torch.float64,
+                              seed=5).view(-1, n, 4)
+        Wt = fe.random_normal(n, 4, dtype=torch.float64, seed=6)
+        Yt = torch.randn(32, 20, dtype=torch.float64, device="cuda", generator=gen)
+        Ot = torch.empty((5, n, 4), dtype=torch.float64, device="cuda")
+        Ct = (torch.randn(32, 4, dtype=torch.float64, device="cuda", generator=gen) * 1e-3)
+        for _ in range(args.warmup + args.steps):
+            if args.only == "tcrestart":
+                fe.block_combine(Vt, Yt, 5, Ot, engine="tc")
+            elif args.only == "tcupdate":
+                fe.block_update(Vt, Ct, Wt, -1.0, 1.0, engine="tc")
+            else:
+                fe.block_gram(Vt, Wt, engine="tc")
+        torch.cuda.synchronize()
+        print(json.dumps({"only": args.only, "n": n}))
+        return
     if args.only == "ugram1":
         # one fused update + Gram launch at the FP64 solve's shape (7 blocks of n x 4)
         Vg, Cg, Wg = ugram_inputs(fe, torch, n)
@@ -891,9 +912,10 @@ def main():
                     help="skip the full scale-14 solves (both arms)")
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
                     help="where the clock samples are written")
-    ap.add_argument("--only", default="all", choices=["all", "solve", "spmm1", "gram1", "ugram1"],
-                    help="solve: warm-up + timed solves only; spmm1 / gram1 / ugram1: launches "
-                         "of one kernel only (profiler captures)")
+    ap.add_argument("--only", default="all",
+                    choices=["all", "solve", "spmm1", "gram1", "ugram1", "tcrestart", "tcupdate", "tcgram"],
+                    help="solve: warm-up + timed solves only; spmm1 / gram1 / ugram1 / tcrestart / "
+                         "tcupdate / tcgram: launches of one kernel only (profiler captures)")
     ap.add_argument("--b", type=int, default=4)
     ap.add_argument("--solve-mode", default="fp64", choices=["fp64", "mixed"],
                     help="--only solve: which solve to run")
