@@ -250,6 +250,48 @@ def test_tc_gram_matches_oracle(shape):
     _gram_check(Vh, Wh, G.cpu().numpy())
 
 
+def _offset_dev(h, off):
+    """h on the device, starting `off` doubles into a larger buffer (8 bytes off a 16-byte
+    boundary for odd off): the tensor-core kernels then read rows with plain loads instead of
+    TMA bulk copies."""
+    t = torch()
+    buf = t.zeros(h.size + off + 1, dtype=t.float64, device="cuda")
+    view = buf[off:off + h.size].view(h.shape)
+    view.copy_(t.from_numpy(np.ascontiguousarray(h)))
+    return view
+
+
+@pytest.mark.parametrize("n,nv,bv,nout", [(4099, 8, 4, 5), (1000, 3, 2, 4), (2048, 12, 4, 1)])
+def test_tc_combine_unaligned_blocks(n, nv, bv, nout):
+    """V 8 bytes off a 16-byte boundary (no TMA staging) and an unaligned output: the same bound
+    as the aligned case, bit-identical to the aligned result."""
+    rng = np.random.default_rng(n + nv)
+    Vh = rng.standard_normal((nv, n, bv))
+    Yh = rng.standard_normal((nv * bv, nout * bv))
+    t = torch()
+    Y = to_dev(Yh)
+    out_a = fe.block_combine(to_dev(Vh), Y, nout, engine="tc")
+    Ou = _offset_dev(np.zeros((nout, n, bv)), 1)
+    fe.block_combine(_offset_dev(Vh, 1), Y, nout, Out=Ou, engine="tc")
+    t.cuda.synchronize()
+    got = _flat(Ou.cpu().numpy())
+    assert np.array_equal(got, _flat(out_a.cpu().numpy()))
+    _check(Vh, Yh, got)
+
+
+@pytest.mark.parametrize("n,nv,bv,bw", [(4099, 9, 4, 4), (3001, 5, 2, 2)])
+def test_tc_gram_unaligned_blocks(n, nv, bv, bw):
+    """V and W 8 bytes off a 16-byte boundary (plain loads instead of TMA staging): within the
+    stated bound, bit-identical to the aligned result."""
+    rng = np.random.default_rng(n + 5 * nv)
+    Vh = rng.standard_normal((nv, n, bv))
+    Wh = rng.standard_normal((n, bw))
+    Ga = fe.block_gram(to_dev(Vh), to_dev(Wh), engine="tc").cpu().numpy()
+    Gu = fe.block_gram(_offset_dev(Vh, 1), _offset_dev(Wh, 1), engine="tc").cpu().numpy()
+    assert np.array_equal(Ga, Gu)
+    _gram_check(Vh, Wh, Gu)
+
+
 def test_tc_gram_integers_exact_and_alias():
     """Integer data: every tile's digit products and their FP64 sums are exact, so G equals the
     integer product; W may be one of V's blocks."""
