@@ -19,12 +19,12 @@
 // 2^-49 (K + 1) max_c |V[r][c]| max_c |Y[c][q]| + 2^-52 |result|; the FP64 pipe is not used at
 // all (FP64 on this part runs at 1/64 of FP32).
 //
-// Kernel structure (one 128-row tile per loop trip, two persistent CTAs of 256 threads per SM):
-// two threads share a row of the V tile; each loads and splits half of its K values and writes
-// the digits into shared memory in the no-swizzle K-major core-matrix layout; thread 0 issues
-// the 28 x (K/16) tcgen05.mma into the CTA's tensor memory and commits to an mbarrier; then
-// each of the two threads reads the row's accumulators (TMEM lane = row) for half of the N
-// results with tcgen05.ld, assembles them in FP64 and stores them.
+// Kernels: for K <= 32 a warp-specialised pipeline (tc_combine_pipe_kernel: TMA producer,
+// digit splitters, one MMA-issuing thread, result assemblers over double-buffered tiles; see its
+// comment); for 32 < K <= 64 tc_combine_kernel, one 128-row tile per loop trip and two
+// persistent CTAs of 256 threads per SM: two threads share a row of the V tile, each splits half
+// of its K values into the digit tiles, thread 0 issues one MMA per digit and K-step and commits
+// to an mbarrier, then the two threads assemble half of the row's N results each.
 #include <math.h>
 #include <string.h>
 
@@ -937,19 +937,17 @@ int tc_combine(const BlockSet& V, int64_t n, const double* Y, int ldy, const Blo
 // (i, c) of V^T (7 * KV <= 252 rows, two 128-row M tiles), B the digit rows (j, q) of W^T
 // (7 * bw rows), K = the tile's 128 rows; every accumulator D[(i, c)][(j, q)] sums 128
 // products below 2^16 and is exact.  TMEM lane (i, c) then forms T_i = sum_j D 2^(8 (6 - j))
-// for each q in 64-bit integers and converts it, scaled by 2^(8 (6 - i)) and the tile's column
-// exponents, to FP64; the seven slices i are added in FP64 (smallest first) into the CTA's
-// accumulator of G, and the CTAs' partial Gram matrices are added in a fixed order.  (The
-// pipelined form below adds the slices exactly in 128-bit integers and rounds once per tile.)
+// for each q in 64-bit integers; the seven slices i of each output are added exactly in
+// 128-bit integers, and the sum, scaled by the tile's column exponents, is rounded once to FP64
+// and added to the CTA's accumulator of G, and the CTAs' partial Gram matrices are added in a fixed order.
 // Error per tile: 2^-50 * 128 * max|V[., c]| * max|W[., q]| over the tile's rows, plus the FP64
-// roundings of the sums over slices, tiles and CTAs.
+// roundings of the sums over tiles and CTAs.
 namespace {
 constexpr int kGramMaxKV = 36;                       // 7 * 36 = 252 digit rows of V^T
 constexpr int kGramMaxBW = 8;                        // 7 * 8 = 56 digit rows of W^T
 constexpr int kGramRows = 128;                       // rows per tile (MMA K = 8 x 16)
 constexpr uint32_t kGSBO = (kGramRows / 8) * kCoreBytes;  // 2048 B between 8-row groups
 constexpr int kGATile = 128 * kGramRows * 2;         // one 128-row M tile of V^T digits: 32 KB
-constexpr int kGramUnits = 4;                        // (column, 8-row group) units per thread
 
 struct TcGramArgs {
   const double* vblk[kMaxBlocks];
@@ -964,240 +962,6 @@ struct TcGramArgs {
   int nxb;               // staging buffers of the pipelined kernel (1 or 2)
 };
 }  // namespace
-
-template <int BW>
-__global__ void __launch_bounds__(256, 2) tc_gram_kernel(const TcGramArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr int bw = BW;
-  constexpr int NP = (7 * BW + 15) / 16 * 16;
-  const int KV = a.KV, nmt = a.nmt;
-  const int ncol = KV + bw;
-  unsigned char* sA = smem;                                   // nmt x 32 KB
-  unsigned char* sB = sA + (size_t)nmt * kGATile;             // NP x 128 FP16
-  // staged rows: V block j at sX + j * XS, W at sX + nvb * XS; XS = 128 rows + 4 doubles of
-  // padding, so that the blocks' rows fall on different shared-memory banks
-  double* sX = reinterpret_cast<double*>(sB + (size_t)NP * kGramRows * 2);
-  // per-slice partial products [7 KV][bw]: they live in the A tiles, which are free from the end
-  // of a tile's MMAs to the next tile's digit writes
-  double* sPd = reinterpret_cast<double*>(sA);
-  const int XS = kGramRows * a.bv + 4;           // doubles per staged V block
-  const int nvb = KV / a.bv;
-  int* sEx = reinterpret_cast<int*>(sX + (size_t)nvb * XS + (size_t)kGramRows * BW + 4);  // [2][ncol]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sEx + 2 * (kGramMaxKV + kGramMaxBW));
-  uint64_t* lbar = bar + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols_t = nmt * NP <= 32 ? 32u : nmt * NP <= 64 ? 64u : 128u;
-
-  // zero the digit tiles once (rows beyond 7 KV / 7 bw stay zero), exponents of tile 0
-  {
-    int4* z = reinterpret_cast<int4*>(smem);
-    const int n16 = (int)(((size_t)nmt * kGATile + (size_t)NP * kGramRows * 2) / 16);
-    for (int e = tid; e < n16; e += 256) z[e] = make_int4(0, 0, 0, 0);
-    for (int e = tid; e < 2 * ncol; e += 256) sEx[e] = 0;
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(tslot, ncols_t);
-    tc::tmem_relinquish();
-  }
-  const int64_t ntiles = (a.n + kGramRows - 1) / kGramRows;
-  // the tile's rows of every V block and of W by TMA bulk copies (block j's rows land at
-  // sX + j * XS, W's at sX + nvb * XS) when the byte counts are multiples of 16
-  auto bulk_ok = [&](int64_t t) {
-    const int64_t rows = min((int64_t)kGramRows, a.n - t * kGramRows);
-    return a.bulk && (rows * a.bv * 8) % 16 == 0 && (rows * bw * 8) % 16 == 0;
-  };
-  auto issue = [&](int64_t t) {
-    const int64_t r0 = t * kGramRows;
-    const int64_t rows = min((int64_t)kGramRows, a.n - r0);
-    const uint32_t vb = (uint32_t)(rows * a.bv * 8), wb = (uint32_t)(rows * bw * 8);
-    tc::mbar_arrive_expect_tx(lbar, vb * (uint32_t)nvb + wb);
-    for (int j = 0; j < nvb; ++j) tc::bulk_g2s(sX + (size_t)j * XS, a.vblk[j] + r0 * a.bv, vb, lbar);
-    tc::bulk_g2s(sX + (size_t)nvb * XS, a.W + r0 * bw, wb, lbar);
-  };
-  if (tid == 0) {
-    tc::mbar_init(bar, 1);
-    tc::mbar_init(lbar, 1);
-    tc::mbar_fence_init();
-  }
-  tc::fence_async_smem();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  if (tid == 0 && (int64_t)blockIdx.x < ntiles && bulk_ok(blockIdx.x)) issue(blockIdx.x);
-  const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_f16_f32(128, NP);
-  const uint32_t sa0 = tc::smem_addr(sA), sb0 = tc::smem_addr(sB);
-  const int nout = KV * bw;
-  double acc[(kGramMaxKV * kGramMaxBW + 255) / 256];
-#pragma unroll
-  for (int k = 0; k < (kGramMaxKV * kGramMaxBW + 255) / 256; ++k) acc[k] = 0.0;
-  uint32_t phase = 0;
-  bool failed = false;
-  int par = 0;
-
-  // this thread's (column, 8-row group) units -- the same in every tile: column pointer and
-  // stride, and where each digit's 16-byte core-matrix row goes
-  const double* ucol[kGramUnits];
-  int ustride[kGramUnits], uc[kGramUnits], ug[kGramUnits], usoff[kGramUnits];
-#pragma unroll
-  for (int k = 0; k < kGramUnits; ++k) {
-    const int u = tid + 256 * k;
-    uc[k] = u < ncol * 16 ? u % ncol : -1;
-    ug[k] = u / ncol;
-    ucol[k] = nullptr;
-    ustride[k] = 0;
-    usoff[k] = 0;
-    if (uc[k] >= 0) {
-      const int c = uc[k];
-      ucol[k] = c < KV ? a.vblk[c / a.bv] + c % a.bv : a.W + (c - KV);
-      ustride[k] = c < KV ? a.bv : bw;
-      usoff[k] = c < KV ? (c / a.bv) * XS + c % a.bv : nvb * XS + (c - KV);
-    }
-  }
-
-  uint32_t lphase = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, par ^= 1) {
-    int* ex = sEx + par * ncol;          // this tile's column exponents
-    int* ex_next = sEx + (par ^ 1) * ncol;
-    const int64_t r0 = tile * kGramRows;
-    const bool bulk = bulk_ok(tile);
-    bool ok = true;
-    if (bulk) {
-      ok = wait_sleep(lbar, lphase);
-      if (!ok) {
-        failed = true;
-        wait_sleep(lbar, lphase);  // no copy left in flight
-      }
-      lphase ^= 1;
-    }
-    // ---- (column, 8-row group) units and the tile's column exponents
-    double x[kGramUnits][8];
-#pragma unroll
-    for (int k = 0; k < kGramUnits; ++k) {
-      if (uc[k] >= 0) {
-        int e = 0;
-        const int64_t rb = r0 + ug[k] * 8;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int64_t r = rb + t;
-          double v = 0.0;
-          if (r < a.n) v = bulk ? sX[usoff[k] + (ug[k] * 8 + t) * ustride[k]] : __ldg(ucol[k] + r * ustride[k]);
-          x[k][t] = v;
-          e = max(e, exp_field(v));
-        }
-        atomicMax(ex + uc[k], e);
-      }
-    }
-    for (int e = tid; e < ncol; e += 256) ex_next[e] = 0;   // the next tile's exponents start at 0
-    __syncthreads();  // every unit is in registers: the staging buffer takes the next tile
-    if (tid == 0) {
-      const int64_t nt = tile + gridDim.x;
-      if (nt < ntiles && bulk_ok(nt)) issue(nt);
-    }
-    // ---- digits: column c's 8-row group g as one 16-byte core-matrix row per digit
-#pragma unroll
-    for (int k = 0; k < kGramUnits; ++k) {
-      if (uc[k] >= 0) {
-        const int c = uc[k], g = ug[k];
-        const int emax = ex[c];
-        uint32_t w[kDigits][4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const double x0 = x[k][2 * e], x1 = x[k][2 * e + 1];
-          split_pair_f16(x0, x1, emax, w, e);
-        }
-#pragma unroll
-        for (int i = 0; i < kDigits; ++i) {
-          unsigned char* dst;
-          if (c < KV) {
-            const int m = i * KV + c;
-            dst = sA + (size_t)(m >> 7) * kGATile + ((m & 127) >> 3) * kGSBO + g * kCoreBytes + (m & 7) * 16;
-          } else {
-            const int nn = i * bw + (c - KV);
-            dst = sB + (nn >> 3) * kGSBO + g * kCoreBytes + (nn & 7) * 16;
-          }
-          *reinterpret_cast<uint4*>(dst) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
-        }
-      }
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- all digit products of the tile: D_mt = A_mt B^T over 8 K-steps of 16 rows
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int mt = 0; mt < nmt; ++mt)
-#pragma unroll
-        for (int ks = 0; ks < kGramRows / 16; ++ks) {
-          const uint64_t ad = tc::smem_desc(sa0 + mt * kGATile + ks * 2 * kCoreBytes, kCoreBytes, kGSBO);
-          const uint64_t bd = tc::smem_desc(sb0 + ks * 2 * kCoreBytes, kCoreBytes, kGSBO);
-          tc::mma_f16(tbase + (uint32_t)(mt * NP), ad, bd, idesc, ks > 0 ? 1u : 0u);
-        }
-      tc::mma_commit(bar);
-    }
-    if (!wait_sleep(bar, phase)) {
-      ok = false;
-      failed = true;
-      wait_sleep(bar, phase);
-    }
-    phase ^= 1;
-    tc::fence_after_sync();
-    // ---- lane (i, c) of M tile mt: T_i for every q, to FP64 with the tile's scales
-    const int mt = warp >> 2;
-    if (mt < nmt) {
-      const int m = mt * 128 + (warp & 3) * 32 + lane;
-      const uint32_t laddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * NP);
-      uint32_t d[NP / 4][4];
-#pragma unroll
-      for (int c4 = 0; c4 < NP / 4; ++c4) tc::tmem_ld4(laddr + (uint32_t)(4 * c4), d[c4]);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int c4 = 0; c4 < NP / 4; ++c4) tc::reg_after_wait(d[c4]);
-      if (m < 7 * KV) {
-        const int i = m / KV, c = m % KV;
-        const int ec = ex[c];
-#define DG(j) acc_int(d[((j) * bw + q) / 4][((j) * bw + q) % 4])
-#pragma unroll
-        for (int q = 0; q < bw; ++q) {
-          {
-            const int64_t hi = ((int64_t)DG(0) << 16) + ((int64_t)DG(1) << 8) + DG(2);
-            const int64_t lo = ((int64_t)DG(3) << 24) + ((int64_t)DG(4) << 16) + ((int64_t)DG(5) << 8) + DG(6);
-            const int fq = ex[KV + q];
-            double y = 0.0;
-            if (!ok) y = __longlong_as_double(0x7FF8000000000000ll);
-            else if (ec > 0 && fq > 0) y = assemble(hi, lo, ec + fq - 2108 + kAsmShift - 8 * i);
-            sPd[q * (7 * KV) + m] = y;
-          }
-        }
-#undef DG
-      }
-    }
-    __syncthreads();
-    // ---- G[c][q] += sum over the slices i, smallest first
-#pragma unroll
-    for (int k = 0; k < (kGramMaxKV * kGramMaxBW + 255) / 256; ++k) {
-      const int o = tid + 256 * k;
-      if (o < nout) {
-        const int c = o / bw, q = o % bw;
-        double t = 0.0;
-#pragma unroll
-        for (int i = kDigits - 1; i >= 0; --i) t += sPd[q * (7 * KV) + i * KV + c];
-        acc[k] += t;
-      }
-    }
-    tc::fence_before_sync();
-    __syncthreads();  // TMEM, digit tiles and sPd free for the next tile
-  }
-#pragma unroll
-  for (int k = 0; k < (kGramMaxKV * kGramMaxBW + 255) / 256; ++k) {
-    const int o = tid + 256 * k;
-    if (o < nout) a.partial[(int64_t)blockIdx.x * nout + o] = acc[k];
-  }
-  if (failed && lane == 0) atomicExch(a.status, 1);
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tbase, ncols_t);
-}
 
 // ---------------------------------------------------------------- pipelined Gram
 // The same Gram with its phases overlapped, in the warp roles of the pipelined block product:
@@ -1573,53 +1337,19 @@ int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha,
   a.NP = (int)ceil_div(7 * bw, 16) * 16;
   a.nmt = (int)ceil_div(7 * a.KV, 128);
   a.n = n;
-  {
-    GramPipeLayout L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV, 2);
-    if (L.total > 227 * 1024) L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV, 1);
-    a.nxb = L.nxb;
-    if (L.total <= 227 * 1024 && a.KV * bw <= 3 * kGEpiThreads) {
-      static KernelSetup kp[4];
-      const int bj = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
-      const void* fp = bw == 1 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<1>)
-                     : bw == 2 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<2>)
-                     : bw == 4 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<4>)
-                               : reinterpret_cast<const void*>(tc_gram_pipe_kernel<8>);
-      FE_TRY(kernel_configure(kp[bj], fp, 227 * 1024));
-      const int64_t nt = ceil_div(n, kGramRows);
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)num_sms()));
-      const int nout = a.KV * bw;
-      double* scr = small_scratch(18, (size_t)grid * nout + 2);
-      if (!scr) return FE_ERR_OOM;
-      a.partial = scr;
-      a.status = reinterpret_cast<int*>(scr + (size_t)grid * nout);
-      FE_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
-      switch (bw) {
-        case 1: tc_gram_pipe_kernel<1><<<grid, kGPipeThreads, L.total, s>>>(a); break;
-        case 2: tc_gram_pipe_kernel<2><<<grid, kGPipeThreads, L.total, s>>>(a); break;
-        case 4: tc_gram_pipe_kernel<4><<<grid, kGPipeThreads, L.total, s>>>(a); break;
-        default: tc_gram_pipe_kernel<8><<<grid, kGPipeThreads, L.total, s>>>(a); break;
-      }
-      count_launch();
-      FE_CUDA(cudaGetLastError());
-      return gram_reduce(a.partial, grid, nout, alpha, G, s);
-    }
-  }
-  const size_t smem = (size_t)a.nmt * kGATile + (size_t)a.NP * kGramRows * 2 +
-                      sizeof(double) * ((size_t)(a.KV / a.bv) * (kGramRows * a.bv + 4) + (size_t)kGramRows * bw + 4) +
-                      4 * 2 * (kGramMaxKV + kGramMaxBW) + 64;
-  static KernelSetup ks[4];
-  const int bi = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
-  (void)bi;
-  const void* fn = bw == 1 ? reinterpret_cast<const void*>(tc_gram_kernel<1>)
-                 : bw == 2 ? reinterpret_cast<const void*>(tc_gram_kernel<2>)
-                 : bw == 4 ? reinterpret_cast<const void*>(tc_gram_kernel<4>)
-                           : reinterpret_cast<const void*>(tc_gram_kernel<8>);
-  FE_TRY(kernel_configure(ks[bi], fn, 227 * 1024));
-  // two CTAs per SM (registers and shared memory allow it; TMEM: at most 128 columns each), so
-  // that one CTA's loads and digit work overlap the other's MMA wait and sums
-  const int per_sm = smem <= 113 * 1024 ? 2 : 1;   // 2 x (smem + 1 KB reserved) <= 228 KB
-  const int64_t ntiles = ceil_div(n, kGramRows);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms()));
+  GramPipeLayout L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV, 2);
+  if (L.total > 227 * 1024) L = gram_pipe_layout(a.nmt, a.NP, a.KV / a.bv, a.bv, bw, a.KV, 1);
+  a.nxb = L.nxb;
+  FE_ARG(L.total <= 227 * 1024 && a.KV * bw <= 3 * kGEpiThreads, "tc_gram: shape too large");
+  static KernelSetup kp[4];
+  const int bj = bw == 1 ? 0 : bw == 2 ? 1 : bw == 4 ? 2 : 3;
+  const void* fp = bw == 1 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<1>)
+                 : bw == 2 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<2>)
+                 : bw == 4 ? reinterpret_cast<const void*>(tc_gram_pipe_kernel<4>)
+                           : reinterpret_cast<const void*>(tc_gram_pipe_kernel<8>);
+  FE_TRY(kernel_configure(kp[bj], fp, 227 * 1024));
+  const int64_t nt = ceil_div(n, kGramRows);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)num_sms()));
   const int nout = a.KV * bw;
   double* scr = small_scratch(18, (size_t)grid * nout + 2);
   if (!scr) return FE_ERR_OOM;
@@ -1627,10 +1357,10 @@ int tc_gram(const BlockSet& V, int64_t n, const double* W, int bw, double alpha,
   a.status = reinterpret_cast<int*>(scr + (size_t)grid * nout);
   FE_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
   switch (bw) {
-    case 1: tc_gram_kernel<1><<<grid, 256, smem, s>>>(a); break;
-    case 2: tc_gram_kernel<2><<<grid, 256, smem, s>>>(a); break;
-    case 4: tc_gram_kernel<4><<<grid, 256, smem, s>>>(a); break;
-    default: tc_gram_kernel<8><<<grid, 256, smem, s>>>(a); break;
+    case 1: tc_gram_pipe_kernel<1><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+    case 2: tc_gram_pipe_kernel<2><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+    case 4: tc_gram_pipe_kernel<4><<<grid, kGPipeThreads, L.total, s>>>(a); break;
+    default: tc_gram_pipe_kernel<8><<<grid, kGPipeThreads, L.total, s>>>(a); break;
   }
   count_launch();
   FE_CUDA(cudaGetLastError());
