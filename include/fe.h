@@ -201,6 +201,12 @@ int fe_spmm(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
  */
 int fe_spmm_t(fe_csr h, const void* X, void* Y, int b, fe_dtype dt);
 
+/* ------------------------------------------------------------------ block operations */
+/* The n x b block arguments of the block operations below (V, W, Out) are read and written with
+ * 16-byte vector accesses and must start on a 16-byte boundary (every cudaMalloc and torch
+ * allocation does); an unaligned one gives FE_ERR_INVALID.  The small coefficient matrices
+ * (C, Y, G, R) have no alignment requirement. */
+
 /*
  * MvTransMv (Table 1, "op3"): G = alpha * V^T W.
  * V: DEVICE, nv blocks of n x bv (block j at element j*n*bv), so V^T W is (nv*bv) x bw.

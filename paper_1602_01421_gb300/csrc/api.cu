@@ -332,6 +332,7 @@ int fe_block_gram_ex(const void* V, int64_t n, int nv, int bv, const void* W, in
   FE_ARG(nv >= 1 && nv <= 128, "fe_block_gram: nv = %d not in [1, 128]", nv);
   FE_ARG(is_pow2_le16(bv) && is_pow2_le16(bw), "fe_block_gram: bv, bw must be in {1,2,4,8,16}");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_gram: bad dtype");
+  FE_ARG(aligned16(V) && aligned16(W), "fe_block_gram: V and W must be 16-byte aligned");
   BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
   return gram(vs, n, W, bw, bw, dt, alpha, G, cur_stream(), engine);
 }
@@ -363,6 +364,7 @@ int fe_block_update_ex(const void* V, int64_t n, int nv, int bv, const double* C
   }
   FE_ARG(engine == FE_ENGINE_AUTO || engine == FE_ENGINE_FMA || engine == FE_ENGINE_TC,
          "fe_block_update_ex: engine = %d", engine);
+  FE_ARG(aligned16(W) && (nv == 0 || aligned16(V)), "fe_block_update: V and W must be 16-byte aligned");
   BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
   if (engine != FE_ENGINE_FMA) {
     BlockSet ws = make_blockset(W, 1, bw, bw, n * bw, dt);
@@ -390,6 +392,7 @@ int fe_block_combine(const void* V, int64_t n, int nv, int bv, const double* Y, 
     FE_ARG(oa + (size_t)nout * n * bv * es <= va || va + (size_t)nv * n * bv * es <= oa,
            "fe_block_combine: Out aliases V");
   }
+  FE_ARG(aligned16(V) && aligned16(Out), "fe_block_combine: V and Out must be 16-byte aligned");
   BlockSet vs = make_blockset(V, nv, bv, bv, n * bv, dt);
   BlockSet os = make_blockset(Out, nout, bv, bv, n * bv, dt);
   return combine(vs, n, Y, nout * bv, os, dt, cur_stream(), engine);
@@ -410,6 +413,7 @@ int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* 
     FE_ARG(wa + n * b * es <= va || va + (size_t)nv * n * b * es <= wa,
            "fe_block_update_gram: W aliases V");
   }
+  FE_ARG(aligned16(W) && (nv == 0 || aligned16(V)), "fe_block_update_gram: V and W must be 16-byte aligned");
   BlockSet vs = make_blockset(V, nv, b, b, n * b, dt);
   return update_gram(vs, n, C, alpha, beta, nullptr, W, b, dt, 1, nullptr, G, cur_stream());
 }
@@ -422,6 +426,7 @@ int fe_block_orth(const void* V, int64_t n, int nv, int b, void* W, fe_dtype dt,
   FE_ARG(is_pow2_le16(b), "fe_block_orth: b must be in {1,2,4,8,16}");
   FE_ARG((int64_t)(nv + 1) * b <= n, "fe_block_orth: (nv+1)*b > n");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_orth: bad dtype");
+  FE_ARG(aligned16(W) && (nv == 0 || aligned16(V)), "fe_block_orth: V and W must be 16-byte aligned");
   BlockSet vs = make_blockset(V, nv, b, b, n * b, dt);
   DevBuf an;
   FE_TRY(an.alloc(sizeof(double)));

@@ -45,6 +45,8 @@ struct DevBuf {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline bool is_pow2_le16(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16; }
+// Block arguments are read and written with 16-byte vector accesses.
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 int num_sms();  // SMs of the current device
 
 // Per-device launch set-up of one kernel, shared by every host thread.  The dynamic shared-

@@ -48,6 +48,7 @@ extern "C" int fe_block_gram_noalloc(const void* V, int64_t n, int nv, int bv, c
   FE_ARG(nv >= 1 && nv <= 32, "fe_block_gram_noalloc: nv = %d not in [1, 32]", nv);
   FE_ARG(is_pow2_le16(bv) && is_pow2_le16(bw), "fe_block_gram_noalloc: bv, bw must be in {1,2,4,8,16}");
   FE_ARG(dt == FE_F32 || dt == FE_F64, "fe_block_gram_noalloc: bad dtype");
+  FE_ARG(aligned16(V) && aligned16(W), "fe_block_gram_noalloc: V and W must be 16-byte aligned");
   const int nout = nv * bv * bw;
   FE_ARG(nout <= kNoAllocMaxOutputs,
          "fe_block_gram_noalloc: G has nv*bv*bw = %d entries, more than the %d this entry point "

@@ -306,7 +306,9 @@ __global__ void __launch_bounds__(kThreads, KMAX <= 32 ? 2 : 1) tc_combine_kerne
 #pragma unroll
           for (int p = 0; p < BV; ++p) v[c0 + p] = src[p];
         } else {
-          ld_row<double, BV>(a.vblk[(cbeg + c0) / BV] + r * BV, &v[c0]);
+          const double* src = a.vblk[(cbeg + c0) / BV] + r * BV;   // scalar loads: any alignment
+#pragma unroll
+          for (int p = 0; p < BV; ++p) v[c0 + p] = src[p];
         }
       } else {
 #pragma unroll
