@@ -197,7 +197,7 @@ __device__ int jacobi_sweeps(T* A, T* Q, int ld, int m, int mp, double thresh, i
 // (2 mp ld doubles of global memory, L2-resident).
 // Two precisions: FP32 Jacobi sweeps take the matrix to a relative off-diagonal norm of about
 // 1e-6 (FP32 rotations run at the FP32 rate of the SM, FP64 ones at 1/64 of it); the FP32
-// eigenvector matrix is made exactly orthogonal in FP64 (Cholesky QR), the FP64 matrix is
+// eigenvector matrix is made orthogonal to FP64 rounding (two Newton-Schulz steps), the FP64 matrix is
 // transformed by it (Q^T T Q, an exact orthogonal similarity), and FP64 sweeps finish from there
 // -- two or three, since Jacobi converges quadratically once the off-diagonal part is small.
 template <bool BIG>
