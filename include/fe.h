@@ -427,6 +427,15 @@ typedef struct {
                              vectors <= 32), and the second Gram-Schmidt pass (update and
                              Gram) on the tensor cores where the shapes allow (nv*b <= 36,
                              b <= 8); FP64 FMA elsewhere (FE_ENGINE_AUTO) */
+  int orth_local;         /* FP64 subspace, first Gram-Schmidt pass of a new block W = A v_j:
+                             1 = its coefficients against the older blocks v_i (i < j) are read
+                             from the projected matrix, v_i^T A v_j = H[j][i] for symmetric A
+                             (the Lanczos recurrence: nonzero only for v_{j-1} and, after a
+                             restart, the kept vectors), and only v_j^T W is computed; the
+                             second pass is the full Gram as always (1); 0 = a full Gram in the
+                             first pass too.  FP32 subspaces (the mixed mode's first phase)
+                             always take the full first pass: there it keeps the restart
+                             count lower */
 } fe_eigs_opts;
 
 void fe_eigs_opts_default(fe_eigs_opts* opts);

@@ -229,12 +229,13 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
          mode: str = "fp64", start=None, seed: int = 1, max_restarts: int = 500,
          mlp_weights=None, mlp_hidden: int = 64, mixed_tol: float = 5e-6,
          orth_pass1: str = "fp32", return_vectors: bool = True, raise_on_noconverge: bool = True,
-         subspace: str = "device", engine: str = "auto"):
+         subspace: str = "device", engine: str = "auto", orth_local: bool = True):
     """Block Krylov-Schur (fe_eigs_ex).  subspace="host" keeps the subspace blocks in pinned
     host memory (newest block cached on the device).  Returns (evals numpy, evecs (n, nev) CUDA float64 or
     None, stats dict).  orth_pass1: "fp32" or "fp64" arithmetic for the first Gram-Schmidt
     pass's Gram on an FP64 subspace.  engine: "auto"/"tc" (tensor-core restart products where
-    supported) or "fma"."""
+    supported) or "fma".  orth_local: first Gram-Schmidt pass from the projected matrix's
+    symmetry (only v_j^T W computed) instead of a full Gram."""
     torch = _torch()
     lib = load()
     o = _lib.EigsOpts()
@@ -246,6 +247,7 @@ def eigs(h: Csr, nev: int, block: int, nblocks: int, tol: float = 1e-8, which: s
     o.orth_pass1 = {"fp32": 0, "fp64": 1}[orth_pass1]
     o.subspace_host = {"device": 0, "host": 1}[subspace]
     o.engine = _lib.ENGINE[engine]
+    o.orth_local = 1 if orth_local else 0
     o.mlp_hidden = int(mlp_hidden)
     if start is not None:
         start = start.to(torch.float64).contiguous()

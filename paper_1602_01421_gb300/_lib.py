@@ -52,7 +52,7 @@ class EigsOpts(ctypes.Structure):
                 ("mlp_weights", ctypes.c_void_p), ("mlp_hidden", ctypes.c_int),
                 ("mixed_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
                 ("orth_pass1", ctypes.c_int), ("subspace_host", ctypes.c_int),
-                ("engine", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("orth_local", ctypes.c_int)]
 
 
 class EigsStats(ctypes.Structure):

@@ -37,7 +37,8 @@ namespace fe {
 
 int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
             int update_anorm, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
-            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32, int engine);
+            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32, int engine,
+            const double* d_known = nullptr, int ldk = 0, int nz_first = 0);
 int launch_ritz(const double* H, int m, int b, int which, int max_sweeps, double tol,
                 double* theta, double* Y, double* rho, int* info, double* work, cudaStream_t s);
 size_t ritz_work_doubles(int m);
@@ -107,6 +108,7 @@ struct Phase {
   uint64_t seed;
   int max_restarts, max_sweeps;
   int pass1_f32 = 0;  // FP64 subspace: first Gram-Schmidt pass's Gram in FP32 arithmetic
+  int orth_local = 1; // first pass: older blocks' coefficients from H (symmetry), v_j^T W only
   int op_ata = 0;  // 1: iterate with A^T A (SVD of a directed graph's matrix, Section 4.3.2)
   int subspace_host = 0;  // 1: subspace blocks in mapped pinned host memory, newest block cached
   int engine = FE_ENGINE_AUTO;  // FP64 restart / Ritz-vector products (tensor cores where supported)
@@ -204,9 +206,14 @@ struct Phase {
       FE_TRY(spmm_dispatch(x, w));
       ++spmm_blocks;
       BlockSet V = slots(0, j + 1);
+      // v_i^T A v_j = H[j][i] (i < j) for symmetric A: block row j of H holds the first
+      // pass's coefficients against the older blocks -- R_{j-1}^T for v_{j-1}, and after a
+      // restart (j = k / b) the coupling of the kept vectors; zero elsewhere
+      const int nz_first = j == k / b ? 0 : j - 1;
       FE_TRY(orth_ex(V, n, w, b, dt, anorm, 1, seed, &rng_counter, H + (size_t)j * b, m,
                      H + (size_t)(j + 1) * b * m + (size_t)j * b, m, &replacements, s, pass1_f32,
-                     orth_engine()));
+                     orth_engine(), orth_local && dt == FE_F64 ? H + (size_t)j * b * m : nullptr, m,
+                     nz_first));
       if (subspace_host) {
         FE_CUDA(cudaMemcpyAsync(slot[j + 1], w, (size_t)n * b * dt_size(dt), cudaMemcpyDefault, s));
         std::swap(cache[0], cache[1]);
@@ -397,6 +404,7 @@ void fe_eigs_opts_default(fe_eigs_opts* o) {
   o->mlp_hidden = 64;
   o->mixed_tol = 5e-6;
   o->max_sweeps = 60;
+  o->orth_local = 1;
 }
 
 int fe_eigs(fe_csr h, int nev, int block, int nblocks, double tol, fe_which which,
@@ -455,6 +463,7 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
   p1.max_restarts = o.max_restarts;
   p1.max_sweeps = o.max_sweeps;
   p1.pass1_f32 = o.orth_pass1 == 0;
+  p1.orth_local = o.orth_local != 0;
   p1.op_ata = op_ata;
   p1.subspace_host = o.subspace_host != 0;
   p1.engine = o.engine;
@@ -520,6 +529,7 @@ static int solve(fe_csr h, int nev, int block, int nblocks, double tol, fe_which
     p2.max_restarts = o.max_restarts;
     p2.max_sweeps = o.max_sweeps;
     p2.pass1_f32 = o.orth_pass1 == 0;
+    p2.orth_local = o.orth_local != 0;
     p2.op_ata = op_ata;
     p2.subspace_host = o.subspace_host != 0;
     p2.engine = o.engine;

@@ -332,9 +332,25 @@ static int orth_fallback(const BlockSet& V, int64_t n, void* W, int b, fe_dtype 
   return FE_OK;
 }
 
+// sG1 ((k + b) x b, rows j*b + p for block j's column p, then the b rows of S1): rows of the
+// older blocks from the known coefficients (row r, column q = known[q * ldk + r], blocks below
+// nz_first zero), the newest block's rows and S1 from the local Gram [v_last W]^T W (2b x b).
+__global__ void known_g1_kernel(double* __restrict__ sG1, int k, int b, const double* __restrict__ known,
+                                int ldk, int nz_first, const double* __restrict__ local) {
+  const int kold = k - b;
+  for (int e = threadIdx.x; e < (k + b) * b; e += blockDim.x) {
+    const int r = e / b, q = e - (e / b) * b;
+    double x;
+    if (r < kold) x = r / b >= nz_first ? known[(size_t)q * ldk + r] : 0.0;
+    else x = local[(r - kold) * b + q];
+    sG1[e] = x;
+  }
+}
+
 int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_anorm,
             int update_anorm, uint64_t seed, uint64_t* rng_counter, double* d_G, int ldg,
-            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32, int engine) {
+            double* d_R, int ldr, int* replaced, cudaStream_t s, int pass1_f32, int engine,
+            const double* d_known, int ldk, int nz_first) {
   FE_ARG(V.nv >= 0 && V.nv + 1 <= kMaxBlocks, "orth: too many blocks");
   FE_ARG(b >= 1 && b <= 16, "orth: b = %d", b);
   const int k = V.nv * b;
@@ -355,11 +371,30 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   BlockSet Vx = blockset_of(vx, b, b);
   FE_ARG(V.nv == 0 || V.bv == b, "orth: V block width %d != b %d", V.bv, b);
   // pass 1: [G1; S1] = [V W]^T W (FP64 blocks: optionally in FP32 arithmetic -- G1 only steers
-  // the first subtraction; pass 2 is FP64, and H receives G1 + G2, what was actually subtracted)
-  if (pass1_f32 && dt == FE_F64)
+  // the first subtraction; pass 2 is FP64, and H receives G1 + G2, what was actually subtracted).
+  // With known coefficients (d_known: the solver's symmetric projected matrix) only the newest
+  // block's rows and S1 are computed, [v_last W]^T W; the first update then involves blocks
+  // nz_first .. last only.
+  const bool local = d_known != nullptr && V.nv > 0;
+  int v0 = 0;   // first block of the first update
+  if (local) {
+    FE_ARG(nz_first >= 0 && nz_first < V.nv, "orth: nz_first = %d", nz_first);
+    v0 = nz_first;
+    BlockSet Vl = blockset_of({V.blk[V.nv - 1], W}, b, b);
+    double* sLoc = small_scratch(19, (size_t)2 * b * b);
+    if (!sLoc) return FE_ERR_OOM;
+    if (pass1_f32 && dt == FE_F64)
+      FE_TRY(gram_f32_arith(Vl, n, static_cast<const double*>(W), b, 1.0, sLoc, s));
+    else
+      FE_TRY(gram(Vl, n, W, b, b, dt, 1.0, sLoc, s));
+    known_g1_kernel<<<1, 256, 0, s>>>(sG1, k, b, d_known, ldk, nz_first, sLoc);
+    count_launch();
+    FE_CUDA(cudaGetLastError());
+  } else if (pass1_f32 && dt == FE_F64) {
     FE_TRY(gram_f32_arith(Vx, n, static_cast<const double*>(W), b, 1.0, sG1, s));
-  else
+  } else {
     FE_TRY(gram(Vx, n, W, b, b, dt, 1.0, sG1, s));
+  }
   // the fused update + Gram sweeps hold a b x b accumulator per lane: b = 16 keeps two kernels
   const bool fused = b <= 8;
   // FP64 blocks on the tensor cores (engine AUTO or TC): the update as a split-product block
@@ -369,7 +404,9 @@ int orth_ex(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d
   const bool tc2 = V.nv > 0 && engine != FE_ENGINE_FMA && dt == FE_F64 &&
                    tc_combine_supported(V, Wset, dt) && tc_gram_supported(Vx, b, b, dt);
   if (tc2) {
-    FE_TRY(tc_combine(V, n, sG1, b, Wset, s, -1.0, 1.0));     // W <- W - V G1
+    std::vector<const void*> vu(V.blk + v0, V.blk + V.nv);
+    BlockSet Vu = blockset_of(vu, b, b);
+    FE_TRY(tc_combine(Vu, n, sG1 + (size_t)v0 * b * b, b, Wset, s, -1.0, 1.0));   // W <- W - V G1
     FE_TRY(tc_gram(Vx, n, static_cast<const double*>(W), b, 1.0, sG2, s));  // [G2; S]
     orth_post2_kernel<<<1, 256, 0, s>>>(sG1, sG2, k, b, d_anorm, update_anorm, d_G, ldg, sRacc,
                                         sM, sC, status);
@@ -426,7 +463,7 @@ int orth(const BlockSet& V, int64_t n, void* W, int b, fe_dtype dt, double* d_an
          double* d_R, int ldr, int* replaced, cudaStream_t s) {
   (void)anorm_floor;
   return orth_ex(V, n, W, b, dt, d_anorm, 0, seed, rng_counter, d_G, ldg, d_R, ldr, replaced, s, 0,
-                 FE_ENGINE_FMA);
+                 FE_ENGINE_FMA, nullptr, 0, 0);
 }
 
 }  // namespace fe

@@ -85,7 +85,7 @@ def test_struct_layouts_match_header():
     # field offsets the C compiler gives the structs (x86-64 and aarch64 share the LP64 ABI)
     assert ctypes.sizeof(_lib.CsrOpts) == 72
     assert ctypes.sizeof(_lib.CsrInfo) == 120
-    assert ctypes.sizeof(_lib.EigsOpts) == 72
+    assert ctypes.sizeof(_lib.EigsOpts) == 80
     assert ctypes.sizeof(_lib.EigsStats) == 72
 
 
