@@ -61,6 +61,21 @@ def test_eigs_rmat14_matches_oracle(mode, pass1):
     assert s.min() > 1 - 1e-6
 
 
+@pytest.mark.parametrize("name,which", [("rmat14", "LM"), ("rmat12", "LA")])
+def test_eigs_local_first_pass_matches_full(name, which):
+    """First Gram-Schmidt pass from the projected matrix's symmetry (orth_local, the default)
+    against the full first pass: the same eigenvalues (to 1e-10 relative), both converged,
+    residuals within tolerance by the oracle's SpMM, restart counts within a few."""
+    g = graphgen.rmat(14 if name == "rmat14" else 12, seed=2)
+    with fe.Csr.from_graph(g) as h:
+        ev1, X1, st1 = fe.eigs(h, 8, 4, 8, 1e-8, which, seed=3)
+        ev0, X0, st0 = fe.eigs(h, 8, 4, 8, 1e-8, which, seed=3, orth_local=False)
+    assert st1["converged"] and st0["converged"]
+    assert np.allclose(ev1, ev0, rtol=1e-10, atol=1e-10 * np.abs(ev0).max())
+    _check_pairs(g, ev1, X1, 1e-8, np.abs(ev0).max())
+    assert abs(st1["restarts"] - st0["restarts"]) <= max(5, st0["restarts"] // 5)
+
+
 def test_eigs_same_start_same_iteration_as_oracle():
     g = graphgen.rmat(12, seed=4)
     start = graphgen.normal_block(g.n, 4, seed=9)
