@@ -19,6 +19,10 @@ the CPU oracle on a bounded sample.
     python bench.py --config mixed24|learned24|semiext27     (single configurations; semiext27
                                                               is not in the default run: its
                                                               graph generation alone takes ~2 min)
+    python bench.py --only solve [--solve-mode mixed]        (timed solves only)
+    python bench.py --only spmm1|gram1|ugram1|tcrestart|tcupdate|tcgram
+                                                             (launches of one kernel, for
+                                                              profiler captures)
 
 Under torchrun (N > 1) every rank solves its own copy of the workload (replicas: one solve
 runs on one GPU and is not split across GPUs); value = all ranks' solves / the slowest rank's
