@@ -68,6 +68,29 @@ def test_null_and_bad_arguments():
     assert lib.fe_csr_create(0, None, None, ctypes.byref(out)) == _lib.FE_ERR_INVALID
 
 
+def test_unaligned_blocks_rejected_on_host():
+    """Block arguments 8 bytes off a 16-byte boundary: FE_ERR_INVALID with an alignment message
+    from every block operation, before any device work (the pointers are never touched)."""
+    lib = fe.load()
+    V, W, O, C = (ctypes.c_void_p(0x100008), ctypes.c_void_p(0x200000), ctypes.c_void_p(0x300008),
+                  ctypes.c_void_p(0x400000))
+    Va = ctypes.c_void_p(0x100000)
+    f64, n = 1, 1024
+    calls = [
+        lambda: lib.fe_block_gram_ex(V, n, 2, 4, W, 4, f64, 1.0, C, 0),
+        lambda: lib.fe_block_gram(Va, n, 2, 4, ctypes.c_void_p(0x200008), 4, f64, 1.0, C),
+        lambda: lib.fe_block_gram_noalloc(V, n, 2, 4, W, 4, f64, 1.0, C),
+        lambda: lib.fe_block_update_ex(V, n, 2, 4, C, 1.0, 1.0, W, 4, f64, 0),
+        lambda: lib.fe_block_update(Va, n, 2, 4, C, 1.0, 1.0, ctypes.c_void_p(0x200008), 4, f64),
+        lambda: lib.fe_block_combine(Va, n, 2, 4, C, 2, O, f64, 0),
+        lambda: lib.fe_block_update_gram(V, n, 2, 4, C, 1.0, 1.0, W, f64, C),
+        lambda: lib.fe_block_orth(Va, n, 2, 4, ctypes.c_void_p(0x200008), f64, 1.0, 1, C, C, None),
+    ]
+    for call in calls:
+        assert call() == _lib.FE_ERR_INVALID
+        assert b"16-byte aligned" in lib.fe_last_error()
+
+
 def test_bad_index_format_rejected_on_host():
     lib = fe.load()
     rowptr = np.array([0, 1, 2], dtype=np.int64)
