@@ -295,9 +295,10 @@ int fe_block_update_gram(const void* V, int64_t n, int nv, int b, const double* 
  * engine (fe_engine): for FP64 with K = nv*bv <= 64 and N = nout*bv <= 32, FE_ENGINE_AUTO and
  * FE_ENGINE_TC use the tensor cores: every V row is cut, relative to its largest exponent, into
  * seven 8-bit digits, every Y column likewise; the digit products (exact in FP16 x FP16 -> FP32
- * for K <= 32 per accumulator) of weight classes i + j <= 6 are summed on the tensor cores and
- * assembled in 128-bit integer arithmetic, so that |error| <= 2^-49 K max_c|V[r][c]|
- * max_c|Y[c][q]| + 2^-52 |result| (results below 2^-1022 flush to zero; entries must be finite,
+ * for K <= 32 per accumulator) of weight classes i + j <= 6 are summed on the tensor cores,
+ * assembled in integer arithmetic (two 64-bit words, then the value without its 12 lowest bits)
+ * and rounded once, so that |error| <= 2^-49 (K + 1) max_c|V[r][c]| max_c|Y[c][q]|
+ * + 2^-52 |result| (results below 2^-1022 flush to zero; entries must be finite,
  * subnormal entries are read as zero).  Otherwise, and for FE_ENGINE_FMA, FMA kernels in dt
  * (FP32 blocks: FP32 arithmetic).  Errors: FE_ERR_INVALID (including FE_ENGINE_TC with an
  * unsupported shape), FE_ERR_OOM, FE_ERR_CUDA.  Asynchronous.

@@ -4,7 +4,7 @@ MvTimesMatAddMv, fe_block_gram_ex (Table 1 "op3", MvTransMv) against the oracle'
 and of the solver with tensor-core restart products and second Gram-Schmidt pass against the
 oracle's Block Krylov-Schur.
 
-Bounds: the stated worst case |err| <= 2^-49 K max_c|V[r][c]| max_c|Y[c][q]| + 2^-52 |ref|
+Bounds: the stated worst case |err| <= 2^-49 (K + 1) max_c|V[r][c]| max_c|Y[c][q]| + 2^-52 |ref|
 (+ 2^-1022: results below the normal range flush to zero),
 and the FP64 block-operation tolerance 1e-13 (|V| |Y|) on N(0,1) data; integer data whose
 products fit in 53 bits are reproduced exactly.
@@ -40,7 +40,7 @@ def _check(Vh, Yh, got):
     K = AA.shape[1]
     err = np.abs(got - ref)
     # (results below the normal range, 2^-1022, flush to zero)
-    stated = (2.0 ** -49 * K * np.abs(AA).max(axis=1)[:, None] * np.abs(Yh).max(axis=0)[None, :]
+    stated = (2.0 ** -49 * (K + 1) * np.abs(AA).max(axis=1)[:, None] * np.abs(Yh).max(axis=0)[None, :]
               + 2.0 ** -52 * np.abs(ref) + 2.0 ** -1022)
     assert (err <= stated).all(), f"stated bound: worst {np.max(err - stated):.3e}"
     return err, np.abs(AA) @ np.abs(Yh)
@@ -141,7 +141,7 @@ def test_tc_update_matches_oracle(shape, aligned):
     K = AA.shape[1]
     err = np.abs(got - ref)
     vc = np.abs(AA) @ np.abs(Ch)
-    stated = (2.0 ** -49 * K * np.abs(AA).max(axis=1)[:, None] * np.abs(Ch).max(axis=0)[None, :]
+    stated = (2.0 ** -49 * (K + 1) * np.abs(AA).max(axis=1)[:, None] * np.abs(Ch).max(axis=0)[None, :]
               + 2.0 ** -52 * (vc + np.abs(Wh)) + 2.0 ** -1022)
     assert (err <= stated).all(), f"stated bound: worst {np.max(err - stated):.3e}"
     assert (err <= 1e-13 * (vc + np.abs(Wh))).all()
