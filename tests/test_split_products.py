@@ -194,3 +194,24 @@ def test_op3_tile_within_stated_bound():
                      * Fraction(float(np.abs(W[:, q]).max())) + Fraction(2) ** -52 * abs(ex[c][q])
                      + Fraction(2) ** -1022)
             assert err <= bound, (c, q, float(err), float(bound))
+
+
+def test_fp16_digit_encoding_constants():
+    """The FP16 digit encoding of the tensor-core kernels, checked against IEEE binary16: the
+    bit pattern 0x6400 | d is 1024 + d for every digit d in [0, 255]; 0x3C00 / 0xBC00 are +1 / -1;
+    XOR with 0xD800 turns +-1 into -+1024; and (1024 + d) s + (-1024 s) = s d exactly, so one
+    FP16 FMA per digit gives the signed digit (products of two digits, at most 255^2, and sums of
+    up to 258 of them are exact in the FP32 accumulator: 258 * 255^2 < 2^24)."""
+    d = np.arange(256, dtype=np.uint16)
+    enc = (np.uint16(0x6400) | d).view(np.float16)
+    assert np.array_equal(enc.astype(np.float64), 1024.0 + d)
+    for sbits, sval in ((0x3C00, 1.0), (0xBC00, -1.0)):
+        s = np.array([sbits], dtype=np.uint16).view(np.float16)[0]
+        c = np.array([sbits ^ 0xD800], dtype=np.uint16).view(np.float16)[0]
+        assert float(s) == sval and float(c) == -1024.0 * sval
+        # each step is exact in binary16 (|values| <= 1279 < 2^11), so the FMA equals this
+        prod = (enc * s).astype(np.float64)
+        assert np.array_equal(prod, (1024.0 + d) * sval)
+        out = (enc * s + c).astype(np.float64)
+        assert np.array_equal(out, sval * d)
+    assert 258 * 255 ** 2 < 2 ** 24 < 259 * 255 ** 2      # 258 is the largest safe count
