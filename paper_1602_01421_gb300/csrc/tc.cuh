@@ -124,16 +124,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)1 << 46;
   return d;
 }
-// Instruction descriptor of tcgen05.mma.kind::f16: BF16 A and B, FP32 D, both K-major, no
-// negation or sparsity; N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4)                      // D format: F32
-         | (1u << 7)                    // A format: BF16
-         | (1u << 10)                   // B format: BF16
-         | ((uint32_t)(N >> 3) << 17)   // N
-         | ((uint32_t)(M >> 4) << 24);  // M
-}
-// The same with FP16 A and B (format code 0).
+// Instruction descriptor of tcgen05.mma.kind::f16: FP16 A and B (format code 0), FP32 D, both
+// K-major, no negation or sparsity; N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4)                      // D format: F32
          | ((uint32_t)(N >> 3) << 17)   // N
@@ -142,7 +134,7 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
 
 // ---------------------------------------------------------------- MMA, commit, loads
 // D[tmem] = A x B^T (accumulate = 0) or D += A x B^T (accumulate = 1); A is M x 16, B is N x 16
-// (both K-major, both FP16 or both BF16 as the instruction descriptor says), D is M x N FP32
+// (both K-major, both FP16 as the instruction descriptor says), D is M x N FP32
 // (lane = row, column = n for M = 128).
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
