@@ -382,12 +382,6 @@ static int check_eigs_args(fe_csr h, int nev, int block, int nblocks, double tol
   return FE_OK;
 }
 
-static int pow2_at_least(int x) {
-  int p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
 }  // namespace fe
 
 using namespace fe;
