@@ -19,7 +19,6 @@ import ctypes
 
 import numpy as np
 
-from . import _lib
 from ._lib import check, load
 
 

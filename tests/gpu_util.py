@@ -1,7 +1,6 @@
 """Helpers for the GPU parity tests (the CUDA path is compared with the CPU oracle)."""
 import numpy as np
 
-import graphgen
 from oracle import core
 
 

@@ -7,7 +7,6 @@ import re
 import numpy as np
 import pytest
 
-import graphgen
 import paper_1602_01421_gb300 as fe
 from paper_1602_01421_gb300 import _lib
 

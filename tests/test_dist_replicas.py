@@ -3,8 +3,6 @@ the slowest rank's time), exercised with 2 gloo ranks on the CPU."""
 import os
 import socket
 
-import pytest
-import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

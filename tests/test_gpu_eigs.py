@@ -11,7 +11,7 @@ import graphgen
 import paper_1602_01421_gb300 as fe
 from oracle import bks, core
 from tests import closed_forms
-from tests.gpu_util import to_dev, torch
+from tests.gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
 

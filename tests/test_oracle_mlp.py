@@ -1,7 +1,6 @@
 """Pins for the learned-start oracle (oracle/mlp.py): finite differences, invariances, brute
 force for the features, Adam's first step in closed form."""
 import numpy as np
-import pytest
 
 import graphgen
 from oracle import mlp, rng
