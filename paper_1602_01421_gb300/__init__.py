@@ -28,6 +28,8 @@ def _torch():
 
 def _stream():
     torch = _torch()
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the library's kernels need a GPU (there is no CPU path)")
     load().fe_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
