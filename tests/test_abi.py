@@ -137,3 +137,16 @@ def test_struct_field_offsets_match_c_compiler(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_mlp_param_count_matches_the_oracles_packing():
+    """fe_mlp_param_count (host) against the oracle's packed layout [W1, b1, W2, b2, W3, b3];
+    -1 for unsupported widths."""
+    from oracle import mlp
+    lib = fe.load()
+    for hidden in (32, 64):
+        for b in (1, 2, 4, 8, 16):
+            assert lib.fe_mlp_param_count(hidden, b) == mlp.param_count(hidden, b) \
+                == 8 * hidden + hidden + hidden * hidden + hidden + hidden * b + b
+    for hidden, b in ((16, 4), (32, 3), (48, 4), (64, 32)):
+        assert lib.fe_mlp_param_count(hidden, b) == -1
