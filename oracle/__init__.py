@@ -1,8 +1,10 @@
 """CPU oracle for the FlashEigen hot path (arXiv 1602.01421).
 
-TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
-leg may import this package.  The CUDA library never calls it, and it shares no code with
-the CUDA library: it is a plain, slow, FP64 restatement of what the method computes.
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (the
+CPU baseline and the reference arm) may import this package; bench.py's large-graph legs also
+use its SpMM to check the residuals of the eigenpairs they report, after the timed solves.  The
+CUDA library never calls it, and it shares no code with the CUDA library: it is a plain, slow,
+FP64 restatement of what the method computes.
 
 Contents (each function cites the passage it follows):
   core.spmm / core.spmm_rows   Y = A X, Section 3.3 (plain C, FP64 accumulate)
