@@ -189,18 +189,22 @@ def _unsorted_with_duplicates(seed):
     return rowptr, colidx
 
 
-def _graphs():
-    g12 = graphgen.rmat(12, seed=3)
-    star = graphgen.star(9000)
-    cyc = graphgen.cycle(1001)
-    comp = graphgen.complete(70)
-    rp, ci = _unsorted_with_duplicates(4)
-    return {"rmat12": (g12.rowptr, g12.colidx), "star9000": (star.rowptr, star.colidx),
-            "cycle1001": (cyc.rowptr, cyc.colidx), "complete70": (comp.rowptr, comp.colidx),
-            "unsorted_dup": (rp, ci)}
+def _csr(g):
+    return g.rowptr, g.colidx
 
 
-GRAPHS = _graphs()
+GRAPHS = {"rmat12": lambda: _csr(graphgen.rmat(12, seed=3)),
+          "star9000": lambda: _csr(graphgen.star(9000)),
+          "cycle1001": lambda: _csr(graphgen.cycle(1001)),
+          "complete70": lambda: _csr(graphgen.complete(70)),
+          "unsorted_dup": lambda: _unsorted_with_duplicates(4)}
+_made = {}
+
+
+def _graph(name):
+    if name not in _made:
+        _made[name] = GRAPHS[name]()
+    return _made[name]
 # (tail_max, hub_min, hub_chunk): the defaults, the packed default tail, and tiny thresholds that
 # send rows of every graph down every path
 PARAMS = [(128, 4096, 4096), (16, 4096, 4096), (8, 64, 32), (0, 16, 7)]
@@ -210,7 +214,7 @@ PARAMS = [(128, 4096, 4096), (16, 4096, 4096), (8, 64, 32), (0, 16, 7)]
 @pytest.mark.parametrize("params", PARAMS)
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 def test_plan_matches_csr(dump_exe, tmp_path, name, params, packed):
-    rowptr, colidx = GRAPHS[name]
+    rowptr, colidx = _graph(name)
     n = len(rowptr) - 1
     for r0, r1 in ((0, n), (n // 3, n - n // 5)):          # whole matrix and a row panel
         p = build_plan(dump_exe, tmp_path, rowptr, colidx, r0, r1, *params, packed)
@@ -219,7 +223,7 @@ def test_plan_matches_csr(dump_exe, tmp_path, name, params, packed):
 
 def test_plan_check_is_sensitive(dump_exe, tmp_path):
     """A plan with one ELL entry or one gap bit changed fails the checks."""
-    rowptr, colidx = GRAPHS["rmat12"]
+    rowptr, colidx = _graph("rmat12")
     n = len(rowptr) - 1
     p = build_plan(dump_exe, tmp_path, rowptr, colidx, 0, n, 8, 64, 32, False)
     p["ell"] = p["ell"].copy()
