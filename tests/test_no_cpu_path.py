@@ -35,10 +35,19 @@ def _calls():
     return calls
 
 
-@pytest.mark.parametrize("name", sorted(_calls()))
+NAMES = ["block_gram", "block_gram_tc", "block_update", "block_update_tc", "block_update_gram",
+         "block_combine", "block_orth", "block_orth_first", "mlp_forward", "mlp_span_loss_grad",
+         "mlp_adam", "random_normal"]
+
+
+@pytest.mark.parametrize("name", NAMES)
 def test_host_tensors_are_refused(name):
+    calls = _calls()
+    if name not in calls:
+        pytest.skip("a CUDA device is present and the call takes no tensor")
+    assert set(calls) <= set(NAMES)
     with pytest.raises((ValueError, RuntimeError)) as e:
-        _calls()[name]()
+        calls[name]()
     msg = str(e.value)
     assert "CUDA" in msg or "NVIDIA" in msg or "GPU" in msg, msg
 
